@@ -1,0 +1,609 @@
+/*
+ * Plain FP64 CPU oracle for BiCGStab with k right-hand sides.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference that the
+ * CUDA library is checked against.  It shares no code with the CUDA path and
+ * is never linked into it: only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load it.
+ *
+ * Source: B. Krasnopolsky, "Revisiting Performance of BiCGStab Methods for
+ * Solving Systems with Multiple Right-Hand Sides" (arXiv:1907.12874).
+ *   - Algorithm 1  (classical BiCGStab)             -> classical_basic()
+ *   - Algorithm 2  (merged BiCGStab)                -> classical_merged()
+ *   - Algorithm 4  (merged Pipelined BiCGStab)      -> pipelined_*()
+ *   - Algorithm 6  (merged Reordered BiCGStab, M^-1 = identity applied as a
+ *                   vector copy, as in the paper's benchmarks, Sec. 2.3)
+ *                                                   -> reordered_*()
+ *   - "basic" forms: one BLAS-like loop per vector operation, the
+ *     4-vector update of Algorithm 4 split into two calls (Table 2 and its
+ *     footnote); "merged" forms: one loop per merged line of the listings.
+ *   - Multi-vector layout: the k vectors are stored row-wise in one array,
+ *     element (i, c) at i*k + c (Sec. 3.1).
+ *
+ * How it is written (so a reader can check it against the listings by eye):
+ *   - every column c is solved on its own, as a strided view of the
+ *     interleaved arrays; nothing couples columns, so column c of a k-RHS
+ *     solve is bitwise the single-RHS solve of that column;
+ *   - every listing step is one loop over the rows, in listing order;
+ *   - dot products are Neumaier-compensated sums in ascending row order;
+ *   - build with -ffp-contract=off: no fused multiply-add, every + - * / and
+ *     sqrt is one IEEE round-to-nearest operation, evaluated left to right as
+ *     written.
+ *
+ * Readings where the paper is silent (the CUDA path follows the same rules):
+ *   R1 stop test: the listings compare a squared residual norm with eps^2;
+ *      eps = tol * ||b_c||_2 (relative tolerance), strict "<", per column.
+ *   R2 before the loop: ||b_c|| == 0 -> x_c = 0, converged, 0 iterations;
+ *      (r0,r0) < eps^2 -> converged with x0, 0 iterations.
+ *   R3 a column stops on its own break; its iteration count is the number of
+ *      iterates x_{j+1} it formed.  x_{j+1} is formed as soon as omega_j is
+ *      known and finite.  After maxit passes the status is MAXIT.
+ *   R4 shadow residual r^_0 = r_0.
+ *   R5 psi (classical), phi (Pipelined, Reordered): a zero denominator of
+ *      omega sets omega = 0.  Any other division by an exact zero in the
+ *      scalar recurrences (delta, rho, omega in beta, the alpha denominator
+ *      of Algorithm 4) is BREAKDOWN; a non-finite scalar is NONFINITE.
+ *   R6 merged norm estimates (theta - omega*phi, pi - omega*theta,
+ *      eta - omega*theta) are used as written for the stop test; the history
+ *      records sqrt(max(0, estimate)).  The basic classical form computes
+ *      (r,r) directly (Algorithm 1, conv-check line).
+ *   R7 Algorithm 4: the vectors of step j-1 start at zero, beta_{-1} = 0,
+ *      omega_{-1} = 0, alpha_0 = rho_0/(r_0,w_0).
+ *   R8 flag ORACLE_NO_STOP_TEST: no convergence test at all (fixed iteration
+ *      count benchmarking, Sec. 2.3 uses N_it = 1000); breakdown rules stay.
+ *
+ * Memory-traffic bookkeeping: every loop reports how many distinct full
+ * vectors it reads and writes (SpMV and the identity-preconditioner copies
+ * are counted apart), which reproduces the per-iteration counts of Table 2.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_CLASSICAL_BASIC 0
+#define ORACLE_CLASSICAL_MERGED 1
+#define ORACLE_REORDERED_BASIC 2
+#define ORACLE_REORDERED_MERGED 3
+#define ORACLE_PIPELINED_BASIC 4
+#define ORACLE_PIPELINED_MERGED 5
+
+#define ST_CONVERGED 0
+#define ST_MAXIT 1
+#define ST_BREAKDOWN 2
+#define ST_NONFINITE 3
+
+#define ORACLE_NO_STOP_TEST 1
+
+typedef struct {
+  int64_t n;
+  const int32_t *rowptr, *colidx;
+  const double *vals;
+} csr_t;
+
+/* A column of an interleaved N x k block: element i lives at p[i * s]. */
+typedef struct {
+  double *p;
+  int64_t s;
+} col_t;
+
+/* Vector read / write counters of the current solve (SpMV and copies apart). */
+typedef struct {
+  int64_t reads, writes, copies, spmv;
+} traffic_t;
+
+static traffic_t g_tr;
+static void rw(int r, int w) { g_tr.reads += r; g_tr.writes += w; }
+
+#define AT(v, i) ((v).p[(i) * (v).s])
+
+/* ---------------- primitives ---------------- */
+
+/* y = A x (one SpMV over a strided column). */
+static void spmv(const csr_t *A, col_t x, col_t y) {
+  g_tr.spmv++;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < A->n; ++i) {
+    double acc = 0.0;
+    for (int32_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) acc += A->vals[e] * AT(x, A->colidx[e]);
+    AT(y, i) = acc;
+  }
+}
+
+/* Neumaier-compensated sum of x_i * y_i, i ascending. */
+static double dot(const csr_t *A, col_t x, col_t y) {
+  double sum = 0.0, comp = 0.0;
+  for (int64_t i = 0; i < A->n; ++i) {
+    double p = AT(x, i) * AT(y, i);
+    double t = sum + p;
+    if (fabs(sum) >= fabs(p))
+      comp += (sum - t) + p;
+    else
+      comp += (p - t) + sum;
+    sum = t;
+  }
+  return sum + comp;
+}
+
+/* Compensated accumulator used inside merged loops (same arithmetic as dot()). */
+typedef struct {
+  double sum, comp;
+} acc_t;
+static void acc_add(acc_t *a, double p) {
+  double t = a->sum + p;
+  if (fabs(a->sum) >= fabs(p))
+    a->comp += (a->sum - t) + p;
+  else
+    a->comp += (p - t) + a->sum;
+  a->sum = t;
+}
+static double acc_val(const acc_t *a) { return a->sum + a->comp; }
+
+/* M^{-1} = identity, applied as a copy y = x (Sec. 2.3). */
+static void precond_copy(const csr_t *A, col_t x, col_t y) {
+  g_tr.copies++;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < A->n; ++i) AT(y, i) = AT(x, i);
+}
+
+static void set_zero(const csr_t *A, col_t y) {
+  for (int64_t i = 0; i < A->n; ++i) AT(y, i) = 0.0;
+}
+
+static double hist_value(double est) {
+  if (isnan(est)) return est;
+  return est > 0.0 ? sqrt(est) : 0.0;
+}
+
+static int finite(double v) { return isfinite(v) ? 1 : 0; }
+
+/* Per-column result record. */
+typedef struct {
+  int32_t iters, status;
+} res_t;
+
+/* Common set-up shared by every variant: r = b - A x, ||b||^2, rho0, eps^2.
+ * Returns 1 if the column is already finished (R2), 0 if it must iterate. */
+static int setup(const csr_t *A, col_t b, col_t x, col_t r, col_t tmp, double tol, int flags,
+                 double *rho0, double *eps2, double *hist, int64_t hs, res_t *out) {
+  spmv(A, x, tmp);
+  for (int64_t i = 0; i < A->n; ++i) AT(r, i) = AT(b, i) - AT(tmp, i);
+  double bn2 = dot(A, b, b);
+  *rho0 = dot(A, r, r);
+  *eps2 = tol * tol * bn2;
+  hist[0] = hist_value(*rho0);
+  (void)hs;
+  out->iters = 0;
+  if (bn2 == 0.0) { /* R2: b = 0 -> x = 0 */
+    set_zero(A, x);
+    hist[0] = 0.0;
+    out->status = ST_CONVERGED;
+    return 1;
+  }
+  if (!finite(bn2) || !finite(*rho0)) {
+    out->status = ST_NONFINITE;
+    return 1;
+  }
+  if (!(flags & ORACLE_NO_STOP_TEST) && *rho0 < *eps2) {
+    out->status = ST_CONVERGED;
+    return 1;
+  }
+  return 0;
+}
+
+/* ---------------- Algorithm 1: classical BiCGStab, basic form ---------------- */
+static void classical_basic(const csr_t *A, col_t b, col_t x, col_t r, col_t *w, double tol, int maxit,
+                            int flags, double *hist, int64_t hs, res_t *out) {
+  col_t r0 = w[0], p = w[1], v = w[2], s = w[3], t = w[4];
+  double rho, eps2;
+  if (setup(A, b, x, r, v, tol, flags, &rho, &eps2, hist, hs, out)) return;
+  const int64_t n = A->n;
+  for (int64_t i = 0; i < n; ++i) AT(r0, i) = AT(r, i); /* r^_0 = r_0 (R4) */
+  for (int64_t i = 0; i < n; ++i) AT(p, i) = AT(r, i);  /* p_0 = r_0 */
+  for (int j = 0; j < maxit; ++j) {
+    spmv(A, p, v);                         /* v_j = A p_j */
+    double delta = dot(A, v, r0); rw(2, 0); /* delta_j = (v_j, r_0) */
+    if (!finite(delta)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    if (delta == 0.0) { out->iters = j; out->status = ST_BREAKDOWN; return; }
+    double alpha = rho / delta;
+    if (!finite(alpha)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    for (int64_t i = 0; i < n; ++i) AT(s, i) = AT(r, i) - alpha * AT(v, i); /* s_j */
+    rw(2, 1);
+    spmv(A, s, t);                        /* t_j = A s_j */
+    double phi = dot(A, t, s); rw(2, 0);  /* phi_j = (t_j, s_j) */
+    double psi = dot(A, t, t); rw(1, 0);  /* psi_j = (t_j, t_j) */
+    if (!finite(phi) || !finite(psi)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    double omega = psi == 0.0 ? 0.0 : phi / psi; /* R5 */
+    if (!finite(omega)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(p, i) + omega * AT(s, i);
+    rw(3, 1);
+    for (int64_t i = 0; i < n; ++i) AT(r, i) = AT(s, i) - omega * AT(t, i);
+    rw(2, 1);
+    out->iters = j + 1;
+    double rr = dot(A, r, r); rw(1, 0);   /* (r_{j+1}, r_{j+1}) */
+    hist[(j + 1) * hs] = hist_value(rr);
+    if (!finite(rr)) { out->status = ST_NONFINITE; return; }
+    if (!(flags & ORACLE_NO_STOP_TEST) && rr < eps2) { out->status = ST_CONVERGED; return; }
+    double rho1 = dot(A, r, r0); rw(2, 0); /* rho_{j+1} = (r_{j+1}, r_0) */
+    if (!finite(rho1)) { out->status = ST_NONFINITE; return; }
+    if (rho == 0.0 || omega == 0.0) { out->status = ST_BREAKDOWN; return; }
+    double beta = (rho1 / rho) * (alpha / omega);
+    if (!finite(beta)) { out->status = ST_NONFINITE; return; }
+    for (int64_t i = 0; i < n; ++i) AT(p, i) = AT(r, i) + beta * (AT(p, i) - omega * AT(v, i));
+    rw(3, 1);
+    rho = rho1;
+  }
+  out->status = ST_MAXIT;
+}
+
+/* ---------------- Algorithm 2: merged BiCGStab ---------------- */
+static void classical_merged(const csr_t *A, col_t b, col_t x, col_t r, col_t *w, double tol, int maxit,
+                             int flags, double *hist, int64_t hs, res_t *out) {
+  col_t r0 = w[0], p = w[1], v = w[2], s = w[3], t = w[4];
+  double rho, eps2;
+  if (setup(A, b, x, r, v, tol, flags, &rho, &eps2, hist, hs, out)) return;
+  const int64_t n = A->n;
+  for (int64_t i = 0; i < n; ++i) { AT(r0, i) = AT(r, i); AT(p, i) = AT(r, i); }
+  for (int j = 0; j < maxit; ++j) {
+    spmv(A, p, v);
+    double delta = dot(A, v, r0); rw(2, 0);
+    if (!finite(delta)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    if (delta == 0.0) { out->iters = j; out->status = ST_BREAKDOWN; return; }
+    double alpha = rho / delta;
+    if (!finite(alpha)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    for (int64_t i = 0; i < n; ++i) AT(s, i) = AT(r, i) - alpha * AT(v, i);
+    rw(2, 1);
+    spmv(A, s, t);
+    /* group 1: phi = (t,s), psi = (t,t), theta = (s,s) in one pass over t and s */
+    acc_t aphi = {0, 0}, apsi = {0, 0}, ath = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+      double ti = AT(t, i), si = AT(s, i);
+      acc_add(&aphi, ti * si);
+      acc_add(&apsi, ti * ti);
+      acc_add(&ath, si * si);
+    }
+    rw(2, 0);
+    double phi = acc_val(&aphi), psi = acc_val(&apsi), theta = acc_val(&ath);
+    if (!finite(phi) || !finite(psi) || !finite(theta)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    double omega = psi == 0.0 ? 0.0 : phi / psi;
+    if (!finite(omega)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    double est = theta - omega * phi; /* (r_{j+1}, r_{j+1}) = (s,s) - omega (s,t) */
+    hist[(j + 1) * hs] = hist_value(est);
+    int stop = !finite(est) || (!(flags & ORACLE_NO_STOP_TEST) && est < eps2);
+    if (stop) {
+      /* group 2 (break branch): x and r update in one pass */
+      for (int64_t i = 0; i < n; ++i) {
+        double si = AT(s, i);
+        AT(x, i) = AT(x, i) + alpha * AT(p, i) + omega * si;
+        AT(r, i) = si - omega * AT(t, i);
+      }
+      rw(4, 2);
+      out->iters = j + 1;
+      out->status = finite(est) ? ST_CONVERGED : ST_NONFINITE;
+      return;
+    }
+    /* group 3: x, r update and rho_{j+1} = (r_{j+1}, r_0) in one pass */
+    acc_t arho = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+      double si = AT(s, i);
+      AT(x, i) = AT(x, i) + alpha * AT(p, i) + omega * si;
+      double ri = si - omega * AT(t, i);
+      AT(r, i) = ri;
+      acc_add(&arho, ri * AT(r0, i));
+    }
+    rw(5, 2);
+    out->iters = j + 1;
+    double rho1 = acc_val(&arho);
+    if (!finite(rho1)) { out->status = ST_NONFINITE; return; }
+    if (rho == 0.0 || omega == 0.0) { out->status = ST_BREAKDOWN; return; }
+    double beta = (rho1 / rho) * (alpha / omega);
+    if (!finite(beta)) { out->status = ST_NONFINITE; return; }
+    for (int64_t i = 0; i < n; ++i) AT(p, i) = AT(r, i) + beta * (AT(p, i) - omega * AT(v, i));
+    rw(3, 1);
+    rho = rho1;
+  }
+  out->status = ST_MAXIT;
+}
+
+/* ---------------- Algorithm 6: Reordered BiCGStab, M^-1 = copy ---------------- */
+static void reordered(const csr_t *A, col_t b, col_t x, col_t r, col_t *w, double tol, int maxit, int flags,
+                      int merged, double *hist, int64_t hs, res_t *out) {
+  col_t r0 = w[0], z = w[1], vh = w[2], v = w[3], s = w[4], th = w[5], t = w[6], rt = w[7], q = w[8];
+  double rho, eps2;
+  if (setup(A, b, x, r, v, tol, flags, &rho, &eps2, hist, hs, out)) return;
+  const int64_t n = A->n;
+  for (int64_t i = 0; i < n; ++i) AT(r0, i) = AT(r, i); /* r^_0 = r_0 */
+  precond_copy(A, r, z);                                /* z_0 = M^-1 r_0 */
+  for (int64_t i = 0; i < n; ++i) AT(vh, i) = AT(z, i); /* v^_0 = z_0 */
+  for (int j = 0; j < maxit; ++j) {
+    spmv(A, vh, v);                        /* v_j = A v^_j */
+    double delta = dot(A, v, r0); rw(2, 0); /* delta_j = (v_j, r_0) */
+    precond_copy(A, v, s);                 /* s_j = M^-1 v_j */
+    if (!finite(delta)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    if (delta == 0.0) { out->iters = j; out->status = ST_BREAKDOWN; return; }
+    double alpha = rho / delta;
+    if (!finite(alpha)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    for (int64_t i = 0; i < n; ++i) AT(th, i) = AT(z, i) - alpha * AT(s, i); /* t^_j */
+    rw(2, 1);
+    spmv(A, th, t);                        /* t_j = A t^_j */
+    double theta, phi, psi, eta;
+    if (merged) {
+      /* r~ = r - alpha v with theta = (t,r~), phi = (t,t), psi = (t,r_0), eta = (r~,r~) */
+      acc_t a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0}, a4 = {0, 0};
+      for (int64_t i = 0; i < n; ++i) {
+        double ri = AT(r, i) - alpha * AT(v, i);
+        AT(rt, i) = ri;
+        double ti = AT(t, i);
+        acc_add(&a1, ti * ri);
+        acc_add(&a2, ti * ti);
+        acc_add(&a3, ti * AT(r0, i));
+        acc_add(&a4, ri * ri);
+      }
+      rw(4, 1);
+      theta = acc_val(&a1); phi = acc_val(&a2); psi = acc_val(&a3); eta = acc_val(&a4);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(rt, i) = AT(r, i) - alpha * AT(v, i);
+      rw(2, 1);
+      theta = dot(A, t, rt); rw(2, 0);
+      phi = dot(A, t, t); rw(1, 0);
+      psi = dot(A, t, r0); rw(2, 0);
+      eta = dot(A, rt, rt); rw(1, 0);
+    }
+    precond_copy(A, t, q);                 /* q_j = M^-1 t_j */
+    if (!finite(theta) || !finite(phi) || !finite(psi) || !finite(eta)) {
+      out->iters = j; out->status = ST_NONFINITE; return;
+    }
+    double omega = phi == 0.0 ? 0.0 : theta / phi;
+    if (!finite(omega)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    for (int64_t i = 0; i < n; ++i) AT(r, i) = AT(rt, i) - omega * AT(t, i); /* r_{j+1} */
+    rw(2, 1);
+    double est = eta - omega * theta;
+    hist[(j + 1) * hs] = hist_value(est);
+    int status = -1;
+    if (!finite(est)) status = ST_NONFINITE;
+    else if (!(flags & ORACLE_NO_STOP_TEST) && est < eps2) status = ST_CONVERGED;
+    double rho1 = 0.0, beta = 0.0;
+    if (status < 0) {
+      rho1 = -omega * psi; /* rho_{j+1} = -omega_j psi_j */
+      if (rho == 0.0 || omega == 0.0) status = ST_BREAKDOWN;
+      else {
+        beta = (rho1 / rho) * (alpha / omega);
+        if (!finite(beta) || !finite(rho1)) status = ST_NONFINITE;
+      }
+    }
+    if (status >= 0) { /* break branch: only x_{j+1} */
+      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(vh, i) + omega * AT(th, i);
+      rw(3, 1);
+      out->iters = j + 1;
+      out->status = status;
+      return;
+    }
+    if (merged) {
+      /* x, z and v^ in one pass */
+      for (int64_t i = 0; i < n; ++i) {
+        double vhi = AT(vh, i), thi = AT(th, i);
+        AT(x, i) = AT(x, i) + alpha * vhi + omega * thi;
+        double zi = thi - omega * AT(q, i);
+        AT(z, i) = zi;
+        AT(vh, i) = zi + beta * (vhi - omega * AT(s, i));
+      }
+      rw(5, 3);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(vh, i) + omega * AT(th, i);
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(z, i) = AT(th, i) - omega * AT(q, i);
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(vh, i) = AT(z, i) + beta * (AT(vh, i) - omega * AT(s, i));
+      rw(3, 1);
+    }
+    out->iters = j + 1;
+    rho = rho1;
+  }
+  out->status = ST_MAXIT;
+}
+
+/* ---------------- Algorithm 4: Pipelined BiCGStab ---------------- */
+static void pipelined(const csr_t *A, col_t b, col_t x, col_t r, col_t *w, double tol, int maxit, int flags,
+                      int merged, double *hist, int64_t hs, res_t *out) {
+  col_t r0 = w[0], wv = w[1], t = w[2], p = w[3], s = w[4], z = w[5], v = w[6], q = w[7], y = w[8], tmp = w[9];
+  double rho, eps2;
+  if (setup(A, b, x, r, v, tol, flags, &rho, &eps2, hist, hs, out)) return;
+  const int64_t n = A->n;
+  for (int64_t i = 0; i < n; ++i) AT(r0, i) = AT(r, i);
+  spmv(A, r, wv); /* w_0 = A r_0 */
+  spmv(A, wv, t); /* t_0 = A w_0 */
+  double rw0 = dot(A, r0, wv);
+  if (!finite(rw0)) { out->status = ST_NONFINITE; return; }
+  if (rw0 == 0.0) { out->status = ST_BREAKDOWN; return; }
+  double alpha = rho / rw0; /* alpha_0 = rho_0 / (r_0, w_0) */
+  if (!finite(alpha)) { out->status = ST_NONFINITE; return; }
+  double beta = 0.0, omega = 0.0; /* beta_{-1} = 0, omega_{-1} = 0 (R7) */
+  set_zero(A, p); set_zero(A, s); set_zero(A, z); set_zero(A, v);
+  for (int j = 0; j < maxit; ++j) {
+    double theta, phi, pi;
+    if (merged) {
+      /* p, s, z, q, y in one pass with theta = (q,y), phi = (y,y), pi = (q,q) */
+      acc_t a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
+      for (int64_t i = 0; i < n; ++i) {
+        double ri = AT(r, i), wi = AT(wv, i), si = AT(s, i), zi = AT(z, i);
+        double pn = ri + beta * (AT(p, i) - omega * si);
+        double sn = wi + beta * (si - omega * zi);
+        double zn = AT(t, i) + beta * (zi - omega * AT(v, i));
+        double qn = ri - alpha * sn;
+        double yn = wi - alpha * zn;
+        AT(p, i) = pn; AT(s, i) = sn; AT(z, i) = zn; AT(q, i) = qn; AT(y, i) = yn;
+        acc_add(&a1, qn * yn);
+        acc_add(&a2, yn * yn);
+        acc_add(&a3, qn * qn);
+      }
+      rw(7, 5);
+      theta = acc_val(&a1); phi = acc_val(&a2); pi = acc_val(&a3);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(p, i) = AT(r, i) + beta * (AT(p, i) - omega * AT(s, i));
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(s, i) = AT(wv, i) + beta * (AT(s, i) - omega * AT(z, i));
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(z, i) = AT(t, i) + beta * (AT(z, i) - omega * AT(v, i));
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(q, i) = AT(r, i) - alpha * AT(s, i);
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(y, i) = AT(wv, i) - alpha * AT(z, i);
+      rw(2, 1);
+      theta = dot(A, q, y); rw(2, 0);
+      phi = dot(A, y, y); rw(1, 0);
+      pi = dot(A, q, q); rw(1, 0);
+    }
+    spmv(A, z, v); /* v_j = A z_j */
+    if (!finite(theta) || !finite(phi) || !finite(pi)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    omega = phi == 0.0 ? 0.0 : theta / phi;
+    if (!finite(omega)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    if (merged) {
+      for (int64_t i = 0; i < n; ++i) {
+        double qi = AT(q, i);
+        AT(x, i) = AT(x, i) + alpha * AT(p, i) + omega * qi;
+        AT(r, i) = qi - omega * AT(y, i);
+      }
+      rw(4, 2);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(p, i) + omega * AT(q, i);
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(r, i) = AT(q, i) - omega * AT(y, i);
+      rw(2, 1);
+    }
+    out->iters = j + 1;
+    double est = pi - omega * theta;
+    hist[(j + 1) * hs] = hist_value(est);
+    if (!finite(est)) { out->status = ST_NONFINITE; return; }
+    if (!(flags & ORACLE_NO_STOP_TEST) && est < eps2) { out->status = ST_CONVERGED; return; }
+    double rho1, psi, sigma, delta;
+    if (merged) {
+      /* w_{j+1} = y - omega (t - alpha v) with rho, psi, sigma, delta in one pass */
+      acc_t a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0}, a4 = {0, 0};
+      for (int64_t i = 0; i < n; ++i) {
+        double wn = AT(y, i) - omega * (AT(t, i) - alpha * AT(v, i));
+        AT(wv, i) = wn;
+        double r0i = AT(r0, i);
+        acc_add(&a1, r0i * AT(r, i));
+        acc_add(&a2, r0i * AT(z, i));
+        acc_add(&a3, r0i * wn);
+        acc_add(&a4, r0i * AT(s, i));
+      }
+      rw(7, 1);
+      rho1 = acc_val(&a1); psi = acc_val(&a2); sigma = acc_val(&a3); delta = acc_val(&a4);
+    } else {
+      /* the 4-vector update takes two BLAS-like calls (Table 2 footnote) */
+      for (int64_t i = 0; i < n; ++i) AT(tmp, i) = AT(t, i) - alpha * AT(v, i);
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(wv, i) = AT(y, i) - omega * AT(tmp, i);
+      rw(2, 1);
+      rho1 = dot(A, r0, r); rw(2, 0);
+      psi = dot(A, r0, z); rw(2, 0);
+      sigma = dot(A, r0, wv); rw(2, 0);
+      delta = dot(A, r0, s); rw(2, 0);
+    }
+    spmv(A, wv, t); /* t_{j+1} = A w_{j+1} */
+    if (!finite(rho1) || !finite(psi) || !finite(sigma) || !finite(delta)) { out->status = ST_NONFINITE; return; }
+    if (rho == 0.0 || omega == 0.0) { out->status = ST_BREAKDOWN; return; }
+    beta = (alpha / omega) * (rho1 / rho);
+    double den = sigma + beta * delta - beta * omega * psi;
+    if (!finite(beta) || !finite(den)) { out->status = ST_NONFINITE; return; }
+    if (den == 0.0) { out->status = ST_BREAKDOWN; return; }
+    alpha = rho1 / den;
+    if (!finite(alpha)) { out->status = ST_NONFINITE; return; }
+    rho = rho1;
+  }
+  out->status = ST_MAXIT;
+}
+
+/* ---------------- exported entry points ---------------- */
+
+/* Number of N-vectors of scratch per column a variant needs. */
+static int n_work(int variant) {
+  switch (variant) {
+    case ORACLE_CLASSICAL_BASIC:
+    case ORACLE_CLASSICAL_MERGED: return 5;
+    case ORACLE_REORDERED_BASIC:
+    case ORACLE_REORDERED_MERGED: return 9;
+    case ORACLE_PIPELINED_BASIC:
+    case ORACLE_PIPELINED_MERGED: return 10;
+    default: return -1;
+  }
+}
+
+/* y = A x for an interleaved N x k block (SpMV per column, Eq. for Sigma_mul's operation). */
+int oracle_spmm(int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals, int32_t k,
+                const double *X, double *Y) {
+  if (n < 0 || k < 1) return -1;
+  csr_t A = {n, rowptr, colidx, vals};
+  for (int32_t c = 0; c < k; ++c) {
+    col_t x = {(double *)X + c, k}, y = {Y + c, k};
+    spmv(&A, x, y);
+  }
+  return 0;
+}
+
+/* Solve A X = B column by column.
+ *   B, X0 (nullable = zero), X, R (nullable): N x k interleaved.
+ *   hist (nullable): (maxit+1) x k, entry (j, c) = estimate of ||r_j|| of column c,
+ *     NaN where column c formed no iterate j.
+ *   true_relres (nullable): ||b_c - A x_c|| / ||b_c|| after the solve (0 when b_c = 0).
+ *   traffic (nullable, 4 int64): vector reads, writes, identity copies, SpMVs summed over all
+ *     columns and iterations (set-up included).
+ * Returns 0, or -1 on a bad argument. */
+int oracle_solve(int variant, int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                 int32_t k, const double *B, const double *X0, double tol, int32_t maxit, int32_t flags,
+                 double *X, double *R, int32_t *iters, int32_t *status, double *hist, double *true_relres,
+                 int64_t *traffic) {
+  int nw = n_work(variant);
+  if (nw < 0 || n < 0 || k < 1 || maxit < 0 || !(tol >= 0.0)) return -1;
+  csr_t A = {n, rowptr, colidx, vals};
+  memset(&g_tr, 0, sizeof(g_tr));
+  double *work = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(nw + 2));
+  double *hbuf = (double *)malloc(sizeof(double) * (size_t)(maxit + 1));
+  if (!work || !hbuf) { free(work); free(hbuf); return -2; }
+  for (int32_t c = 0; c < k; ++c) {
+    col_t w[10];
+    for (int q = 0; q < nw; ++q) w[q] = (col_t){work + (size_t)q * n, 1};
+    col_t rloc = {work + (size_t)nw * n, 1};
+    col_t b = {(double *)B + c, k};
+    col_t x = {X + c, k};
+    for (int64_t i = 0; i < n; ++i) AT(x, i) = X0 ? X0[i * k + c] : 0.0;
+    for (int32_t j = 0; j <= maxit; ++j) hbuf[j] = NAN;
+    res_t res = {0, ST_MAXIT};
+    switch (variant) {
+      case ORACLE_CLASSICAL_BASIC: classical_basic(&A, b, x, rloc, w, tol, maxit, flags, hbuf, 1, &res); break;
+      case ORACLE_CLASSICAL_MERGED: classical_merged(&A, b, x, rloc, w, tol, maxit, flags, hbuf, 1, &res); break;
+      case ORACLE_REORDERED_BASIC: reordered(&A, b, x, rloc, w, tol, maxit, flags, 0, hbuf, 1, &res); break;
+      case ORACLE_REORDERED_MERGED: reordered(&A, b, x, rloc, w, tol, maxit, flags, 1, hbuf, 1, &res); break;
+      case ORACLE_PIPELINED_BASIC: pipelined(&A, b, x, rloc, w, tol, maxit, flags, 0, hbuf, 1, &res); break;
+      case ORACLE_PIPELINED_MERGED: pipelined(&A, b, x, rloc, w, tol, maxit, flags, 1, hbuf, 1, &res); break;
+    }
+    if (iters) iters[c] = res.iters;
+    if (status) status[c] = res.status;
+    if (hist)
+      for (int32_t j = 0; j <= maxit; ++j) hist[(int64_t)j * k + c] = hbuf[j];
+    if (R)
+      for (int64_t i = 0; i < n; ++i) R[i * k + c] = AT(rloc, i);
+    if (true_relres) {
+      col_t ax = {work + (size_t)(nw + 1) * n, 1};
+      spmv(&A, x, ax);
+      for (int64_t i = 0; i < n; ++i) AT(ax, i) = AT(b, i) - AT(ax, i);
+      double bn2 = dot(&A, b, b), rn2 = dot(&A, ax, ax);
+      true_relres[c] = bn2 == 0.0 ? 0.0 : sqrt(rn2) / sqrt(bn2);
+    }
+  }
+  if (traffic) {
+    traffic[0] = g_tr.reads; traffic[1] = g_tr.writes; traffic[2] = g_tr.copies; traffic[3] = g_tr.spmv;
+  }
+  free(work);
+  free(hbuf);
+  return 0;
+}
+
+/* Threads the OpenMP runtime will use for the parallel loops (1 without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+int oracle_threads(void) { return omp_get_max_threads(); }
+#else
+int oracle_threads(void) { return 1; }
+#endif
