@@ -1,0 +1,417 @@
+"""Benchmark: RHS-iterations/s of multi-RHS BiCGStab on GB300, merged vs plain forms.
+
+Workload (default): 3-D 7-point upwind convection-diffusion on a 128^3 grid
+(2,097,152 rows, 14,581,760 nonzeros, FP64 CSR), k = 32 right-hand sides
+U[-1,1], x0 = 0, relative tolerance 1e-8, merged classical BiCGStab
+(Algorithm 2 of Krasnopolsky, arXiv:1907.12874).  One step = one complete
+solve (set-up, iterations until every column stops, true residual).
+
+value    = sum over columns of iterations / solve time (device-resident inputs,
+           CUDA events on the solving stream, max over ranks);
+e2e      = the same through the C-ABI with pinned host buffers, the copies of
+           B in and X out inside the timed region;
+roofline = the dominant kernel (largest share of the per-kernel event times of
+           one profiled solve): algorithmic bytes or FP64 flops per launch over
+           its mean launch time, against the measured HBM copy bandwidth or the
+           FP64 peak (152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz);
+cpu_baseline = the FP64 oracle on a bounded sample on the host cores.
+
+Multi-GPU (torchrun): every rank solves its own k right-hand sides (different
+seeds) on its own GPU; there is no data-path collective (weak scaling).
+--impl reference times the oracle instead (the CPU reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk x flop/FMA x max clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--grid", type=int, default=128, help="grid edge n (n^3 unknowns)")
+    p.add_argument("--k", type=int, default=32, help="right-hand sides per GPU")
+    p.add_argument("--variant", default="classical_merged")
+    p.add_argument("--tol", type=float, default=1e-8)
+    p.add_argument("--maxit", type=int, default=5000)
+    p.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--sweep", action="store_true", help="also time every variant at k = 1..32")
+    p.add_argument("--eager", action="store_true",
+                   help="run every solve in the library's host-loop mode (same kernels, one launch at a time, "
+                        "CUDA events around each) instead of the CUDA graph; profilers cannot see kernels inside "
+                        "graphs with conditional nodes")
+    p.add_argument("--minimal", action="store_true",
+                   help="only the warm-up and timed solves (for profiler captures): no e2e, plain, kernel "
+                        "times or CPU baseline")
+    return p.parse_args()
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bicgk_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_algorithmic(name: str, n: int, nnz: int, k: int):
+    """Algorithmic bytes and FP64 flops of one launch of a kernel class (ideal x reuse)."""
+    from paper_1907_12874_gb300 import bicgk as bk  # noqa: F401
+    vec = 8.0 * n * k
+    if name.startswith("spmm"):
+        resid = name.startswith("spmm_resid")
+        b = 12.0 * nnz + 4.0 * (n + 1) + 2 * vec + (vec if resid else 0.0)
+        f = 2.0 * nnz * k + (n * k if resid else 0.0)
+        return b, f
+    table = {  # reads, writes, FP64 flops per element (FMA = 2)
+        "dot_delta": (2, 0, 2), "upd_s": (2, 1, 2), "merged_phi_psi_theta": (2, 0, 6),
+        "merged_x_r_rho": (5, 2, 8), "upd_p": (3, 1, 4), "dot_phi": (2, 0, 2), "dot_psi": (1, 0, 2),
+        "upd_x": (3, 1, 4), "upd_r": (2, 1, 2), "dot_rr": (1, 0, 2), "dot_rho": (2, 0, 2),
+        "precond_copy_s": (1, 1, 0), "precond_copy_q": (1, 1, 0), "upd_that": (2, 1, 2),
+        "merged_rtilde_4dots": (4, 1, 10), "merged_x_z_vhat": (5, 3, 10), "upd_rtilde": (2, 1, 2),
+        "dot_theta": (2, 0, 2), "dot_eta": (1, 0, 2), "upd_z": (2, 1, 2), "upd_vhat": (3, 1, 4),
+        "merged_pszqy_3dots": (7, 5, 22), "merged_x_r": (4, 2, 6), "merged_w_4dots": (7, 1, 12),
+        "upd_q": (2, 1, 2), "upd_y": (2, 1, 2), "dot_pi": (1, 0, 2), "upd_w_part1": (2, 1, 2),
+        "upd_w_part2": (2, 1, 2), "dot_sigma": (2, 0, 2), "setup_classical": (2, 2, 4),
+        "setup_reordered": (2, 3, 4), "setup_pipelined": (2, 5, 4), "dot_r0_w0": (2, 0, 2),
+        "dot_true_residual": (1, 0, 2),
+    }
+    r, w, fl = table.get(name, (0, 0, 0))
+    return (r + w) * vec, fl * n * k
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if current.
+
+    The summary records the hash of the CUDA sources it was taken on; a changed
+    kernel source makes the figure stale (reported as null).
+    """
+    path = os.path.join(ROOT, "profiles", "ncu_dram_traffic.md")
+    if not os.path.exists(path):
+        return {}
+    h = source_hash()
+    out = {}
+    for line in open(path):
+        m = re.match(r"\|\s*([a-z0-9_]+)\s*\|\s*(\d+)\s*\|\s*([0-9.e+]+)\s*\|\s*([0-9a-f]{12})\s*\|", line)
+        if m and m.group(4) == h:
+            out[(m.group(1), int(m.group(2)))] = float(m.group(3))
+    return out
+
+
+def source_hash() -> str:
+    hsh = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1907_12874_gb300", "csrc", "*"))):
+        hsh.update(open(p, "rb").read())
+    return hsh.hexdigest()[:12]
+
+
+def cpu_oracle_rate(A, B, variant, cols: int, iters: int):
+    """Oracle RHS-iterations/s on `cols` columns x `iters` fixed iterations of the workload."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.solve(A, B[:, :cols], tol=0.0, maxit=iters, variant=variant, flags=oracle.NO_STOP_TEST)
+    dt = time.perf_counter() - t0
+    return cols * iters / dt, dt
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(v: float, pg, device=None) -> float:
+    """Largest value over all ranks (the timing rule: the slowest rank sets the step time)."""
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_local: float, ms_local: float, pg, device=None) -> float:
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    if pg is None:
+        return units_local / (ms_local / 1e3)
+    import torch
+    t = torch.tensor([units_local], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item()) / (max_over_ranks(ms_local, pg, device) / 1e3)
+
+
+def run_reference(args):
+    """CPU reference arm: the FP64 oracle as it stands, on the host cores, rank 0 only."""
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    from paper_1907_12874_gb300 import inputs
+    A = inputs.convdiff7(args.grid)
+    B = inputs.rhs(A.n, args.k, 2)
+    cols, iters = 1, 10
+    for _ in range(args.warmup):
+        cpu_oracle_rate(A, B, args.variant, cols, iters)
+    rates, secs = [], 0.0
+    for _ in range(args.steps):
+        r, dt = cpu_oracle_rate(A, B, args.variant, cols, iters)
+        rates.append(r)
+        secs += dt
+    value = args.steps * cols * iters / secs
+    sample = f"{cols} column x {iters} fixed iterations of the {args.grid}^3 k={args.k} workload per step"
+    line = {
+        "impl": "reference", "metric": "RHS-iterations/s", "value": value, "unit": "RHS-iterations/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, A),
+        "cpu_baseline": {"value": value, "unit": "RHS-iterations/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "RHS-iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, A):
+    return {"workload": f"convdiff7 upwind {args.grid}^3 (beta=(1,0.5,0.25), h-scaled), k={args.k} RHS U[-1,1], "
+                        f"x0=0, rel tol {args.tol:g}, {args.variant}",
+            "n_rows": A.n, "nnz": A.nnz, "k": args.k, "variant": args.variant, "rel_tol": args.tol,
+            "l2": f"inputs larger than L2: each N x k vector is {8 * A.n * args.k / 1e6:.0f} MB",
+            "parallelism": "one independent k-RHS system per GPU"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1907_12874_gb300 import bicgk, inputs
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    A = inputs.convdiff7(args.grid)
+    B_host = inputs.rhs(A.n, args.k, 2 + rank)
+    op = bicgk.Operator(A)
+    if args.eager:
+        bicgk.set_profiling(op.handle, True)
+    Bd = torch.from_numpy(B_host).to(dev)
+    Xd = torch.empty_like(Bd)
+
+    def one(variant, B=Bd, X=Xd):
+        return op.solve(B, X=X, tol=args.tol, maxit=args.maxit, variant=variant, want_hist=False)
+
+    def timed(variant, steps, warmup, B=Bd, X=Xd, clocks=False):
+        for _ in range(warmup):
+            one(variant, B, X)
+        iters_total = 0
+        launches = 0
+        barrier(pg)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        e0.record(stream)
+        results = []
+        for _ in range(steps):
+            r = one(variant, B, X)
+            results.append(r)
+            launches += bicgk.last_stats(op.handle)["kernel_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.__exit__()
+        barrier(pg)
+        ms = e0.elapsed_time(e1)
+        iters_total = sum(int(r.iters.sum()) for r in results)
+        return ms, iters_total, launches, results, (sampler.summary() if sampler else None)
+
+    # headline: device-resident inputs
+    ms, its, launches, results, clocks = timed(args.variant, args.steps, args.warmup, clocks=not args.minimal)
+    value = aggregate_rate(float(its), ms, pg, dev)
+    ms = max_over_ranks(ms, pg, dev)
+    last = results[-1]
+    conv_ok = bool(np.all(last.status == 0))
+    relres = float(np.max(last.true_relres))
+
+    if args.minimal:
+        op.close()
+        if rank == 0:
+            print(json.dumps({"metric": "RHS-iterations/s", "value": value, "unit": "RHS-iterations/s",
+                              "ms_per_step": ms / args.steps, "eager": args.eager, "iters_per_rhs": float(its) / (args.steps * args.k),
+                              "config": workload_config(args, A), "minimal": True}), flush=True)
+        return
+
+    # end to end through the C-ABI with pinned host buffers
+    Bh = torch.from_numpy(B_host).pin_memory()
+    Xh = torch.empty_like(Bh).pin_memory()
+    ms_e2e, its_e2e, _, _, _ = timed(args.variant, args.steps, 1, B=Bh, X=Xh)
+    e2e_value = aggregate_rate(float(its_e2e), ms_e2e, pg, dev)
+    nbytes = 8 * A.n * args.k
+
+    out = {
+        "metric": "RHS-iterations/s", "value": value, "unit": "RHS-iterations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, A),
+        "iters_per_rhs": float(its) / (args.steps * args.k),
+        "converged": conv_ok, "max_true_relres": relres,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "RHS-iterations/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes + 8 * args.k + 8 * args.k},
+    }
+
+    # merged vs plain on the same GPU (the paper's comparison, Tab. 4)
+    if not args.no_plain:
+        plain = args.variant.replace("merged", "plain")
+        if plain != args.variant:
+            msp, itsp, _, _, _ = timed(plain, args.steps, 1)
+            vp = aggregate_rate(float(itsp), msp, pg, dev)
+            msp = max_over_ranks(msp, pg, dev)
+            out["plain"] = {"variant": plain, "value": vp, "ms_per_step": msp / args.steps,
+                            "merged_speedup": value / vp}
+
+    # per-kernel event times of one solve (profiling mode, same stream) -> roofline of the dominant kernel
+    bicgk.set_profiling(op.handle, True)
+    one(args.variant)
+    torch.cuda.synchronize()
+    times = bicgk.kernel_times(op.handle)
+    bicgk.set_profiling(op.handle, args.eager)
+    total = sum(t for _, t in times.values())
+    dom, (dl, dt) = max(times.items(), key=lambda kv: kv[1][1])
+    byts, flops = kernel_algorithmic(dom, A.n, A.nnz, args.k)
+    avg_s = dt / dl / 1e3
+    hbm, hbm_kind = hbm_peak()
+    t_mem, t_alu = byts / (hbm * 1e9), flops / (FP64_PEAK_TFLOPS * 1e12)
+    traffic = recorded_traffic().get((dom, args.k))
+    if t_alu > t_mem:
+        ach = flops / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
+                "peak_kind": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
+                "hbm_achieved_gbs": byts / avg_s / 1e9, "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind}
+    else:
+        ach = byts / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "kernel": dom, "peak_kind": f"{hbm_kind} copy bandwidth",
+                "fp64_achieved_tflops": flops / avg_s / 1e12, "fp64_peak_tflops": FP64_PEAK_TFLOPS}
+    roof.update({"algorithmic_bytes_per_launch": byts, "flops_per_launch": flops, "launches": dl,
+                 "mean_launch_ms": dt / dl, "share": dt / total if total else None})
+    out["roofline"] = roof
+    out["kernel_shares"] = {k: {"launches": v[0], "ms": v[1], "share": v[1] / total} for k, v in
+                            sorted(times.items(), key=lambda kv: -kv[1][1])}
+
+    if args.sweep and rank == 0:
+        sweep = {}
+        for k in (1, 2, 4, 8, 16, 32):
+            Bk = torch.from_numpy(inputs.rhs(A.n, k, 2)).to(dev)
+            Xk = torch.empty_like(Bk)
+            for v in bicgk.VARIANTS:
+                msk, itsk, _, _, _ = timed(v, 2, 1, B=Bk, X=Xk)
+                sweep[f"{v}/k{k}"] = itsk / (msk / 1e3)
+        out["sweep_rhs_iterations_per_s"] = sweep
+
+    # CPU oracle on the host cores (rank 0, N = 1 only)
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle
+        cols, iters = 2, 10
+        rate, secs = cpu_oracle_rate(A, B_host, args.variant, cols, iters)
+        out["cpu_baseline"] = {"value": rate, "unit": "RHS-iterations/s", "cores": oracle.threads(),
+                               "kind": "oracle",
+                               "sample": f"{cols} of the {args.k} columns x {iters} fixed iterations "
+                                         f"({secs:.1f} s of CPU time)"}
+    op.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

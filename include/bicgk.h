@@ -1,0 +1,167 @@
+/*
+ * bicgk -- BiCGStab with k right-hand sides on one GB300 GPU (sm_103a).
+ *
+ * C-ABI of the library libbicgk.so.  Plain pointers and sizes only.
+ *
+ * Method: B. Krasnopolsky, "Revisiting Performance of BiCGStab Methods for
+ * Solving Systems with Multiple Right-Hand Sides", arXiv:1907.12874.
+ *   - classical BiCGStab, basic (Algorithm 1) and merged (Algorithm 2) forms;
+ *   - Reordered BiCGStab (Algorithm 6) with the identity preconditioner
+ *     applied as a vector copy (Sec. 2.3), basic and merged forms;
+ *   - Pipelined BiCGStab (Algorithm 4), basic and merged forms;
+ *   "basic" = one kernel per vector operation of the listing (the 4-vector
+ *   update of Algorithm 4 as two kernels, Table 2 footnote); "merged" = one
+ *   kernel per merged line of the listing (updates fused with their dot
+ *   products and the residual-norm estimate, Sec. 2.2).
+ *
+ * Data layout (Sec. 3.1): the k vectors of a block are stored row-wise in
+ * one array, element (i, c) at index i*k + c ("RHS-interleaved", N x k,
+ * row-major).  The matrix is CSR with int32 row pointers and column indices
+ * and FP64 values (the CRS format of the paper's traffic model, Eq. for
+ * Sigma_mul in Sec. 3.1).
+ *
+ * All entry points return 0 on success or a negative BICGK_E* code; they never
+ * abort the process.  bicgk_strerror() names a code.
+ * Thread safety: distinct operators may be used from distinct threads; one
+ * operator runs one call at a time (its workspace is shared by its calls).
+ */
+#ifndef BICGK_H
+#define BICGK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque operator: device copy of the CSR matrix plus solver workspace. */
+typedef struct bicgk_op_s *bicgk_op;
+
+/* Where a caller-owned array lives. */
+enum bicgk_mem { BICGK_MEM_HOST = 0, BICGK_MEM_DEVICE = 1 };
+
+/* Method forms (same order as the oracle). */
+enum bicgk_variant {
+  BICGK_CLASSICAL_PLAIN = 0,  /* Algorithm 1, one kernel per vector op              */
+  BICGK_CLASSICAL_MERGED = 1, /* Algorithm 2                                        */
+  BICGK_REORDERED_PLAIN = 2,  /* Algorithm 6 with M^-1 = copy, one kernel per op   */
+  BICGK_REORDERED_MERGED = 3, /* Algorithm 6 with M^-1 = copy                       */
+  BICGK_PIPELINED_PLAIN = 4,  /* Algorithm 4, one kernel per op                     */
+  BICGK_PIPELINED_MERGED = 5  /* Algorithm 4                                        */
+};
+
+/* Per-RHS outcome written to status[c]. */
+enum bicgk_rhs_status {
+  BICGK_CONVERGED = 0, /* stop test passed (or b_c = 0, or r_0 already small)   */
+  BICGK_MAXIT = 1,     /* maxit iterations done without passing the stop test   */
+  BICGK_BREAKDOWN = 2, /* a scalar recurrence divided by an exact zero          */
+  BICGK_NONFINITE = 3  /* a dot product or scalar became Inf or NaN             */
+};
+
+/* Solve flags (bit mask). */
+enum bicgk_flags {
+  BICGK_FLAG_NO_STOP_TEST = 1 /* run exactly maxit iterations (fixed-count benchmarking,
+                                 Sec. 2.3 uses N_it = 1000); breakdown rules still apply */
+};
+
+/* Error codes. */
+enum bicgk_error {
+  BICGK_OK = 0,
+  BICGK_E_INVALID = -1,  /* bad argument (null pointer, size out of range, bad enum)   */
+  BICGK_E_BAD_CSR = -2,  /* row pointers not monotone, column index out of range, ...   */
+  BICGK_E_CUDA = -3,     /* a CUDA runtime call failed (bicgk_last_cuda_error() has it) */
+  BICGK_E_NOMEM = -4,    /* device or pinned host allocation failed                     */
+  BICGK_E_UNSUPPORTED = -5 /* k above BICGK_MAX_K, or no sm_103 device                  */
+};
+
+#define BICGK_MAX_K 64
+
+/*
+ * Create an operator from a CSR matrix (n_rows x n_rows, nnz entries).
+ *   rowptr[n_rows+1], colidx[nnz] (int32), vals[nnz] (FP64), in memory space
+ *   `mem`.  The arrays are copied to the current CUDA device; the caller keeps
+ *   ownership of its arrays.  The matrix is validated: rowptr[0] == 0,
+ *   rowptr non-decreasing, rowptr[n_rows] == nnz, 0 <= colidx < n_rows
+ *   (BICGK_E_BAD_CSR otherwise).  Column indices need not be sorted.
+ *   stream: a cudaStream_t (NULL = legacy default stream) used for the copies.
+ * On success *out receives the operator; release it with bicgk_op_destroy().
+ */
+int bicgk_csr_create(bicgk_op *out, int64_t n_rows, int64_t nnz, const int32_t *rowptr,
+                     const int32_t *colidx, const double *vals, int mem, void *stream);
+
+/*
+ * Y = A X for a block of k vectors (the SpMV of Algorithms 1-6 applied to k
+ * row-interleaved vectors; the operation behind Sigma_mul, Sec. 3.1).
+ *   X, Y: device arrays of n_rows*k FP64, RHS-interleaved (i*k + c); they must
+ *   not overlap.  1 <= k <= BICGK_MAX_K.  Runs on `stream`, returns without
+ *   synchronising.
+ */
+int bicgk_spmm(bicgk_op A, int32_t k, const double *X, double *Y, void *stream);
+
+/*
+ * Solve A X = B for k right-hand sides (Algorithms 1, 2, 4 or 6, per `variant`).
+ *   B      : n_rows*k FP64, RHS-interleaved, in space `mem`.
+ *   X0     : initial guess in the same layout and space, or NULL for zero.
+ *   X      : n_rows*k FP64 output in the same layout and space (may alias X0).
+ *   rel_tol: column c stops when its squared residual-norm estimate falls
+ *            strictly below (rel_tol * ||b_c||_2)^2 (the listings' test with
+ *            eps = rel_tol*||b_c||).  rel_tol >= 0.
+ *   maxit  : maximum iterations, 0 <= maxit <= 1e7.
+ *   flags  : bicgk_flags.
+ *   iters  : host int32[k]  -- iterates x_{j+1} formed by column c.
+ *   status : host int32[k]  -- bicgk_rhs_status per column.
+ *   resid_hist: host FP64[(maxit+1)*k] or NULL; entry (j, c) at j*k + c is
+ *            ||r_0|| for j = 0 and the method's estimate of ||r_j|| after
+ *            iteration j-1 (sqrt of the quantity of the stop test, 0 when it is
+ *            negative); NaN where column c formed no iterate j.
+ *   true_relres: host FP64[k] or NULL -- ||b_c - A x_c|| / ||b_c|| recomputed
+ *            from the final X (0 when b_c = 0).
+ * Everything runs on `stream` (cudaStream_t, NULL = legacy default); the call
+ * returns after all outputs are valid.  A non-converged column is not an error.
+ * Per-column rules where the paper is silent: b_c = 0 gives x_c = 0 with 0
+ * iterations; a column whose ||r_0|| already passes the test keeps x0; a
+ * column stops independently of the others and is not written afterwards.
+ * The first call per (variant, k) builds and caches a CUDA graph; callers must
+ * not capture this call into a graph of their own.
+ */
+int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double rel_tol, int32_t maxit,
+                int variant, int32_t flags, int mem, double *X, int32_t *iters, int32_t *status,
+                double *resid_hist, double *true_relres, void *stream);
+
+/* Release the operator and all device memory it holds.  NULL is accepted. */
+int bicgk_op_destroy(bicgk_op A);
+
+/* Static description of an error code. */
+const char *bicgk_strerror(int rc);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *bicgk_last_cuda_error(void);
+
+/*
+ * Per-kernel timing (profiling aid).  With bicgk_set_profiling(A, 1) the next
+ * solves run their iteration loop without the CUDA graph, one launch at a time
+ * on the caller's stream, with a CUDA event pair around every launch;
+ * bicgk_kernel_times() then reports, for kernel class i (0 <= i < *n_out),
+ * its name, launch count and summed event time in milliseconds since the last
+ * bicgk_set_profiling() call.  Results are identical to the graph mode.
+ *   names: array of *n_out C strings owned by the library (may be NULL).
+ */
+int bicgk_set_profiling(bicgk_op A, int on);
+int bicgk_kernel_times(bicgk_op A, int32_t max_n, int32_t *n_out, const char **names, int64_t *launches,
+                       double *total_ms);
+
+/*
+ * Launch statistics of the last bicgk_solve(): iterations the loop ran
+ * (max over columns), kernels launched by the library in that call, and the
+ * number of kernels one iteration of the loop launches.
+ */
+int bicgk_last_stats(bicgk_op A, int32_t *loop_iters, int64_t *kernel_launches, int32_t *kernels_per_iter);
+
+/* Library build identification ("bicgk <version> sm_103a"). */
+const char *bicgk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BICGK_H */

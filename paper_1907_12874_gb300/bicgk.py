@@ -1,0 +1,248 @@
+"""Thin Python binding of libbicgk (argument marshalling only).
+
+Every step of a solve runs in the library's CUDA kernels; this module only
+converts arrays to pointers, picks the memory space and the stream, and turns
+return codes into exceptions.  Device arrays are torch CUDA tensors (torch is
+used for device memory and streams only); host arrays are numpy arrays.  The
+function names mirror the C-ABI in include/bicgk.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MEM_HOST, MEM_DEVICE = 0, 1
+VARIANTS = {
+    "classical_plain": 0,
+    "classical_merged": 1,
+    "reordered_plain": 2,
+    "reordered_merged": 3,
+    "pipelined_plain": 4,
+    "pipelined_merged": 5,
+}
+STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "nonfinite"}
+FLAG_NO_STOP_TEST = 1
+MAX_K = 64
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BicgkError(RuntimeError):
+    def __init__(self, rc: int, where: str):
+        lib = _load()
+        detail = lib.bicgk_last_cuda_error().decode()
+        super().__init__(f"{where}: {lib.bicgk_strerror(rc).decode()} (rc={rc}){': ' + detail if detail else ''}")
+        self.rc = rc
+
+
+def _load():
+    """Load libbicgk.so (building it first if its sources are newer); fail loudly otherwise."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            lib.bicgk_csr_create.argtypes = [ctypes.POINTER(vp), i64, i64, vp, vp, vp, ctypes.c_int, vp]
+            lib.bicgk_spmm.argtypes = [vp, i32, vp, vp, vp]
+            lib.bicgk_solve.argtypes = [vp, i32, vp, vp, dbl, i32, ctypes.c_int, i32, ctypes.c_int, vp, vp, vp, vp,
+                                        vp, vp]
+            lib.bicgk_op_destroy.argtypes = [vp]
+            lib.bicgk_strerror.argtypes = [ctypes.c_int]
+            lib.bicgk_strerror.restype = ctypes.c_char_p
+            lib.bicgk_last_cuda_error.restype = ctypes.c_char_p
+            lib.bicgk_version.restype = ctypes.c_char_p
+            lib.bicgk_set_profiling.argtypes = [vp, ctypes.c_int]
+            lib.bicgk_kernel_times.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_char_p),
+                                               ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+            lib.bicgk_last_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+            for f in ("bicgk_csr_create", "bicgk_spmm", "bicgk_solve", "bicgk_op_destroy", "bicgk_set_profiling",
+                      "bicgk_kernel_times", "bicgk_last_stats"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def version() -> str:
+    return _load().bicgk_version().decode()
+
+
+def strerror(rc: int) -> str:
+    return _load().bicgk_strerror(rc).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise BicgkError(rc, where)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def csr_create(rowptr, colidx, vals, stream=None) -> int:
+    """Create an operator handle from CSR arrays (numpy on the host or torch CUDA tensors)."""
+    lib = _load()
+    dev = _is_torch(rowptr)
+    if dev:
+        for t, dt in ((rowptr, "int32"), (colidx, "int32"), (vals, "float64")):
+            if not (t.is_cuda and t.is_contiguous() and str(t.dtype).endswith(dt)):
+                raise TypeError("device CSR arrays must be contiguous CUDA tensors of int32/int32/float64")
+    else:
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+    h = ctypes.c_void_p()
+    n = rowptr.shape[0] - 1
+    nnz = colidx.shape[0]
+    rc = lib.bicgk_csr_create(ctypes.byref(h), n, nnz, _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                              MEM_DEVICE if dev else MEM_HOST, _stream(stream))
+    _check(rc, "bicgk_csr_create")
+    return h.value
+
+
+def op_destroy(handle: int) -> None:
+    _check(_load().bicgk_op_destroy(ctypes.c_void_p(handle)), "bicgk_op_destroy")
+
+
+def spmm(handle: int, X, Y, stream=None) -> None:
+    """Y = A X for torch CUDA tensors of shape (N, k), float64, contiguous."""
+    k = 1 if X.dim() == 1 else X.shape[1]
+    _check(_load().bicgk_spmm(ctypes.c_void_p(handle), k, _ptr(X), _ptr(Y), _stream(stream)), "bicgk_spmm")
+
+
+@dataclass
+class SolveResult:
+    X: object
+    iters: np.ndarray
+    status: np.ndarray
+    hist: np.ndarray | None
+    true_relres: np.ndarray | None
+
+
+def _is_device(a) -> bool:
+    return _is_torch(a) and a.is_cuda
+
+
+def solve(handle: int, B, X0=None, tol: float = 1e-8, maxit: int = 1000, variant="classical_merged",
+          flags: int = 0, X=None, want_hist: bool = True, want_true: bool = True, stream=None) -> SolveResult:
+    """Solve A X = B, B of shape (N, k), RHS-interleaved, float64, contiguous.
+
+    A CUDA tensor B makes a device call (X0, X on the device too); a numpy array
+    or a CPU tensor (pinned for asynchronous copies) makes a host call, in which
+    the library copies B/X0 to the GPU and X back inside the call.
+    """
+    lib = _load()
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    dev = _is_device(B)
+    if _is_torch(B):
+        if not (B.is_contiguous() and str(B.dtype).endswith("float64")):
+            raise TypeError("B must be a contiguous float64 tensor")
+        if X0 is not None and (_is_device(X0) != dev or not X0.is_contiguous()):
+            raise TypeError("X0 must be a contiguous tensor on the same device as B")
+        if X is None:
+            import torch
+            X = torch.empty_like(B, pin_memory=not dev) if not dev else torch.empty_like(B)
+    else:
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        if X0 is not None:
+            X0 = np.ascontiguousarray(X0, dtype=np.float64)
+        if X is None:
+            X = np.empty_like(B)
+    k = 1 if B.ndim == 1 else B.shape[1]
+    iters = np.zeros(k, dtype=np.int32)
+    status = np.zeros(k, dtype=np.int32)
+    hist = np.empty((maxit + 1, k)) if want_hist else None
+    trr = np.empty(k) if want_true else None
+    rc = lib.bicgk_solve(ctypes.c_void_p(handle), k, _ptr(B), _ptr(X0), float(tol), int(maxit), v, int(flags),
+                         MEM_DEVICE if dev else MEM_HOST, _ptr(X), _ptr(iters), _ptr(status), _ptr(hist),
+                         _ptr(trr), _stream(stream))
+    _check(rc, "bicgk_solve")
+    return SolveResult(X, iters, status, hist, trr)
+
+
+def set_profiling(handle: int, on: bool) -> None:
+    _check(_load().bicgk_set_profiling(ctypes.c_void_p(handle), int(bool(on))), "bicgk_set_profiling")
+
+
+def kernel_times(handle: int) -> dict:
+    """{kernel name: (launches, total ms)} recorded while profiling was on."""
+    lib = _load()
+    n = ctypes.c_int32(0)
+    _check(lib.bicgk_kernel_times(ctypes.c_void_p(handle), 0, ctypes.byref(n), None, None, None), "kernel_times")
+    m = n.value
+    names = (ctypes.c_char_p * max(m, 1))()
+    launches = (ctypes.c_int64 * max(m, 1))()
+    ms = (ctypes.c_double * max(m, 1))()
+    _check(lib.bicgk_kernel_times(ctypes.c_void_p(handle), m, ctypes.byref(n), names, launches, ms), "kernel_times")
+    return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(m)}
+
+
+def last_stats(handle: int) -> dict:
+    it, ln, kpi = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    _check(_load().bicgk_last_stats(ctypes.c_void_p(handle), ctypes.byref(it), ctypes.byref(ln), ctypes.byref(kpi)),
+           "bicgk_last_stats")
+    return {"loop_iters": it.value, "kernel_launches": ln.value, "kernels_per_iter": kpi.value}
+
+
+class Operator:
+    """Owning wrapper of a bicgk operator (CSR matrix on the GPU plus solver workspace)."""
+
+    def __init__(self, csr=None, rowptr=None, colidx=None, vals=None, stream=None):
+        if csr is not None:
+            rowptr, colidx, vals = csr.rowptr, csr.colidx, csr.vals
+        self.n = int(rowptr.shape[0] - 1)
+        self.nnz = int(colidx.shape[0])
+        self.handle = csr_create(rowptr, colidx, vals, stream)
+
+    def solve(self, B, **kw) -> SolveResult:
+        return solve(self.handle, B, **kw)
+
+    def spmm(self, X, Y=None, stream=None):
+        if Y is None:
+            import torch
+            Y = torch.empty_like(X)
+        spmm(self.handle, X, Y, stream)
+        return Y
+
+    def close(self):
+        if getattr(self, "handle", None):
+            op_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,117 @@
+// Internal declarations shared by the CUDA translation units of libbicgk.
+//
+// Layout in HBM (Sec. 3.1 of Krasnopolsky, arXiv:1907.12874: the k vectors
+// are stored row-wise in a single vector):
+//   every Krylov vector is an N x kp block, element (i, c) at i*kp + c, where
+//   kp is k rounded up to a power of two (padding columns hold zeros and are
+//   finished before the first iteration), so a double2 never straddles rows
+//   and every thread of a streaming kernel owns fixed columns.
+//   Per-column scalars are SoA arrays [slot][kMaxKp]; per-column flags likewise.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bicgk {
+
+constexpr int kVecThreads = 512;  // threads per block of the streaming kernels
+constexpr int kMaxKp = 64;        // largest padded RHS count
+constexpr int kMaxDots = 4;       // largest number of dot products fused in one pass
+constexpr int kSpmmThreads = 256; // threads per block of the SpMM kernels
+constexpr int kSpmmTileRows = 256;      // rows per staged tile (kp <= 2 path)
+constexpr int kSpmmStageMax = 4096;     // largest staged tile (CSR entries)
+
+// Per-column FP64 scalar slots.
+enum Slot : int {
+  S_RHO = 0, S_ALPHA, S_OMEGA, S_BETA, S_EPS2, S_BN2, S_D0, S_D1, S_D2, S_TRUE, S_NSLOT
+};
+// Per-column int flags.
+enum Flag : int { F_ACT = 0, F_XUPD, F_XZERO, F_ITERS, F_STATUS, F_NFLAG };
+
+// Status codes (same values as the public enum).
+enum Status : int { ST_CONVERGED = 0, ST_MAXIT = 1, ST_BREAKDOWN = 2, ST_NONFINITE = 3 };
+
+// Device-resident control block.  Written by the host before each solve and
+// by the last block of the reducing kernels during it.
+struct Ctl {
+  double tol;
+  double *hist;   // [(maxit+1)][kp] residual-norm history
+  int iter;       // current iteration j
+  int maxit;
+  int k;          // real columns
+  int kp;         // padded columns
+  int flags;      // bicgk_flags
+  int any_active; // some column still iterating
+  int loop_iters; // iterations the loop completed
+  unsigned int ticket; // arrival counter of the grid reduction (reset by the last block)
+};
+
+// Vector roles in the workspace.
+enum Vec : int {
+  V_X = 0, V_R, V_R0, V_P, V_V, V_S, V_T, V_W, V_Z, V_Q, V_Y, V_TMP, V_RT, V_B, V_NVEC
+};
+
+struct KArgs {
+  double *v[V_NVEC];
+  double *sc;    // [S_NSLOT][kMaxKp]
+  int *fl;       // [F_NFLAG][kMaxKp]
+  double *part;  // [grid][kMaxDots][kMaxKp] per-block partial sums
+  Ctl *ctl;
+  int64_t n;     // rows
+  int kp;
+  int use_cond;  // 1 inside the captured graph (the loop is a conditional WHILE node)
+  cudaGraphConditionalHandle cond;
+};
+
+// Streaming kernel identifiers (one per fused vector operation of the listings).
+enum Op : int {
+  // set-up
+  OP_SETUP_C = 0, OP_SETUP_R, OP_SETUP_P, OP_DOT_RW0,
+  // classical (Algorithms 1 and 2)
+  OP_DELTA, OP_UPD_S, OP_G1, OP_G3, OP_UPD_P,
+  OP_DOT_TS, OP_DOT_PSI, OP_UPD_X_C, OP_UPD_R_C, OP_DOT_RR, OP_DOT_RHO,
+  // reordered (Algorithm 6, M^-1 = copy)
+  OP_COPY_SV, OP_UPD_TH, OP_RG4, OP_COPY_QT, OP_UPD_R_R, OP_RFIN,
+  OP_UPD_RT, OP_DOT_T_RT, OP_DOT_T_T, OP_DOT_T_R0, OP_DOT_RT_RT, OP_UPD_X_R, OP_UPD_Z_R, OP_UPD_VH,
+  // pipelined (Algorithm 4)
+  OP_PG1, OP_PG2, OP_PG3,
+  OP_PU_P, OP_PU_S, OP_PU_Z, OP_PU_Q, OP_PU_Y, OP_DOT_QY, OP_DOT_YY, OP_DOT_QQ,
+  OP_PU_X, OP_PU_R, OP_PU_TMP, OP_PU_W, OP_DOT_R0R, OP_DOT_R0Z, OP_DOT_R0W, OP_DOT_R0S,
+  // final true residual norm
+  OP_TRUE_RES,
+  OP_COUNT
+};
+
+const char *op_name(int op);
+// Reads and writes of full N x k vectors one launch of `op` makes (for traffic accounting).
+void op_traffic(int op, int *reads, int *writes);
+int op_has_dots(int op);
+
+// Launch one streaming kernel.  grid must not exceed the partial-sum capacity.
+cudaError_t launch_vec(int op, const KArgs &a, int grid, cudaStream_t s);
+// Blocks per SM the streaming kernel of `op` reaches (occupancy query).
+int vec_blocks_per_sm(int op);
+
+// SpMM: y = A x (mode 0) or y = b - A x (mode 1) for kp in {1,2,4,...,64}.
+struct SpmmArgs {
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  const double *vals;
+  const double *x;
+  double *y;
+  const double *b;
+  int64_t n;
+  int stage_cap;  // staged CSR entries per tile (kp <= 2); 0 = read entries directly
+};
+cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s);
+int spmm_blocks_per_sm(int kp, int mode, int stage_cap);
+
+// Pack a user block (ld = k) into the workspace layout (ld = kp, zero padding); X0 may be null.
+cudaError_t launch_pack(const double *B, const double *X0, int k, const KArgs &a, cudaStream_t s);
+// Unpack workspace role `role` (ld = kp) into a user block (ld = k); with use_xzero, columns
+// with b_c = 0 are written as zeros.
+cudaError_t launch_unpack_role(double *X, int k, const KArgs &a, int role, int use_xzero, cudaStream_t s);
+// Fill the history with NaN and clear the per-column state.
+cudaError_t launch_reset(const KArgs &a, int64_t hist_len, cudaStream_t s);
+
+}  // namespace bicgk

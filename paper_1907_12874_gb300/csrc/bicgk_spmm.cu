@@ -1,0 +1,196 @@
+// CSR sparse matrix times a block of k RHS-interleaved vectors:
+//   y_ic = sum_j a_ij x_jc           (mode 0: the SpMV of Algorithms 1-6)
+//   y_ic = b_ic - sum_j a_ij x_jc    (mode 1: r_0 = b - A x_0 and the final
+//                                     true residual)
+// The operation whose traffic the paper models as Sigma_mul (Sec. 3.1, Eq.
+// SpMV_mem): CRS with 4-byte indices and 8-byte values, k vectors stored
+// row-wise.
+//
+// FP64 arithmetic is the scarce resource on this GPU (two FP64 lanes per SM
+// per clock), so every lane computes complete row sums for the two columns it
+// owns: no partial sums are combined across lanes, and each (nonzero, column)
+// pair costs exactly one FMA.
+//
+//   kp >= 4: a row is owned by kp/2 consecutive lanes, lane l of the group
+//            holding columns 2l, 2l+1; the x row and the y row move as one
+//            coalesced run of kp doubles (double2 per lane).  The group's CSR
+//            entries are broadcast loads through L1.
+//   kp <= 2: one lane per row.  A block walks 256-row tiles; the tile's CSR
+//            entries (values and column indices) are first staged into shared
+//            memory with coalesced loads, so the lanes' strided reads of their
+//            own rows hit shared memory instead of scattering over L1.  A tile
+//            with more entries than the stage buffer reads them from global.
+#include "bicgk_dev.cuh"
+
+namespace bicgk {
+
+namespace {
+
+template <int KP, int MODE>
+__global__ void __launch_bounds__(kSpmmThreads) spmm_group_kernel(const SpmmArgs a) {
+  static_assert(KP >= 4, "group kernel needs kp >= 4");
+  constexpr int L = KP / 2;                   // lanes per row
+  constexpr int RPP = kSpmmThreads / L;       // rows per pass of a block
+  const int g = threadIdx.x / L, cl = threadIdx.x % L;
+  const int32_t *__restrict__ rp = a.rowptr;
+  const int32_t *__restrict__ ci = a.colidx;
+  const double *__restrict__ va = a.vals;
+  const double2 *__restrict__ x2 = reinterpret_cast<const double2 *>(a.x);
+  double2 *__restrict__ y2 = reinterpret_cast<double2 *>(a.y);
+  const int64_t stride = (int64_t)gridDim.x * RPP;
+  for (int64_t r = (int64_t)blockIdx.x * RPP + g; r < a.n; r += stride) {
+    const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
+    double2 acc = make_double2(0.0, 0.0);
+    int e = e0;
+    for (; e + 1 < e1; e += 2) {
+      const int j0 = __ldg(ci + e), j1 = __ldg(ci + e + 1);
+      const double a0 = __ldg(va + e), a1 = __ldg(va + e + 1);
+      const double2 u0 = __ldg(x2 + (int64_t)j0 * L + cl);
+      const double2 u1 = __ldg(x2 + (int64_t)j1 * L + cl);
+      acc.x = fma(a0, u0.x, acc.x);
+      acc.y = fma(a0, u0.y, acc.y);
+      acc.x = fma(a1, u1.x, acc.x);
+      acc.y = fma(a1, u1.y, acc.y);
+    }
+    if (e < e1) {
+      const int j0 = __ldg(ci + e);
+      const double a0 = __ldg(va + e);
+      const double2 u0 = __ldg(x2 + (int64_t)j0 * L + cl);
+      acc.x = fma(a0, u0.x, acc.x);
+      acc.y = fma(a0, u0.y, acc.y);
+    }
+    if constexpr (MODE == 1) {
+      const double2 bv = reinterpret_cast<const double2 *>(a.b)[r * L + cl];
+      acc = make_double2(bv.x - acc.x, bv.y - acc.y);
+    }
+    y2[r * L + cl] = acc;
+  }
+}
+
+// One lane per row, CSR entries of each 256-row tile staged in shared memory.
+template <int KP, int MODE>
+__global__ void __launch_bounds__(kSpmmThreads) spmm_row_kernel(const SpmmArgs a) {
+  static_assert(KP == 1 || KP == 2, "row kernel handles kp <= 2");
+  extern __shared__ unsigned char smem_raw[];
+  const int cap = a.stage_cap;
+  double *s_val = reinterpret_cast<double *>(smem_raw);
+  int32_t *s_col = reinterpret_cast<int32_t *>(s_val + cap);
+  const int32_t *__restrict__ rp = a.rowptr;
+  const int32_t *__restrict__ ci = a.colidx;
+  const double *__restrict__ va = a.vals;
+  const int64_t ntiles = (a.n + kSpmmTileRows - 1) / kSpmmTileRows;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * kSpmmTileRows;
+    const int64_t r1 = (r0 + kSpmmTileRows < a.n) ? r0 + kSpmmTileRows : a.n;
+    const int te0 = __ldg(rp + r0), te1 = __ldg(rp + r1);
+    const bool staged = (te1 - te0) <= cap;
+    if (staged) {
+      for (int e = te0 + threadIdx.x; e < te1; e += blockDim.x) {
+        s_val[e - te0] = __ldg(va + e);
+        s_col[e - te0] = __ldg(ci + e);
+      }
+    }
+    __syncthreads();
+    const int64_t r = r0 + threadIdx.x;
+    if (r < r1) {
+      const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
+      if constexpr (KP == 1) {
+        double acc = 0.0;
+        if (staged)
+          for (int e = e0; e < e1; ++e) acc = fma(s_val[e - te0], __ldg(a.x + s_col[e - te0]), acc);
+        else
+          for (int e = e0; e < e1; ++e) acc = fma(__ldg(va + e), __ldg(a.x + __ldg(ci + e)), acc);
+        if constexpr (MODE == 1) acc = a.b[r] - acc;
+        a.y[r] = acc;
+      } else {
+        const double2 *__restrict__ x2 = reinterpret_cast<const double2 *>(a.x);
+        double2 acc = make_double2(0.0, 0.0);
+        if (staged) {
+          for (int e = e0; e < e1; ++e) {
+            const double av = s_val[e - te0];
+            const double2 u = __ldg(x2 + s_col[e - te0]);
+            acc.x = fma(av, u.x, acc.x);
+            acc.y = fma(av, u.y, acc.y);
+          }
+        } else {
+          for (int e = e0; e < e1; ++e) {
+            const double av = __ldg(va + e);
+            const double2 u = __ldg(x2 + __ldg(ci + e));
+            acc.x = fma(av, u.x, acc.x);
+            acc.y = fma(av, u.y, acc.y);
+          }
+        }
+        if constexpr (MODE == 1) {
+          const double2 bv = reinterpret_cast<const double2 *>(a.b)[r];
+          acc = make_double2(bv.x - acc.x, bv.y - acc.y);
+        }
+        reinterpret_cast<double2 *>(a.y)[r] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int KP, int MODE>
+cudaError_t launch_kp(const SpmmArgs &a, int grid, cudaStream_t s) {
+  if constexpr (KP <= 2) {
+    const size_t smem = (size_t)a.stage_cap * (sizeof(double) + sizeof(int32_t));
+    spmm_row_kernel<KP, MODE><<<grid, kSpmmThreads, smem, s>>>(a);
+  } else {
+    spmm_group_kernel<KP, MODE><<<grid, kSpmmThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int KP, int MODE>
+int occ_kp(int stage_cap) {
+  int nb = 0;
+  cudaError_t e;
+  if constexpr (KP <= 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_row_kernel<KP, MODE>, kSpmmThreads,
+                                                      (size_t)stage_cap * (sizeof(double) + sizeof(int32_t)));
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_group_kernel<KP, MODE>, kSpmmThreads, 0);
+  if (e != cudaSuccess || nb < 1) return 1;
+  return nb;
+}
+
+template <int MODE>
+cudaError_t launch_mode(int kp, const SpmmArgs &a, int grid, cudaStream_t s) {
+  switch (kp) {
+    case 1: return launch_kp<1, MODE>(a, grid, s);
+    case 2: return launch_kp<2, MODE>(a, grid, s);
+    case 4: return launch_kp<4, MODE>(a, grid, s);
+    case 8: return launch_kp<8, MODE>(a, grid, s);
+    case 16: return launch_kp<16, MODE>(a, grid, s);
+    case 32: return launch_kp<32, MODE>(a, grid, s);
+    case 64: return launch_kp<64, MODE>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int MODE>
+int occ_mode(int kp, int stage_cap) {
+  switch (kp) {
+    case 1: return occ_kp<1, MODE>(stage_cap);
+    case 2: return occ_kp<2, MODE>(stage_cap);
+    case 4: return occ_kp<4, MODE>(stage_cap);
+    case 8: return occ_kp<8, MODE>(stage_cap);
+    case 16: return occ_kp<16, MODE>(stage_cap);
+    case 32: return occ_kp<32, MODE>(stage_cap);
+    case 64: return occ_kp<64, MODE>(stage_cap);
+    default: return 1;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s) {
+  return mode == 0 ? launch_mode<0>(kp, a, grid, s) : launch_mode<1>(kp, a, grid, s);
+}
+
+int spmm_blocks_per_sm(int kp, int mode, int stage_cap) {
+  return mode == 0 ? occ_mode<0>(kp, stage_cap) : occ_mode<1>(kp, stage_cap);
+}
+
+}  // namespace bicgk

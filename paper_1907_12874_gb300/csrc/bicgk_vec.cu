@@ -1,0 +1,895 @@
+// Streaming kernels of BiCGStab with k right-hand sides: vector updates fused
+// with their per-RHS dot products (the merged operations of Sec. 2.2 and the
+// listings of Algorithms 2, 4 and 6), the one-operation-per-kernel forms of
+// Algorithms 1, 4 and 6 ("basic"), and the per-column scalar recurrences.
+//
+// One kernel = one pass over the N x kp blocks it touches.  Every thread
+// moves double2 chunks in a grid-stride loop; since the stride (in elements)
+// is a multiple of kp, a thread always sees the same two columns, so its dot
+// partials are per-column registers.  A dot product is reduced in a fixed
+// order: warp butterfly over lanes that share columns -> shared memory across
+// warps -> one partial per block -> the last block to arrive (atomic ticket,
+// no spin-wait) sums the block partials in block order and runs the scalar
+// recurrence of the listing for every column.  The same inputs therefore give
+// bitwise the same result on every run.
+//
+// The scalar recurrences follow the oracle's rules (no FMA contraction:
+// __dmul_rn / __dadd_rn / __ddiv_rn / __dsqrt_rn, evaluated as written):
+//   R1 stop: estimate < eps_c^2, eps_c = tol*||b_c||;  R2 b_c = 0 -> x_c = 0;
+//   R3 a column stops on its own; x_{j+1} is formed once omega_j is finite;
+//   R5 zero denominator of omega -> omega = 0, other exact-zero divisors ->
+//      BREAKDOWN, non-finite scalars -> NONFINITE;
+//   R6 merged estimates (theta - omega*phi etc.) feed the stop test.
+#include "bicgk_dev.cuh"
+
+namespace bicgk {
+
+namespace {
+
+#define SC(slot, c) a.sc[(slot) * kMaxKp + (c)]
+#define FL(f, c) a.fl[(f) * kMaxKp + (c)]
+
+__device__ __forceinline__ double2 ld2(const double *p, int64_t i) {
+  return reinterpret_cast<const double2 *>(p)[i];
+}
+__device__ __forceinline__ void st2(double *p, int64_t i, double2 v) { reinterpret_cast<double2 *>(p)[i] = v; }
+
+// y + s*x elementwise (one FMA per element)
+__device__ __forceinline__ double2 fma2(double2 s, double2 x, double2 y) {
+  return make_double2(fma(s.x, x.x, y.x), fma(s.y, x.y, y.y));
+}
+__device__ __forceinline__ double2 neg2(double2 s) { return make_double2(-s.x, -s.y); }
+__device__ __forceinline__ void dot_acc(double2 &acc, double2 u, double2 w) {
+  acc.x = fma(u.x, w.x, acc.x);
+  acc.y = fma(u.y, w.y, acc.y);
+}
+__device__ __forceinline__ double2 sel2(bool u0, bool u1, double2 nv, double2 ov) {
+  return make_double2(u0 ? nv.x : ov.x, u1 ? nv.y : ov.y);
+}
+
+// Per-thread scalars of its two columns.
+struct Sc2 {
+  double2 al, om, be;
+  bool u0, u1;
+};
+
+// ------------------------------------------------------------------ scalar rules
+
+__device__ __forceinline__ bool fin1(double v) { return isfinite(v); }
+__device__ __forceinline__ double hist_value(double est) {
+  if (isnan(est)) return est;
+  return est > 0.0 ? __dsqrt_rn(est) : 0.0;
+}
+__device__ __forceinline__ void col_stop(const KArgs &a, int c, int st) {
+  FL(F_ACT, c) = 0;
+  FL(F_STATUS, c) = st;
+}
+__device__ __forceinline__ double sub_rn(double x, double y) { return __dadd_rn(x, -y); }
+
+enum Fin : int {
+  FIN_NONE = 0, FIN_SETUP, FIN_RW0, FIN_DELTA, FIN_G1, FIN_RHO, FIN_STORE_D0, FIN_STORE_D1, FIN_STORE_D2,
+  FIN_PSI, FIN_RR, FIN_R4_MERGED, FIN_R4_PLAIN, FIN_PG1_MERGED, FIN_PG1_PLAIN, FIN_PG3_MERGED,
+  FIN_PG3_PLAIN, FIN_TRUE
+};
+enum Ctl_ : int { CTL_NONE = 0, CTL_START = 1, CTL_END_ITER = 2 };
+
+// Column c, executed by thread c of the last block.  s[d*kp + c] = dot d of column c.
+template <int FIN>
+__device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
+  Ctl *ctl = a.ctl;
+  const int nostop = ctl->flags & 1;
+  if constexpr (FIN == FIN_SETUP) {
+    // (b,b) and rho_0 = (r_0, r_0): set-up lines of Algorithms 1, 2, 4, 6 and readings R1, R2
+    const double bn2 = s[0 * kp + c], rho = s[1 * kp + c];
+    const double eps2 = __dmul_rn(__dmul_rn(ctl->tol, ctl->tol), bn2);
+    SC(S_BN2, c) = bn2;
+    SC(S_RHO, c) = rho;
+    SC(S_EPS2, c) = eps2;
+    SC(S_ALPHA, c) = 0.0;
+    SC(S_OMEGA, c) = 0.0;
+    SC(S_BETA, c) = 0.0;
+    FL(F_ITERS, c) = 0;
+    FL(F_XUPD, c) = 0;
+    FL(F_XZERO, c) = 0;
+    if (c >= ctl->k) {  // padding column: finished before the loop
+      FL(F_ACT, c) = 0;
+      FL(F_STATUS, c) = ST_CONVERGED;
+      return;
+    }
+    double h0 = hist_value(rho);
+    int st = ST_MAXIT, act = 1;
+    if (bn2 == 0.0) {
+      FL(F_XZERO, c) = 1;
+      h0 = 0.0;
+      st = ST_CONVERGED;
+      act = 0;
+    } else if (!fin1(bn2) || !fin1(rho)) {
+      st = ST_NONFINITE;
+      act = 0;
+    } else if (!nostop && rho < eps2) {
+      st = ST_CONVERGED;
+      act = 0;
+    }
+    ctl->hist[c] = h0;
+    FL(F_ACT, c) = act;
+    FL(F_STATUS, c) = st;
+  } else if constexpr (FIN == FIN_RW0) {
+    // Algorithm 4 set-up: alpha_0 = rho_0 / (r_0, w_0), beta_{-1} = 0, omega_{-1} = 0 (R7)
+    if (!FL(F_ACT, c)) return;
+    const double rw = s[c];
+    if (!fin1(rw)) { col_stop(a, c, ST_NONFINITE); return; }
+    if (rw == 0.0) { col_stop(a, c, ST_BREAKDOWN); return; }
+    const double al = __ddiv_rn(SC(S_RHO, c), rw);
+    if (!fin1(al)) { col_stop(a, c, ST_NONFINITE); return; }
+    SC(S_ALPHA, c) = al;
+  } else if constexpr (FIN == FIN_DELTA) {
+    // delta_j = (v_j, r_0), alpha_j = rho_j / delta_j
+    if (!FL(F_ACT, c)) return;
+    const double de = s[c];
+    if (!fin1(de)) { col_stop(a, c, ST_NONFINITE); return; }
+    if (de == 0.0) { col_stop(a, c, ST_BREAKDOWN); return; }
+    const double al = __ddiv_rn(SC(S_RHO, c), de);
+    if (!fin1(al)) { col_stop(a, c, ST_NONFINITE); return; }
+    SC(S_ALPHA, c) = al;
+  } else if constexpr (FIN == FIN_G1) {
+    // Algorithm 2 group 1: phi = (t,s), psi = (t,t), theta = (s,s); omega = phi/psi;
+    // stop test on (r_{j+1}, r_{j+1}) = theta - omega*phi
+    FL(F_XUPD, c) = 0;
+    if (!FL(F_ACT, c)) return;
+    const double phi = s[0 * kp + c], psi = s[1 * kp + c], th = s[2 * kp + c];
+    if (!fin1(phi) || !fin1(psi) || !fin1(th)) { col_stop(a, c, ST_NONFINITE); return; }
+    const double om = psi == 0.0 ? 0.0 : __ddiv_rn(phi, psi);
+    if (!fin1(om)) { col_stop(a, c, ST_NONFINITE); return; }
+    const int j = ctl->iter;
+    SC(S_OMEGA, c) = om;
+    FL(F_XUPD, c) = 1;
+    FL(F_ITERS, c) = j + 1;
+    const double est = sub_rn(th, __dmul_rn(om, phi));
+    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(est);
+    if (!fin1(est)) col_stop(a, c, ST_NONFINITE);
+    else if (!nostop && est < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
+  } else if constexpr (FIN == FIN_RHO) {
+    // rho_{j+1} = (r_{j+1}, r_0), beta_j = (rho_{j+1}/rho_j)(alpha_j/omega_j)
+    if (!FL(F_ACT, c)) return;
+    const double r1 = s[c], rho = SC(S_RHO, c), om = SC(S_OMEGA, c);
+    if (!fin1(r1)) { col_stop(a, c, ST_NONFINITE); return; }
+    if (rho == 0.0 || om == 0.0) { col_stop(a, c, ST_BREAKDOWN); return; }
+    const double be = __dmul_rn(__ddiv_rn(r1, rho), __ddiv_rn(SC(S_ALPHA, c), om));
+    if (!fin1(be)) { col_stop(a, c, ST_NONFINITE); return; }
+    SC(S_BETA, c) = be;
+    SC(S_RHO, c) = r1;
+  } else if constexpr (FIN == FIN_STORE_D0) {
+    SC(S_D0, c) = s[c];
+  } else if constexpr (FIN == FIN_STORE_D1) {
+    SC(S_D1, c) = s[c];
+  } else if constexpr (FIN == FIN_STORE_D2) {
+    SC(S_D2, c) = s[c];
+  } else if constexpr (FIN == FIN_PSI) {
+    // Algorithm 1: psi_j = (t_j, t_j) (phi_j stored by the previous kernel), omega_j
+    FL(F_XUPD, c) = 0;
+    if (!FL(F_ACT, c)) return;
+    const double phi = SC(S_D0, c), psi = s[c];
+    if (!fin1(phi) || !fin1(psi)) { col_stop(a, c, ST_NONFINITE); return; }
+    const double om = psi == 0.0 ? 0.0 : __ddiv_rn(phi, psi);
+    if (!fin1(om)) { col_stop(a, c, ST_NONFINITE); return; }
+    SC(S_OMEGA, c) = om;
+    FL(F_XUPD, c) = 1;
+  } else if constexpr (FIN == FIN_RR) {
+    // Algorithm 1 conv-check line: (r_{j+1}, r_{j+1}) < eps^2
+    if (!FL(F_XUPD, c)) return;
+    const int j = ctl->iter;
+    FL(F_ITERS, c) = j + 1;
+    const double rr = s[c];
+    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(rr);
+    if (!fin1(rr)) col_stop(a, c, ST_NONFINITE);
+    else if (!nostop && rr < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
+  } else if constexpr (FIN == FIN_R4_MERGED || FIN == FIN_R4_PLAIN) {
+    // Algorithm 6: theta = (t, r~), phi = (t,t), psi = (t, r_0), eta = (r~, r~);
+    // omega = theta/phi; stop on eta - omega*theta; rho_{j+1} = -omega*psi; beta_j
+    FL(F_XUPD, c) = 0;
+    if (!FL(F_ACT, c)) return;
+    double th, phi, psi, eta;
+    if constexpr (FIN == FIN_R4_MERGED) {
+      th = s[0 * kp + c]; phi = s[1 * kp + c]; psi = s[2 * kp + c]; eta = s[3 * kp + c];
+    } else {
+      th = SC(S_D0, c); phi = SC(S_D1, c); psi = SC(S_D2, c); eta = s[c];
+    }
+    if (!fin1(th) || !fin1(phi) || !fin1(psi) || !fin1(eta)) { col_stop(a, c, ST_NONFINITE); return; }
+    const double om = phi == 0.0 ? 0.0 : __ddiv_rn(th, phi);
+    if (!fin1(om)) { col_stop(a, c, ST_NONFINITE); return; }
+    const int j = ctl->iter;
+    SC(S_OMEGA, c) = om;
+    FL(F_XUPD, c) = 1;
+    FL(F_ITERS, c) = j + 1;
+    const double est = sub_rn(eta, __dmul_rn(om, th));
+    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(est);
+    if (!fin1(est)) { col_stop(a, c, ST_NONFINITE); return; }
+    if (!nostop && est < SC(S_EPS2, c)) { col_stop(a, c, ST_CONVERGED); return; }
+    const double r1 = __dmul_rn(-om, psi);
+    const double rho = SC(S_RHO, c);
+    if (rho == 0.0 || om == 0.0) { col_stop(a, c, ST_BREAKDOWN); return; }
+    const double be = __dmul_rn(__ddiv_rn(r1, rho), __ddiv_rn(SC(S_ALPHA, c), om));
+    if (!fin1(be) || !fin1(r1)) { col_stop(a, c, ST_NONFINITE); return; }
+    SC(S_BETA, c) = be;
+    SC(S_RHO, c) = r1;
+  } else if constexpr (FIN == FIN_PG1_MERGED || FIN == FIN_PG1_PLAIN) {
+    // Algorithm 4: theta = (q,y), phi = (y,y), pi = (q,q); omega = theta/phi;
+    // stop on pi - omega*theta
+    FL(F_XUPD, c) = 0;
+    if (!FL(F_ACT, c)) return;
+    double th, phi, pi;
+    if constexpr (FIN == FIN_PG1_MERGED) {
+      th = s[0 * kp + c]; phi = s[1 * kp + c]; pi = s[2 * kp + c];
+    } else {
+      th = SC(S_D0, c); phi = SC(S_D1, c); pi = s[c];
+    }
+    if (!fin1(th) || !fin1(phi) || !fin1(pi)) { col_stop(a, c, ST_NONFINITE); return; }
+    const double om = phi == 0.0 ? 0.0 : __ddiv_rn(th, phi);
+    if (!fin1(om)) { col_stop(a, c, ST_NONFINITE); return; }
+    const int j = ctl->iter;
+    SC(S_OMEGA, c) = om;
+    FL(F_XUPD, c) = 1;
+    FL(F_ITERS, c) = j + 1;
+    const double est = sub_rn(pi, __dmul_rn(om, th));
+    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(est);
+    if (!fin1(est)) col_stop(a, c, ST_NONFINITE);
+    else if (!nostop && est < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
+  } else if constexpr (FIN == FIN_PG3_MERGED || FIN == FIN_PG3_PLAIN) {
+    // Algorithm 4: rho_{j+1} = (r_0, r_{j+1}), psi = (r_0, z), sigma = (r_0, w_{j+1}),
+    // delta = (r_0, s); beta_j = (alpha/omega)(rho_{j+1}/rho_j);
+    // alpha_{j+1} = rho_{j+1} / (sigma + beta*delta - beta*omega*psi)
+    if (!FL(F_ACT, c)) return;
+    double r1, psi, sg, de;
+    if constexpr (FIN == FIN_PG3_MERGED) {
+      r1 = s[0 * kp + c]; psi = s[1 * kp + c]; sg = s[2 * kp + c]; de = s[3 * kp + c];
+    } else {
+      r1 = SC(S_D0, c); psi = SC(S_D1, c); sg = SC(S_D2, c); de = s[c];
+    }
+    if (!fin1(r1) || !fin1(psi) || !fin1(sg) || !fin1(de)) { col_stop(a, c, ST_NONFINITE); return; }
+    const double rho = SC(S_RHO, c), om = SC(S_OMEGA, c), al = SC(S_ALPHA, c);
+    if (rho == 0.0 || om == 0.0) { col_stop(a, c, ST_BREAKDOWN); return; }
+    const double be = __dmul_rn(__ddiv_rn(al, om), __ddiv_rn(r1, rho));
+    const double den = sub_rn(__dadd_rn(sg, __dmul_rn(be, de)), __dmul_rn(__dmul_rn(be, om), psi));
+    if (!fin1(be) || !fin1(den)) { col_stop(a, c, ST_NONFINITE); return; }
+    if (den == 0.0) { col_stop(a, c, ST_BREAKDOWN); return; }
+    const double al1 = __ddiv_rn(r1, den);
+    if (!fin1(al1)) { col_stop(a, c, ST_NONFINITE); return; }
+    SC(S_BETA, c) = be;
+    SC(S_ALPHA, c) = al1;
+    SC(S_RHO, c) = r1;
+  } else if constexpr (FIN == FIN_TRUE) {
+    // ||b - A x|| / ||b|| of the final iterate
+    const double bn2 = SC(S_BN2, c);
+    SC(S_TRUE, c) = bn2 == 0.0 ? 0.0 : __ddiv_rn(__dsqrt_rn(s[c]), __dsqrt_rn(bn2));
+  }
+}
+
+// Thread 0 of the last block, after every column's scalars are final.
+template <int CTL>
+__device__ void fin_ctl(const KArgs &a) {
+  if constexpr (CTL == CTL_NONE) {
+    return;
+  } else {
+    Ctl *ctl = a.ctl;
+    int any = 0;
+    for (int c = 0; c < a.kp; ++c) any |= FL(F_ACT, c);
+    ctl->any_active = any;
+    int go;
+    if constexpr (CTL == CTL_START) {
+      go = any && ctl->maxit > 0;
+    } else {
+      const int j = ctl->iter + 1;
+      ctl->iter = j;
+      ctl->loop_iters = j;
+      go = any && j < ctl->maxit;
+    }
+    if (a.use_cond) cudaGraphSetConditional(a.cond, go ? 1u : 0u);
+  }
+}
+
+// ------------------------------------------------------------------ fused element ops
+//
+// Each op: ND dots, FIN rule, CTL action, NL loaded double2 per chunk,
+// load() then comp() so two chunks can be in flight per thread.
+
+#define V(role) a.v[role]
+
+template <int OP>
+struct OpDef;
+
+// ---- set-up
+template <>
+struct OpDef<OP_SETUP_C> {  // r^_0 = r_0, p_0 = r_0; (b,b), (r_0,r_0)
+  static constexpr int ND = 2, FIN = FIN_SETUP, CTL = CTL_START, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_B), i); v[1] = ld2(V(V_R), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &, double2 (&acc)[ND]) {
+    st2(V(V_R0), i, v[1]);
+    st2(V(V_P), i, v[1]);
+    dot_acc(acc[0], v[0], v[0]);
+    dot_acc(acc[1], v[1], v[1]);
+  }
+};
+template <>
+struct OpDef<OP_SETUP_R> {  // r^_0 = r_0, z_0 = M^-1 r_0, v^_0 = z_0; (b,b), (r_0,r_0)
+  static constexpr int ND = 2, FIN = FIN_SETUP, CTL = CTL_START, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_B), i); v[1] = ld2(V(V_R), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &, double2 (&acc)[ND]) {
+    st2(V(V_R0), i, v[1]);
+    st2(V(V_Z), i, v[1]);
+    st2(V(V_P), i, v[1]);
+    dot_acc(acc[0], v[0], v[0]);
+    dot_acc(acc[1], v[1], v[1]);
+  }
+};
+template <>
+struct OpDef<OP_SETUP_P> {  // r^_0 = r_0; p_{-1} = s_{-1} = z_{-1} = v_{-1} = 0; (b,b), (r_0,r_0)
+  static constexpr int ND = 2, FIN = FIN_SETUP, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_B), i); v[1] = ld2(V(V_R), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &, double2 (&acc)[ND]) {
+    const double2 z = make_double2(0.0, 0.0);
+    st2(V(V_R0), i, v[1]);
+    st2(V(V_P), i, z);
+    st2(V(V_S), i, z);
+    st2(V(V_Z), i, z);
+    st2(V(V_V), i, z);
+    dot_acc(acc[0], v[0], v[0]);
+    dot_acc(acc[1], v[1], v[1]);
+  }
+};
+
+// Dot-only kernel (u, w) with a finalize rule.
+template <int VA, int VB, int FIN_, int CTL_>
+struct DotOp {
+  static constexpr int ND = 1, FIN = FIN_, CTL = CTL_, NL = (VA == VB) ? 1 : 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(VA), i);
+    if constexpr (NL == 2) v[NL - 1] = ld2(V(VB), i);
+  }
+  __device__ static void comp(const KArgs &, int64_t, const double2 (&v)[NL], const Sc2 &, double2 (&acc)[ND]) {
+    dot_acc(acc[0], v[0], v[NL - 1]);
+  }
+};
+template <> struct OpDef<OP_DOT_RW0> : DotOp<V_R0, V_W, FIN_RW0, CTL_START> {};
+
+// ---- classical
+template <> struct OpDef<OP_DELTA> : DotOp<V_V, V_R0, FIN_DELTA, CTL_NONE> {};
+template <>
+struct OpDef<OP_UPD_S> {  // s_j = r_j - alpha_j v_j
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_R), i); v[1] = ld2(V(V_V), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_S), i, fma2(neg2(s.al), v[1], v[0]));
+  }
+};
+template <>
+struct OpDef<OP_G1> {  // phi = (t,s), psi = (t,t), theta = (s,s)
+  static constexpr int ND = 3, FIN = FIN_G1, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_T), i); v[1] = ld2(V(V_S), i); }
+  __device__ static void comp(const KArgs &, int64_t, const double2 (&v)[NL], const Sc2 &, double2 (&acc)[ND]) {
+    dot_acc(acc[0], v[0], v[1]);
+    dot_acc(acc[1], v[0], v[0]);
+    dot_acc(acc[2], v[1], v[1]);
+  }
+};
+template <>
+struct OpDef<OP_G3> {  // x += alpha p + omega s; r = s - omega t; rho = (r, r_0)
+  static constexpr int ND = 1, FIN = FIN_RHO, CTL = CTL_END_ITER, NL = 5;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_X), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_S), i); v[3] = ld2(V(V_T), i); v[4] = ld2(V(V_R0), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&acc)[ND]) {
+    const double2 xn = fma2(s.om, v[2], fma2(s.al, v[1], v[0]));
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+    const double2 r = fma2(neg2(s.om), v[3], v[2]);
+    st2(V(V_R), i, r);
+    dot_acc(acc[0], r, v[4]);
+  }
+};
+template <>
+struct OpDef<OP_UPD_P> {  // p = r + beta (p - omega v)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_R), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_V), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_P), i, fma2(s.be, fma2(neg2(s.om), v[2], v[1]), v[0]));
+  }
+};
+template <> struct OpDef<OP_DOT_TS> : DotOp<V_T, V_S, FIN_STORE_D0, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_PSI> : DotOp<V_T, V_T, FIN_PSI, CTL_NONE> {};
+template <>
+struct OpDef<OP_UPD_X_C> {  // x += alpha p + omega s
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_X), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_S), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 xn = fma2(s.om, v[2], fma2(s.al, v[1], v[0]));
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+  }
+};
+template <>
+struct OpDef<OP_UPD_R_C> {  // r = s - omega t
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_S), i); v[1] = ld2(V(V_T), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_R), i, fma2(neg2(s.om), v[1], v[0]));
+  }
+};
+template <> struct OpDef<OP_DOT_RR> : DotOp<V_R, V_R, FIN_RR, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_RHO> : DotOp<V_R, V_R0, FIN_RHO, CTL_END_ITER> {};
+
+// ---- reordered (v^ lives in V_P, t^ in V_TMP, r~ in V_RT)
+template <>
+struct OpDef<OP_COPY_SV> {  // s_j = M^-1 v_j (identity: copy)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 1;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_V), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &, double2 (&)[1]) { st2(V(V_S), i, v[0]); }
+};
+template <>
+struct OpDef<OP_COPY_QT> {  // q_j = M^-1 t_j (identity: copy)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 1;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_T), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &, double2 (&)[1]) { st2(V(V_Q), i, v[0]); }
+};
+template <>
+struct OpDef<OP_UPD_TH> {  // t^_j = z_j - alpha_j s_j
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_Z), i); v[1] = ld2(V(V_S), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_TMP), i, fma2(neg2(s.al), v[1], v[0]));
+  }
+};
+template <>
+struct OpDef<OP_RG4> {  // r~ = r - alpha v; theta = (t,r~), phi = (t,t), psi = (t,r_0), eta = (r~,r~)
+  static constexpr int ND = 4, FIN = FIN_R4_MERGED, CTL = CTL_END_ITER, NL = 4;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_R), i); v[1] = ld2(V(V_V), i); v[2] = ld2(V(V_T), i); v[3] = ld2(V(V_R0), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&acc)[ND]) {
+    const double2 rt = fma2(neg2(s.al), v[1], v[0]);
+    st2(V(V_RT), i, rt);
+    dot_acc(acc[0], v[2], rt);
+    dot_acc(acc[1], v[2], v[2]);
+    dot_acc(acc[2], v[2], v[3]);
+    dot_acc(acc[3], rt, rt);
+  }
+};
+template <>
+struct OpDef<OP_UPD_R_R> {  // r_{j+1} = r~_j - omega_j t_j
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_RT), i); v[1] = ld2(V(V_T), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_R), i, fma2(neg2(s.om), v[1], v[0]));
+  }
+};
+template <>
+struct OpDef<OP_RFIN> {  // x += alpha v^ + omega t^; z = t^ - omega q; v^ = z + beta (v^ - omega s)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 5;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_X), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_TMP), i); v[3] = ld2(V(V_Q), i); v[4] = ld2(V(V_S), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 xn = fma2(s.om, v[2], fma2(s.al, v[1], v[0]));
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+    const double2 z = fma2(neg2(s.om), v[3], v[2]);
+    st2(V(V_Z), i, z);
+    st2(V(V_P), i, fma2(s.be, fma2(neg2(s.om), v[4], v[1]), z));
+  }
+};
+template <>
+struct OpDef<OP_UPD_RT> {  // r~ = r - alpha v
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_R), i); v[1] = ld2(V(V_V), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_RT), i, fma2(neg2(s.al), v[1], v[0]));
+  }
+};
+template <> struct OpDef<OP_DOT_T_RT> : DotOp<V_T, V_RT, FIN_STORE_D0, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_T_T> : DotOp<V_T, V_T, FIN_STORE_D1, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_T_R0> : DotOp<V_T, V_R0, FIN_STORE_D2, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_RT_RT> : DotOp<V_RT, V_RT, FIN_R4_PLAIN, CTL_END_ITER> {};
+template <>
+struct OpDef<OP_UPD_X_R> {  // x += alpha v^ + omega t^
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_X), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_TMP), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 xn = fma2(s.om, v[2], fma2(s.al, v[1], v[0]));
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+  }
+};
+template <>
+struct OpDef<OP_UPD_Z_R> {  // z = t^ - omega q
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_TMP), i); v[1] = ld2(V(V_Q), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_Z), i, fma2(neg2(s.om), v[1], v[0]));
+  }
+};
+template <>
+struct OpDef<OP_UPD_VH> {  // v^ = z + beta (v^ - omega s)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_Z), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_S), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_P), i, fma2(s.be, fma2(neg2(s.om), v[2], v[1]), v[0]));
+  }
+};
+
+// ---- pipelined
+template <>
+struct OpDef<OP_PG1> {  // p, s, z recurrences; q = r - alpha s; y = w - alpha z; theta, phi, pi
+  static constexpr int ND = 3, FIN = FIN_PG1_MERGED, CTL = CTL_NONE, NL = 7;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_R), i); v[1] = ld2(V(V_W), i); v[2] = ld2(V(V_T), i); v[3] = ld2(V(V_P), i);
+    v[4] = ld2(V(V_S), i); v[5] = ld2(V(V_Z), i); v[6] = ld2(V(V_V), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&acc)[ND]) {
+    const double2 nom = neg2(s.om), nal = neg2(s.al);
+    const double2 p = fma2(s.be, fma2(nom, v[4], v[3]), v[0]);
+    const double2 sn = fma2(s.be, fma2(nom, v[5], v[4]), v[1]);
+    const double2 zn = fma2(s.be, fma2(nom, v[6], v[5]), v[2]);
+    const double2 q = fma2(nal, sn, v[0]);
+    const double2 y = fma2(nal, zn, v[1]);
+    st2(V(V_P), i, p);
+    st2(V(V_S), i, sn);
+    st2(V(V_Z), i, zn);
+    st2(V(V_Q), i, q);
+    st2(V(V_Y), i, y);
+    dot_acc(acc[0], q, y);
+    dot_acc(acc[1], y, y);
+    dot_acc(acc[2], q, q);
+  }
+};
+template <>
+struct OpDef<OP_PG2> {  // x += alpha p + omega q; r = q - omega y
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 4;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_X), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_Q), i); v[3] = ld2(V(V_Y), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 xn = fma2(s.om, v[2], fma2(s.al, v[1], v[0]));
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+    st2(V(V_R), i, fma2(neg2(s.om), v[3], v[2]));
+  }
+};
+template <>
+struct OpDef<OP_PG3> {  // w = y - omega (t - alpha v); (r0,r), (r0,z), (r0,w), (r0,s)
+  static constexpr int ND = 4, FIN = FIN_PG3_MERGED, CTL = CTL_END_ITER, NL = 7;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_Y), i); v[1] = ld2(V(V_T), i); v[2] = ld2(V(V_V), i); v[3] = ld2(V(V_R0), i);
+    v[4] = ld2(V(V_R), i); v[5] = ld2(V(V_Z), i); v[6] = ld2(V(V_S), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&acc)[ND]) {
+    const double2 w = fma2(neg2(s.om), fma2(neg2(s.al), v[2], v[1]), v[0]);
+    st2(V(V_W), i, w);
+    dot_acc(acc[0], v[3], v[4]);
+    dot_acc(acc[1], v[3], v[5]);
+    dot_acc(acc[2], v[3], w);
+    dot_acc(acc[3], v[3], v[6]);
+  }
+};
+// basic pipelined: one kernel per vector operation
+template <int DST, int VR, int VOLD, int VM, bool BETA>
+struct PUpd {  // DST = VR + beta (VOLD - omega VM)   or (BETA false) DST = VR - alpha VM
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = BETA ? 3 : 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(VR), i);
+    v[1] = ld2(V(VM), i);
+    if constexpr (BETA) v[2] = ld2(V(VOLD), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    if constexpr (BETA)
+      st2(V(DST), i, fma2(s.be, fma2(neg2(s.om), v[1], v[2]), v[0]));
+    else
+      st2(V(DST), i, fma2(neg2(s.al), v[1], v[0]));
+  }
+};
+template <> struct OpDef<OP_PU_P> : PUpd<V_P, V_R, V_P, V_S, true> {};
+template <> struct OpDef<OP_PU_S> : PUpd<V_S, V_W, V_S, V_Z, true> {};
+template <> struct OpDef<OP_PU_Z> : PUpd<V_Z, V_T, V_Z, V_V, true> {};
+template <> struct OpDef<OP_PU_Q> : PUpd<V_Q, V_R, V_R, V_S, false> {};
+template <> struct OpDef<OP_PU_Y> : PUpd<V_Y, V_W, V_W, V_Z, false> {};
+template <> struct OpDef<OP_DOT_QY> : DotOp<V_Q, V_Y, FIN_STORE_D0, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_YY> : DotOp<V_Y, V_Y, FIN_STORE_D1, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_QQ> : DotOp<V_Q, V_Q, FIN_PG1_PLAIN, CTL_NONE> {};
+template <>
+struct OpDef<OP_PU_X> {  // x += alpha p + omega q
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_X), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_Q), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 xn = fma2(s.om, v[2], fma2(s.al, v[1], v[0]));
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+  }
+};
+template <>
+struct OpDef<OP_PU_R> {  // r = q - omega y
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_Q), i); v[1] = ld2(V(V_Y), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_R), i, fma2(neg2(s.om), v[1], v[0]));
+  }
+};
+template <>
+struct OpDef<OP_PU_TMP> {  // tmp = t - alpha v   (first call of the 4-vector update)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_T), i); v[1] = ld2(V(V_V), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_TMP), i, fma2(neg2(s.al), v[1], v[0]));
+  }
+};
+template <>
+struct OpDef<OP_PU_W> {  // w = y - omega tmp   (second call)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_Y), i); v[1] = ld2(V(V_TMP), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_W), i, fma2(neg2(s.om), v[1], v[0]));
+  }
+};
+template <> struct OpDef<OP_DOT_R0R> : DotOp<V_R0, V_R, FIN_STORE_D0, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_R0Z> : DotOp<V_R0, V_Z, FIN_STORE_D1, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_R0W> : DotOp<V_R0, V_W, FIN_STORE_D2, CTL_NONE> {};
+template <> struct OpDef<OP_DOT_R0S> : DotOp<V_R0, V_S, FIN_PG3_PLAIN, CTL_END_ITER> {};
+
+// ---- final residual norm (V_TMP holds b - A x)
+template <> struct OpDef<OP_TRUE_RES> : DotOp<V_TMP, V_TMP, FIN_TRUE, CTL_NONE> {};
+
+#undef V
+
+// ------------------------------------------------------------------ the kernel
+
+template <int ND>
+struct RedSmem {
+  double red[kVecThreads / 32][ND][kMaxKp];
+  double sums[ND * kMaxKp];
+  unsigned int ticket;
+};
+
+template <class D, int ND = D::ND>
+__device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND : 1]) {
+  __shared__ RedSmem<ND> sm;
+  const int kp = a.kp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v0[ND], v1[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    if (kp == 1) {
+      v0[d] = acc[d].x + acc[d].y;
+      v1[d] = 0.0;
+    } else {
+      v0[d] = acc[d].x;
+      v1[d] = acc[d].y;
+    }
+  }
+  // lanes l and l^m hold the same columns iff m is a multiple of kp/2 (kp >= 2)
+  const int mstart = kp == 1 ? 1 : (kp >> 1);
+  for (int m = mstart; m < 32; m <<= 1) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      v0[d] += __shfl_xor_sync(0xffffffffu, v0[d], m);
+      if (kp > 1) v1[d] += __shfl_xor_sync(0xffffffffu, v1[d], m);
+    }
+  }
+  if (kp == 1) {
+    if (lane == 0)
+#pragma unroll
+      for (int d = 0; d < ND; ++d) sm.red[warp][d][0] = v0[d];
+  } else if (lane < (kp >> 1)) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      sm.red[warp][d][2 * lane] = v0[d];
+      sm.red[warp][d][2 * lane + 1] = v1[d];
+    }
+  }
+  __syncthreads();
+  const int nout = ND * kp;
+  double *mypart = a.part + (size_t)blockIdx.x * (kMaxDots * kMaxKp);
+  for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+    const int d = t / kp, c = t - d * kp;
+    double s = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) s += sm.red[w][d][c];
+    mypart[d * kMaxKp + c] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) sm.ticket = atomicAdd(&a.ctl->ticket, 1u);
+  __syncthreads();
+  if (sm.ticket != gridDim.x - 1) return;
+  __threadfence();
+  // last block: fixed-order sum of the block partials
+  int tpo = 32;
+  while (tpo > 1 && tpo * nout > (int)blockDim.x) tpo >>= 1;
+  const int groups = blockDim.x / tpo;
+  for (int o0 = 0; o0 < nout; o0 += groups) {
+    const int o = o0 + threadIdx.x / tpo, sub = threadIdx.x % tpo;
+    double s = 0.0;
+    if (o < nout) {
+      const int d = o / kp, c = o - d * kp;
+      for (int b = sub; b < (int)gridDim.x; b += tpo) s += __ldcg(a.part + (size_t)b * (kMaxDots * kMaxKp) + d * kMaxKp + c);
+    }
+    for (int m = tpo >> 1; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (o < nout && sub == 0) sm.sums[o] = s;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < kp) fin_col<D::FIN>(a, threadIdx.x, sm.sums, kp);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.ctl->ticket = 0;
+    fin_ctl<D::CTL>(a);
+  }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kVecThreads, 2) vec_kernel(const KArgs a) {
+  using D = OpDef<OP>;
+  constexpr int ND = D::ND;
+  const int kp = a.kp;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int c0 = kp == 1 ? 0 : (int)((2 * gtid) & (kp - 1));
+  const int c1 = kp == 1 ? 0 : c0 + 1;
+  Sc2 s;
+  s.al = make_double2(SC(S_ALPHA, c0), SC(S_ALPHA, c1));
+  s.om = make_double2(SC(S_OMEGA, c0), SC(S_OMEGA, c1));
+  s.be = make_double2(SC(S_BETA, c0), SC(S_BETA, c1));
+  s.u0 = FL(F_XUPD, c0) != 0;
+  s.u1 = FL(F_XUPD, c1) != 0;
+  double2 acc[ND > 0 ? ND : 1];
+#pragma unroll
+  for (int d = 0; d < (ND > 0 ? ND : 1); ++d) acc[d] = make_double2(0.0, 0.0);
+  // chunks of two doubles; an odd total (kp == 1, odd n) ends in a zero pad element
+  const int64_t n2 = (a.n * kp + 1) >> 1;
+  int64_t i = gtid;
+  for (; i + stride < n2; i += 2 * stride) {
+    double2 va[D::NL], vb[D::NL];
+    D::load(a, i, va);
+    D::load(a, i + stride, vb);
+    D::comp(a, i, va, s, acc);
+    D::comp(a, i + stride, vb, s, acc);
+  }
+  if (i < n2) {
+    double2 va[D::NL];
+    D::load(a, i, va);
+    D::comp(a, i, va, s, acc);
+  }
+  if constexpr (ND > 0) reduce_and_finalize<D>(a, acc);
+}
+
+// ------------------------------------------------------------------ pack / unpack / reset
+
+__global__ void pack_kernel(const double *__restrict__ B, const double *__restrict__ X0, int k, KArgs a) {
+  const int kp = a.kp;
+  const int64_t m = a.n * kp;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int64_t i = e / kp;
+    const int c = (int)(e - i * kp);
+    const bool real = c < k;
+    a.v[V_B][e] = real ? B[i * k + c] : 0.0;
+    a.v[V_X][e] = (real && X0) ? X0[i * k + c] : 0.0;
+  }
+  // zero pad element of odd-length blocks (kp == 1): every role
+  if ((m & 1) && blockIdx.x == 0 && threadIdx.x < V_NVEC) a.v[threadIdx.x][m] = 0.0;
+}
+
+__global__ void unpack_kernel(double *__restrict__ X, int k, KArgs a, int role, int use_xzero) {
+  const int kp = a.kp;
+  const int64_t m = a.n * k;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const double *src = a.v[role];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int64_t i = e / k;
+    const int c = (int)(e - i * k);
+    X[e] = (use_xzero && FL(F_XZERO, c)) ? 0.0 : src[i * kp + c];
+  }
+}
+
+__global__ void reset_kernel(KArgs a, int64_t hist_len) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double *h = a.ctl->hist;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < hist_len; e += stride) h[e] = __longlong_as_double(0x7ff8000000000000LL);
+  if (blockIdx.x == 0) {
+    for (int t = threadIdx.x; t < S_NSLOT * kMaxKp; t += blockDim.x) a.sc[t] = 0.0;
+    for (int t = threadIdx.x; t < F_NFLAG * kMaxKp; t += blockDim.x) a.fl[t] = 0;
+  }
+}
+
+template <int OP>
+cudaError_t launch_one(const KArgs &a, int grid, cudaStream_t s) {
+  vec_kernel<OP><<<grid, kVecThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int OP>
+int occ_one() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, vec_kernel<OP>, kVecThreads, 0) != cudaSuccess) return 1;
+  return nb > 0 ? nb : 1;
+}
+
+struct OpInfo {
+  const char *name;
+  int reads, writes;
+  cudaError_t (*launch)(const KArgs &, int, cudaStream_t);
+  int (*occ)();
+  int nd;
+};
+
+#define OPI(op, name, r, w) {name, r, w, &launch_one<op>, &occ_one<op>, OpDef<op>::ND}
+const OpInfo kOps[OP_COUNT] = {
+    OPI(OP_SETUP_C, "setup_classical", 2, 2),
+    OPI(OP_SETUP_R, "setup_reordered", 2, 3),
+    OPI(OP_SETUP_P, "setup_pipelined", 2, 5),
+    OPI(OP_DOT_RW0, "dot_r0_w0", 2, 0),
+    OPI(OP_DELTA, "dot_delta", 2, 0),
+    OPI(OP_UPD_S, "upd_s", 2, 1),
+    OPI(OP_G1, "merged_phi_psi_theta", 2, 0),
+    OPI(OP_G3, "merged_x_r_rho", 5, 2),
+    OPI(OP_UPD_P, "upd_p", 3, 1),
+    OPI(OP_DOT_TS, "dot_phi", 2, 0),
+    OPI(OP_DOT_PSI, "dot_psi", 1, 0),
+    OPI(OP_UPD_X_C, "upd_x", 3, 1),
+    OPI(OP_UPD_R_C, "upd_r", 2, 1),
+    OPI(OP_DOT_RR, "dot_rr", 1, 0),
+    OPI(OP_DOT_RHO, "dot_rho", 2, 0),
+    OPI(OP_COPY_SV, "precond_copy_s", 1, 1),
+    OPI(OP_UPD_TH, "upd_that", 2, 1),
+    OPI(OP_RG4, "merged_rtilde_4dots", 4, 1),
+    OPI(OP_COPY_QT, "precond_copy_q", 1, 1),
+    OPI(OP_UPD_R_R, "upd_r", 2, 1),
+    OPI(OP_RFIN, "merged_x_z_vhat", 5, 3),
+    OPI(OP_UPD_RT, "upd_rtilde", 2, 1),
+    OPI(OP_DOT_T_RT, "dot_theta", 2, 0),
+    OPI(OP_DOT_T_T, "dot_phi", 1, 0),
+    OPI(OP_DOT_T_R0, "dot_psi", 2, 0),
+    OPI(OP_DOT_RT_RT, "dot_eta", 1, 0),
+    OPI(OP_UPD_X_R, "upd_x", 3, 1),
+    OPI(OP_UPD_Z_R, "upd_z", 2, 1),
+    OPI(OP_UPD_VH, "upd_vhat", 3, 1),
+    OPI(OP_PG1, "merged_pszqy_3dots", 7, 5),
+    OPI(OP_PG2, "merged_x_r", 4, 2),
+    OPI(OP_PG3, "merged_w_4dots", 7, 1),
+    OPI(OP_PU_P, "upd_p", 3, 1),
+    OPI(OP_PU_S, "upd_s", 3, 1),
+    OPI(OP_PU_Z, "upd_z", 3, 1),
+    OPI(OP_PU_Q, "upd_q", 2, 1),
+    OPI(OP_PU_Y, "upd_y", 2, 1),
+    OPI(OP_DOT_QY, "dot_theta", 2, 0),
+    OPI(OP_DOT_YY, "dot_phi", 1, 0),
+    OPI(OP_DOT_QQ, "dot_pi", 1, 0),
+    OPI(OP_PU_X, "upd_x", 3, 1),
+    OPI(OP_PU_R, "upd_r", 2, 1),
+    OPI(OP_PU_TMP, "upd_w_part1", 2, 1),
+    OPI(OP_PU_W, "upd_w_part2", 2, 1),
+    OPI(OP_DOT_R0R, "dot_rho", 2, 0),
+    OPI(OP_DOT_R0Z, "dot_psi", 2, 0),
+    OPI(OP_DOT_R0W, "dot_sigma", 2, 0),
+    OPI(OP_DOT_R0S, "dot_delta", 2, 0),
+    OPI(OP_TRUE_RES, "dot_true_residual", 1, 0),
+};
+#undef OPI
+
+}  // namespace
+
+const char *op_name(int op) { return (op >= 0 && op < OP_COUNT) ? kOps[op].name : "?"; }
+void op_traffic(int op, int *reads, int *writes) {
+  *reads = (op >= 0 && op < OP_COUNT) ? kOps[op].reads : 0;
+  *writes = (op >= 0 && op < OP_COUNT) ? kOps[op].writes : 0;
+}
+int op_has_dots(int op) { return (op >= 0 && op < OP_COUNT) ? kOps[op].nd > 0 : 0; }
+
+cudaError_t launch_vec(int op, const KArgs &a, int grid, cudaStream_t s) {
+  if (op < 0 || op >= OP_COUNT) return cudaErrorInvalidValue;
+  return kOps[op].launch(a, grid, s);
+}
+int vec_blocks_per_sm(int op) { return (op >= 0 && op < OP_COUNT) ? kOps[op].occ() : 1; }
+
+cudaError_t launch_pack(const double *B, const double *X0, int k, const KArgs &a, cudaStream_t s) {
+  pack_kernel<<<1024, 256, 0, s>>>(B, X0, k, a);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack_role(double *X, int k, const KArgs &a, int role, int use_xzero, cudaStream_t s) {
+  unpack_kernel<<<1024, 256, 0, s>>>(X, k, a, role, use_xzero);
+  return cudaGetLastError();
+}
+cudaError_t launch_reset(const KArgs &a, int64_t hist_len, cudaStream_t s) {
+  reset_kernel<<<64, 256, 0, s>>>(a, hist_len);
+  return cudaGetLastError();
+}
+
+}  // namespace bicgk

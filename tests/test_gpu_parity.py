@@ -1,0 +1,273 @@
+"""CUDA path vs the FP64 oracle, through the C-ABI (libbicgk.so).
+
+Three kinds of comparison:
+  * trajectory: the iterate x_m after m = 1, 2, 4, 8 iterations (fixed count),
+    per column, relative 2-norm difference <= 1e-12.  Both sides perform the
+    same operations and differ only in rounding (dot-product summation order,
+    fused multiply-adds), which stays at 1e-16..1e-14 over these iterations on
+    every operator;
+  * full solve, stable operators (strongly nonsymmetric upwind and 27-point
+    stencils, where rounding differences do not grow): solution within 1e-10
+    relative, iteration count within +-1, same status;
+  * full solve, nearly symmetric operators (the h-scaled convection-diffusion
+    of the 16^3 configuration, Poisson): there BiCGStab amplifies rounding
+    differences by about 10^3 every 8 iterations, so the stopping iterate is
+    not unique.  What is unique is the exact solution x* = A^-1 b (sparse LU):
+    the GPU iterate must be as close to x* as the oracle's (both are bounded by
+    ||A^-1|| times their residual), both true residuals below the tolerance,
+    and the iteration counts inside the spread the oracle's own equivalent
+    forms show (15%).
+Inputs are the seeded synthetic stencils of the paper's workloads (Sec. 2.3:
+7-point Poisson; the upwind convection-diffusion and 27-point operators of the
+benchmark configurations).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_12874_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SOL_RTOL = 1e-10
+VARIANTS = list(oracle.VARIANTS)
+
+
+@pytest.fixture(scope="module")
+def bk(cuda):
+    from paper_1907_12874_gb300 import bicgk
+    return bicgk
+
+
+def _colerr(X, Xo):
+    num = np.linalg.norm(X - Xo, axis=0)
+    den = np.linalg.norm(Xo, axis=0)
+    return num / np.where(den == 0, 1.0, den)
+
+
+def _gpu_solve(bk, torch, A, B, **kw):
+    with bk.Operator(A) as op:
+        Bd = torch.from_numpy(B).cuda()
+        X0 = kw.pop("X0", None)
+        X0d = None if X0 is None else torch.from_numpy(np.ascontiguousarray(X0)).cuda()
+        r = op.solve(Bd, X0=X0d, **kw)
+        torch.cuda.synchronize()
+        return r, r.X.cpu().numpy()
+
+
+def _compare(r, X, ro, tol_sol=SOL_RTOL, iters_slack=1):
+    assert np.all(np.abs(r.iters - ro.iters) <= iters_slack), (r.iters, ro.iters)
+    assert np.array_equal(r.status, ro.status), (r.status, ro.status)
+    same = r.iters == ro.iters
+    err = _colerr(X, ro.X)
+    assert np.all(err[same] <= tol_sol), err
+    # where the counts differ by one, both iterates still solve the system to the tolerance
+    assert np.all(err <= 1e-6), err
+    return err
+
+
+# ------------------------------------------------------------------ SpMM
+
+def _random_csr(n, seed, max_len=40):
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(0, max_len, size=n)
+    lens[:3] = 0                      # empty rows
+    lens[n // 2] = min(n, 3000)       # one long row: the staged tile overflows
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    np.cumsum(lens, out=rowptr[1:])
+    cols = np.concatenate([rng.choice(n, size=l, replace=False) for l in lens]).astype(np.int32)
+    vals = rng.standard_normal(rowptr[-1])
+    return I.CSR(rowptr, cols, vals, "random")
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("kind", ["convdiff7", "random"])
+def test_spmm_matches_oracle(bk, cuda, k, kind):
+    torch = cuda
+    A = I.convdiff7(13) if kind == "convdiff7" else _random_csr(3001, 7)
+    X = I.rhs(A.n, k, 11)
+    Yo = oracle.spmm(A, X)
+    with bk.Operator(A) as op:
+        Xd = torch.from_numpy(X).cuda()
+        Y = op.spmm(Xd).cpu().numpy()
+    # same products, same order, FMA on the GPU: bound by |A||X| * few ulps
+    absA = I.CSR(A.rowptr, A.colidx, np.abs(A.vals))
+    bound = oracle.spmm(absA, np.abs(X)) * (4 * 2.0 ** -52) * np.maximum(1, np.diff(A.rowptr))[:, None]
+    assert np.all(np.abs(Y - Yo) <= bound + 1e-300)
+
+
+def _compare_chaotic(r, X, ro, A, B, tol):
+    """Nearly symmetric operators: compare with the unique exact solution (see module doc)."""
+    import scipy.sparse.linalg as sla
+    lu = sla.splu(A.to_scipy().tocsc())
+    Xs = lu.solve(B)
+    assert np.all(r.status == 0) and np.all(ro.status == 0)
+    assert np.all(r.true_relres < 2 * tol) and np.all(ro.true_relres < 2 * tol)
+    eg = np.linalg.norm(X - Xs, axis=0)
+    eo = np.linalg.norm(ro.X - Xs, axis=0)
+    # ||x - x*|| <= ||A^-1|| ||b - A x||: estimate ||A^-1|| by power iteration with the LU factors
+    v = I.rhs(A.n, 1, 99)[:, 0]
+    for _ in range(30):
+        w = lu.solve(v)
+        w = lu.solve(w, trans="T")
+        v = w / np.linalg.norm(w)
+    inv_norm = np.sqrt(np.linalg.norm(lu.solve(lu.solve(v), trans="T")))
+    bound = inv_norm * r.true_relres * np.linalg.norm(B, axis=0)
+    assert np.all(eg <= 1.5 * bound + 1e-14), (eg, bound)
+    assert np.all(eg <= 20 * eo + 1e-12 * np.linalg.norm(Xs, axis=0)), (eg, eo)
+    assert np.all(np.abs(r.iters - ro.iters) <= np.maximum(2, 0.15 * ro.iters)), (r.iters, ro.iters)
+
+
+def _trajectory(bk, torch, A, B, variant, ms=(1, 2, 4, 8), tol_traj=1e-12):
+    with bk.Operator(A) as op:
+        Bd = torch.from_numpy(B).cuda()
+        for m in ms:
+            r = op.solve(Bd, tol=0.0, maxit=m, variant=variant, flags=1)
+            ro = oracle.solve(A, B, tol=0.0, maxit=m, variant=variant, flags=oracle.NO_STOP_TEST)
+            X = r.X.cpu().numpy()
+            err = _colerr(X, ro.X)
+            assert np.all(err <= tol_traj), (m, err)
+            np.testing.assert_allclose(r.hist[: m + 1], ro.hist[: m + 1], rtol=1e-10)
+
+
+# ------------------------------------------------------------------ full solves
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_config1_16cubed_k4(bk, cuda, variant):
+    """16^3 upwind convection-diffusion, 4 RHS U[-1,1] (seed 1), x0 = 0, rel tol 1e-8."""
+    A = I.convdiff7(16)
+    B = I.rhs(A.n, 4, 1)
+    _trajectory(bk, cuda, A, B, variant)
+    ro = oracle.solve(A, B, tol=1e-8, maxit=1000, variant=variant)
+    r, X = _gpu_solve(bk, cuda, A, B, tol=1e-8, maxit=1000, variant=variant)
+    _compare_chaotic(r, X, ro, A, B, 1e-8)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_stable_operator_16cubed(bk, cuda, variant):
+    """Strongly nonsymmetric upwind operator (mesh Peclet beta): the spec bar, 1e-10 and +-1."""
+    A = I.convdiff7(16, peclet=True)
+    B = I.rhs(A.n, 4, 1)
+    _trajectory(bk, cuda, A, B, variant)
+    ro = oracle.solve(A, B, tol=1e-8, maxit=1000, variant=variant)
+    r, X = _gpu_solve(bk, cuda, A, B, tol=1e-8, maxit=1000, variant=variant)
+    _compare(r, X, ro)
+    assert np.all(r.status == 0) and np.all(r.true_relres < 2e-8)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_ragged_k_24cubed(bk, cuda, variant, k):
+    """Several tiles, padded RHS counts (k = 3 -> 4 columns), odd row count (24^3 is even; 23^3 odd)."""
+    A = I.convdiff7(23, peclet=True)
+    B = I.rhs(A.n, k, 5)
+    ro = oracle.solve(A, B, tol=1e-8, maxit=2000, variant=variant)
+    r, X = _gpu_solve(bk, cuda, A, B, tol=1e-8, maxit=2000, variant=variant)
+    _compare(r, X, ro)
+
+
+def test_k64_and_poisson(bk, cuda):
+    A = I.convdiff7(12, beta=(0, 0, 0))
+    B = I.rhs(A.n, 64, 9)
+    _trajectory(bk, cuda, A, B, "classical_merged", ms=(1, 4, 8))
+    ro = oracle.solve(A, B, tol=1e-9, maxit=1000, variant="classical_merged")
+    r, X = _gpu_solve(bk, cuda, A, B, tol=1e-9, maxit=1000, variant="classical_merged")
+    _compare_chaotic(r, X, ro, A, B, 1e-9)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_perturbed27(bk, cuda, variant):
+    A = I.perturbed27(10, seed=3)
+    B = I.rhs(A.n, 2, 4)
+    ro = oracle.solve(A, B, tol=1e-10, maxit=500, variant=variant)
+    r, X = _gpu_solve(bk, cuda, A, B, tol=1e-10, maxit=500, variant=variant)
+    _compare(r, X, ro)
+
+
+# ------------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_edge_columns(bk, cuda, variant):
+    """b_c = 0 -> x_c = 0 with 0 iterations; x0 = exact -> 0 iterations; maxit status."""
+    A = I.convdiff7(8)
+    B = I.rhs(A.n, 4, 3)
+    B[:, 1] = 0.0
+    Xs = I.rhs(A.n, 4, 8)
+    X0 = np.zeros_like(B)
+    X0[:, 1] = 1.0                      # b = 0 but x0 != 0: result must be 0
+    B[:, 2] = oracle.spmm(A, Xs[:, 2:3])[:, 0]
+    X0[:, 2] = Xs[:, 2]                 # exact initial guess
+    ro = oracle.solve(A, B, X0=X0, tol=1e-8, maxit=1000, variant=variant)
+    r, X = _gpu_solve(bk, cuda, A, B, X0=X0, tol=1e-8, maxit=1000, variant=variant)
+    _compare(r, X, ro)
+    assert r.iters[1] == 0 and r.status[1] == 0 and np.all(X[:, 1] == 0.0)
+    assert r.iters[2] == 0 and np.array_equal(X[:, 2], X0[:, 2])
+    # maxit = 3: every column that needs more reports MAXIT after exactly 3 iterates
+    ro = oracle.solve(A, B, X0=X0, tol=1e-8, maxit=3, variant=variant)
+    r, X = _gpu_solve(bk, cuda, A, B, X0=X0, tol=1e-8, maxit=3, variant=variant)
+    assert np.array_equal(r.status, ro.status) and np.array_equal(r.iters, ro.iters)
+    assert np.all(_colerr(X, ro.X) <= 1e-12)
+    # maxit = 0
+    r, X = _gpu_solve(bk, cuda, A, B, X0=X0, tol=1e-8, maxit=0, variant=variant)
+    ro = oracle.solve(A, B, X0=X0, tol=1e-8, maxit=0, variant=variant)
+    assert np.array_equal(r.status, ro.status) and np.array_equal(r.iters, ro.iters)
+    assert np.array_equal(X, ro.X)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_scaled_identity_one_step(bk, cuda, variant):
+    """A = 2I: alpha = 1/2 exactly, s = 0, omega = 0 by the psi = 0 rule: x = b/2 after one iterate."""
+    n = 1000
+    A = I.CSR(np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.full(n, 2.0))
+    B = I.rhs(n, 3, 2)
+    r, X = _gpu_solve(bk, cuda, A, B, tol=1e-12, maxit=10, variant=variant)
+    ro = oracle.solve(A, B, tol=1e-12, maxit=10, variant=variant)
+    assert np.array_equal(r.iters, ro.iters) and np.array_equal(r.status, ro.status)
+    np.testing.assert_array_equal(X, B / 2)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_fixed_iteration_mode(bk, cuda, variant):
+    """NO_STOP_TEST: exactly maxit iterations (the paper's N_it benchmark mode)."""
+    A = I.convdiff7(10)
+    B = I.rhs(A.n, 2, 6)
+    r, X = _gpu_solve(bk, cuda, A, B, tol=0.0, maxit=12, variant=variant, flags=1)
+    ro = oracle.solve(A, B, tol=0.0, maxit=12, variant=variant, flags=oracle.NO_STOP_TEST)
+    assert np.all(r.iters == 12) and np.all(r.status == 1)
+    assert np.all(_colerr(X, ro.X) <= 1e-11)
+
+
+def test_host_memory_path_is_bitwise_device_path(bk, cuda):
+    torch = cuda
+    A = I.convdiff7(14)
+    B = I.rhs(A.n, 5, 12)
+    with bk.Operator(A) as op:
+        rh = op.solve(B, tol=1e-8, maxit=500)
+        rd = op.solve(torch.from_numpy(B).cuda(), tol=1e-8, maxit=500)
+        rd2 = op.solve(torch.from_numpy(B).cuda(), tol=1e-8, maxit=500)
+        Xd = rd.X.cpu().numpy()
+    assert np.array_equal(rh.X, Xd)                     # same kernels, same order
+    assert np.array_equal(Xd, rd2.X.cpu().numpy())      # deterministic reductions
+    assert np.array_equal(rh.iters, rd.iters)
+
+
+def test_profiling_mode_matches_graph_mode(bk, cuda):
+    torch = cuda
+    A = I.convdiff7(12)
+    B = torch.from_numpy(I.rhs(A.n, 4, 13)).cuda()
+    with bk.Operator(A) as op:
+        rg = op.solve(B, tol=1e-8, maxit=500, variant="pipelined_merged")
+        bk.set_profiling(op.handle, True)
+        rp = op.solve(B, tol=1e-8, maxit=500, variant="pipelined_merged")
+        times = bk.kernel_times(op.handle)
+        bk.set_profiling(op.handle, False)
+    assert torch.equal(rg.X, rp.X)
+    assert "merged_pszqy_3dots" in times and times["merged_pszqy_3dots"][0] == int(rp.iters.max())
+
+
+def test_bad_csr_rejected(bk, cuda):
+    rowptr = np.array([0, 2, 1], dtype=np.int32)
+    with pytest.raises(bk.BicgkError):
+        bk.csr_create(rowptr, np.array([0, 1], dtype=np.int32), np.ones(2))
+    with pytest.raises(bk.BicgkError):
+        bk.csr_create(np.array([0, 1, 2], dtype=np.int32), np.array([0, 5], dtype=np.int32), np.ones(2))

@@ -175,6 +175,17 @@ def test_recurrence_residual_is_true_residual(variant, m):
     assert np.all(gap <= 200 * m * U * scale), (gap, scale)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_recurrence_residual_at_convergence(variant):
+    """The residual returned with a converged column is b - A x of the returned iterate."""
+    A = I.convdiff7(9, peclet=True)
+    B = I.rhs(A.n, 2, 32)
+    r = oracle.solve(A, B, tol=1e-10, maxit=500, variant=variant)
+    assert np.all(r.status == oracle.CONVERGED)
+    gap = np.linalg.norm(r.R - (B - _sp(A) @ r.X), axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(gap < 0.1 * 1e-10), gap   # rounding drift only, below the tolerance
+
+
 def test_columns_are_independent_bitwise():
     A = I.convdiff7(8, peclet=True)
     B = I.rhs(A.n, 4, 2)
