@@ -151,29 +151,34 @@ def kernel_algorithmic(name: str, n: int, nnz: int, k: int):
     return (r + w) * vec, fl * n * k
 
 
-def recorded_traffic():
-    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if current.
+KERNEL_SOURCES = {"spmm": ("bicgk_dev.cuh", "bicgk_spmm.cu"), "vec": ("bicgk_dev.cuh", "bicgk_vec.cu")}
 
-    The summary records the hash of the CUDA sources it was taken on; a changed
-    kernel source makes the figure stale (reported as null).
+
+def source_hash(kind: str) -> str:
+    """Hash of the CUDA sources a kernel class is compiled from (its ncu figures go stale with them)."""
+    hsh = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        hsh.update(open(os.path.join(ROOT, "paper_1907_12874_gb300", "csrc", f), "rb").read())
+    return hsh.hexdigest()[:12]
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes from the committed ncu summary, for kernels whose source is unchanged.
+
+    Rows of profiles/ncu_dram_traffic.md: | kernel | k | bytes per launch at the bench size | source hash |.
     """
     path = os.path.join(ROOT, "profiles", "ncu_dram_traffic.md")
     if not os.path.exists(path):
         return {}
-    h = source_hash()
     out = {}
     for line in open(path):
         m = re.match(r"\|\s*([a-z0-9_]+)\s*\|\s*(\d+)\s*\|\s*([0-9.e+]+)\s*\|\s*([0-9a-f]{12})\s*\|", line)
-        if m and m.group(4) == h:
+        if not m:
+            continue
+        kind = "spmm" if m.group(1).startswith("spmm") else "vec"
+        if m.group(4) == source_hash(kind):
             out[(m.group(1), int(m.group(2)))] = float(m.group(3))
     return out
-
-
-def source_hash() -> str:
-    hsh = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1907_12874_gb300", "csrc", "*"))):
-        hsh.update(open(p, "rb").read())
-    return hsh.hexdigest()[:12]
 
 
 def cpu_oracle_rate(A, B, variant, cols: int, iters: int):
