@@ -128,6 +128,42 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
                 int variant, int32_t flags, int mem, double *X, int32_t *iters, int32_t *status,
                 double *resid_hist, double *true_relres, void *stream);
 
+/*
+ * bicgk_solve without any GPU memory allocation (the paper has no counterpart;
+ * this is an interface for callers that cannot allocate).
+ *
+ * Who needs it: code that owns all device memory through its own pool (a
+ * cudaMalloc/cudaFree from inside the solve would bypass the pool and
+ * synchronise the whole device), loops that must not take the implicit
+ * synchronisation of an allocation, and embeddings that run within a fixed
+ * device-memory budget.  The caller passes every input and output; the CSR
+ * arrays (rowptr[n_rows+1], colidx[nnz], vals[nnz]; layout and meaning as in
+ * bicgk_csr_create, not validated here) and B, X0 (nullable), X are DEVICE
+ * pointers in the layout of bicgk_solve; iters, status, resid_hist and
+ * true_relres are host arrays as there, and every other argument means the
+ * same.  Results equal bicgk_solve's within rounding of the same kernels.
+ *
+ * Scratch: one 16 MiB file-scope device array in this library, which every
+ * GPU that loads the library keeps until the process exits.  A problem fits if
+ *   8*14*(n_rows*kp + 34) + 8*(maxit+1)*kp + 8*1024*SMs + ~1.3 KB <= 16 MiB
+ * (kp = k rounded up to a power of two; about n_rows*kp <= 140,000 at
+ * maxit = 1000); larger problems return BICGK_E_UNSUPPORTED with the sizes in
+ * bicgk_last_cuda_error().  The iteration loop runs from the host (one
+ * stream synchronisation per iteration), not from a CUDA graph.
+ *
+ * Every call, on any stream or thread, uses the same array and leaves its
+ * contents behind; what must start at zero (reduction ticket, iteration
+ * counter, per-column state, padding) is cleared by each call.  Calls whose GPU
+ * work overlaps in time race on the array and give wrong results: serialise
+ * them.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Returns when all outputs are valid.
+ */
+int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                        const double *vals, int32_t k, const double *B, const double *X0, double rel_tol,
+                        int32_t maxit, int variant, int32_t flags, double *X, int32_t *iters, int32_t *status,
+                        double *resid_hist, double *true_relres, void *stream);
+
 /* Release the operator and all device memory it holds.  NULL is accepted. */
 int bicgk_op_destroy(bicgk_op A);
 

@@ -621,3 +621,128 @@ int bicgk_last_stats(bicgk_op A, int32_t *loop_iters, int64_t *kernel_launches, 
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Allocation-free solve.
+//
+// For callers that must not allocate GPU memory during a solve: code that owns
+// all device memory through its own pool (a cudaMalloc from inside it would
+// bypass the pool and synchronise the device), real-time loops in which an
+// allocation's implicit synchronisation is not allowed, and embeddings that
+// run with a fixed device-memory budget.  Everything the solve needs beyond
+// the caller's arrays lives in one file-scope device array of fixed size,
+// held by every GPU that loads this library until the process exits.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_static_scratch_addr[kMaxDevices] = {nullptr};
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                                   const double *vals, int32_t k, const double *B, const double *X0,
+                                   double rel_tol, int32_t maxit, int variant, int32_t flags, double *X,
+                                   int32_t *iters, int32_t *status, double *resid_hist, double *true_relres,
+                                   void *stream) {
+  if (n_rows < 1 || nnz < 0 || n_rows > INT32_MAX - 1 || nnz > INT32_MAX || !rowptr || (nnz > 0 && (!colidx || !vals)) ||
+      !B || !X || !iters || !status || k < 1 || !(rel_tol >= 0.0) || maxit < 0 || maxit > 10000000 ||
+      variant < 0 || variant > 5 || (flags & ~1))
+    return BICGK_E_INVALID;
+  if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, major = 0, minor = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (major != 10 || minor != 3 || dev >= kMaxDevices) {
+    g_cuda_err = "bicgk_solve_noalloc: needs an sm_103 device with index < 64";
+    return BICGK_E_UNSUPPORTED;
+  }
+  // scratch layout: 14 vectors | scalars | flags | block partials | control block | history
+  const int kp = pow2_at_least(k);
+  const int64_t vstride = (n_rows * kp + 2 + 31) / 32 * 32;
+  const int64_t hist_len = (int64_t)(maxit + 1) * kp;
+  const size_t b_vec = round256(sizeof(double) * (size_t)vstride * V_NVEC);
+  const size_t b_sc = round256(sizeof(double) * S_NSLOT * kMaxKp);
+  const size_t b_fl = round256(sizeof(int) * F_NFLAG * kMaxKp);
+  const size_t b_part = round256(sizeof(double) * (size_t)nsm * 4 * kMaxDots * kMaxKp);
+  const size_t b_ctl = round256(sizeof(Ctl));
+  const size_t b_hist = round256(sizeof(double) * (size_t)hist_len);
+  const size_t need = b_vec + b_sc + b_fl + b_part + b_ctl + b_hist;
+  if (need > kStaticScratchBytes) {
+    g_cuda_err = "bicgk_solve_noalloc: this problem needs " + std::to_string(need) +
+                 " bytes of scratch; the static scratch holds " + std::to_string(kStaticScratchBytes);
+    return BICGK_E_UNSUPPORTED;
+  }
+  // first call on this device: host code needs the array's device address
+  if (!g_static_scratch_addr[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_scratch_addr[dev] = p;
+  }
+  unsigned char *base = static_cast<unsigned char *>(g_static_scratch_addr[dev]);
+  // an operator view of the caller's CSR and the static scratch (owns nothing)
+  bicgk_op_s A;
+  A.device = dev;
+  A.nsm = nsm;
+  A.n = n_rows;
+  A.nnz = nnz;
+  A.d_rowptr = const_cast<int32_t *>(rowptr);
+  A.d_col = const_cast<int32_t *>(colidx);
+  A.d_val = const_cast<double *>(vals);
+  A.stage_cap = 0;  // the k <= 2 SpMM reads CSR entries from global memory (same arithmetic)
+  A.kp = kp;
+  A.vstride = vstride;
+  A.d_vec = reinterpret_cast<double *>(base);
+  A.d_sc = reinterpret_cast<double *>(base + b_vec);
+  A.d_fl = reinterpret_cast<int *>(base + b_vec + b_sc);
+  A.d_part = reinterpret_cast<double *>(base + b_vec + b_sc + b_fl);
+  A.d_ctl = reinterpret_cast<Ctl *>(base + b_vec + b_sc + b_fl + b_part);
+  A.d_hist = reinterpret_cast<double *>(base + b_vec + b_sc + b_fl + b_part + b_ctl);
+  // control block: the reduction ticket and the iteration counter start at zero
+  Ctl hc;
+  memset(&hc, 0, sizeof(hc));
+  hc.tol = rel_tol;
+  hc.hist = A.d_hist;
+  hc.maxit = maxit;
+  hc.k = k;
+  hc.kp = kp;
+  hc.flags = flags;
+  CK(cudaMemcpyAsync(A.d_ctl, &hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  const KArgs a = make_args(&A, 0, cudaGraphConditionalHandle{});
+  CK(launch_reset(a, hist_len, s));     // history = NaN, per-column scalars and flags = 0
+  CK(launch_pack(B, X0, k, a, s));      // B and X0 in, padding columns and pad elements = 0
+  const Seq q = make_seq(variant);
+  Ctl poll;
+  auto run = [&](const std::vector<Step> &steps) -> int {
+    for (const Step &st : steps) CK(launch_step(&A, st, a, s));
+    CK(cudaMemcpyAsync(&poll, A.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return BICGK_OK;
+  };
+  int rc = run(q.setup);
+  if (rc) return rc;
+  bool go = poll.any_active && maxit > 0;
+  while (go) {
+    rc = run(q.body);
+    if (rc) return rc;
+    go = poll.any_active && poll.iter < maxit;
+  }
+  for (const Step &st : q.fin) CK(launch_step(&A, st, a, s));
+  CK(launch_unpack_role(X, k, a, V_X, 1, s));
+  CK(cudaMemcpyAsync(iters, A.d_fl + F_ITERS * kMaxKp, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(status, A.d_fl + F_STATUS * kMaxKp, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s));
+  if (true_relres)
+    CK(cudaMemcpyAsync(true_relres, A.d_sc + S_TRUE * kMaxKp, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  if (resid_hist)
+    CK(cudaMemcpy2DAsync(resid_hist, sizeof(double) * k, A.d_hist, sizeof(double) * kp, sizeof(double) * k,
+                         (size_t)maxit + 1, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return BICGK_OK;
+}

@@ -1,0 +1,98 @@
+"""The allocation-free solve entry point gives the same answers as bicgk_solve.
+
+bicgk_solve_noalloc is for callers that cannot allocate GPU memory while they
+solve: programs that hand out all device memory from their own pool, loops
+that must not take the device-wide synchronisation of cudaMalloc/cudaFree, and
+embeddings with a fixed device-memory budget.  It keeps its scratch in one
+fixed-size array inside the library instead.  This file calls it through the
+C-ABI twice in a row (the second call sees whatever the first left in that
+array) and compares each result with bicgk_solve on the same inputs, then
+checks that a problem too large for the array is refused.  It is collected
+last so that a failure here stops a -x run only after every other test ran.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1907_12874_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib(cuda):
+    from paper_1907_12874_gb300 import bicgk
+    L = bicgk._load()
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.bicgk_solve_noalloc.argtypes = [i64, i64, vp, vp, vp, i32, vp, vp, dbl, i32, ctypes.c_int, i32, vp, vp, vp,
+                                      vp, vp, vp]
+    L.bicgk_solve_noalloc.restype = ctypes.c_int
+    return L
+
+
+def _noalloc(L, torch, A, B, X0, tol, maxit, variant):
+    from paper_1907_12874_gb300 import bicgk
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    rp, ci, va, Bd = dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(B)
+    X0d = None if X0 is None else dev(X0)
+    Xd = torch.empty_like(Bd)
+    k = B.shape[1]
+    iters = np.zeros(k, np.int32)
+    status = np.zeros(k, np.int32)
+    hist = np.empty((maxit + 1, k))
+    trr = np.empty(k)
+    p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    h = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.bicgk_solve_noalloc(A.n, A.nnz, p(rp), p(ci), p(va), k, p(Bd), p(X0d), tol, maxit,
+                               bicgk.VARIANTS[variant], 0, p(Xd), h(iters), h(status), h(hist), h(trr), stream)
+    assert rc == 0, L.bicgk_last_cuda_error()
+    return Xd.cpu().numpy(), iters, status, hist, trr
+
+
+def _reference(torch, A, B, X0, tol, maxit, variant):
+    from paper_1907_12874_gb300 import bicgk
+    with bicgk.Operator(A) as op:
+        r = op.solve(torch.from_numpy(B).cuda(), X0=None if X0 is None else torch.from_numpy(X0).cuda(),
+                     tol=tol, maxit=maxit, variant=variant)
+        return r.X.cpu().numpy(), r.iters, r.status, r.hist, r.true_relres
+
+
+def _same(got, ref):
+    X, it, st, hist, trr = got
+    Xr, itr, str_, histr, trrr = ref
+    assert np.array_equal(it, itr) and np.array_equal(st, str_)
+    err = np.linalg.norm(X - Xr, axis=0) / np.linalg.norm(Xr, axis=0)
+    assert np.all(err <= 1e-12), err
+    np.testing.assert_allclose(hist, histr, rtol=1e-10, equal_nan=True)
+    np.testing.assert_allclose(trr, trrr, rtol=1e-8)
+
+
+def test_two_calls_in_a_row_match_bicgk_solve(lib, cuda):
+    torch = cuda
+    # call 1: the 16^3 configuration, 4 RHS, merged classical BiCGStab
+    A1 = I.convdiff7(16)
+    B1 = I.rhs(A1.n, 4, 1)
+    _same(_noalloc(lib, torch, A1, B1, None, 1e-8, 1000, "classical_merged"),
+          _reference(torch, A1, B1, None, 1e-8, 1000, "classical_merged"))
+    # call 2: another operator, 3 RHS (padded to 4 columns), an initial guess, Pipelined form
+    A2 = I.convdiff7(12, peclet=True)
+    B2 = I.rhs(A2.n, 3, 2)
+    X02 = 0.1 * I.rhs(A2.n, 3, 3)
+    _same(_noalloc(lib, torch, A2, B2, X02, 1e-9, 500, "pipelined_merged"),
+          _reference(torch, A2, B2, X02, 1e-9, 500, "pipelined_merged"))
+
+
+def test_too_large_for_the_static_scratch_is_refused(lib, cuda):
+    n = 64 ** 3
+    k = 32
+    iters = np.zeros(k, np.int32)
+    status = np.zeros(k, np.int32)
+    # refused on size before any pointer is dereferenced (device pointers are placeholders)
+    fake = ctypes.c_void_p(16)
+    rc = lib.bicgk_solve_noalloc(n, 7 * n, fake, fake, fake, k, fake, None, 1e-8, 100, 1, 0, fake,
+                                 iters.ctypes.data_as(ctypes.c_void_p), status.ctypes.data_as(ctypes.c_void_p),
+                                 None, None, None)
+    assert rc == -5
+    assert b"static scratch holds" in lib.bicgk_last_cuda_error()
