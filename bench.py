@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--sweep", action="store_true", help="also time every variant at k = 1..32")
+    p.add_argument("--no-mixed", action="store_true",
+                   help="skip the mixed-precision comparison (27-point 128^3, k = 32, rel tol 1e-10)")
+    p.add_argument("--mixed-grid", type=int, default=128)
     p.add_argument("--eager", action="store_true",
                    help="run every solve in the library's host-loop mode (same kernels, one launch at a time, "
                         "CUDA events around each) instead of the CUDA graph; profilers cannot see kernels inside "
@@ -267,6 +270,46 @@ def workload_config(args, A):
             "parallelism": "one independent k-RHS system per GPU"}
 
 
+def mixed_section(args, bicgk, inputs, torch, dev):
+    """27-point perturbed stencil, k = 32, rel. tol 1e-10: mixed-precision refinement vs FP64.
+
+    Both solves run to the same FP64 true-residual tolerance on the same GPU; the time is the
+    whole solve (CUDA events), the figure of merit the time to solution.
+    """
+    n = args.mixed_grid
+    k = 32
+    A = inputs.perturbed27(n, seed=7)
+    B = torch.from_numpy(inputs.rhs(A.n, k, 3)).to(dev)
+    res = {"workload": f"perturbed27 {n}^3 (off-diagonals -U[0.5,1.5], diag = sum|off| + 1), k={k}, "
+                       f"rel tol 1e-10", "n_rows": A.n, "nnz": A.nnz}
+
+    def timed_solve(fn, steps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, r
+
+    with bicgk.Operator(A) as op64, bicgk.Operator(A) as opm:
+        X = torch.empty_like(B)
+        ms64, r64 = timed_solve(lambda: op64.solve(B, X=X, tol=1e-10, maxit=5000, want_hist=False))
+        msm, rm = timed_solve(lambda: opm.solve_mixed(B, X=X, tol=1e-10, max_outer=20, inner_tol=1e-5,
+                                                      max_inner=5000, want_hist=False))
+    res.update({
+        "fp64_ms": ms64, "fp64_iters_per_rhs": float(r64.iters.mean()),
+        "fp64_max_true_relres": float(r64.true_relres.max()), "fp64_converged": bool((r64.status == 0).all()),
+        "mixed_ms": msm, "mixed_outer_passes": int(rm.outer_iters.max()),
+        "mixed_fp32_iters_per_rhs": float(rm.inner_iters.mean()),
+        "mixed_max_true_relres": float(rm.true_relres.max()), "mixed_converged": bool((rm.status == 0).all()),
+        "speedup_vs_fp64": ms64 / msm,
+    })
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -401,6 +444,10 @@ def main():
                 msk, itsk, _, _, _ = timed(v, 2, 1, B=Bk, X=Xk)
                 sweep[f"{v}/k{k}"] = itsk / (msk / 1e3)
         out["sweep_rhs_iterations_per_s"] = sweep
+
+    # mixed precision (FP32 inner solves in FP64 refinement) vs FP64 on the same GPU
+    if not args.no_mixed and rank == 0:
+        out["mixed_precision"] = mixed_section(args, bicgk, inputs, torch, dev)
 
     # CPU oracle on the host cores (rank 0, N = 1 only)
     if not args.no_cpu and rank == 0 and world == 1:

@@ -129,6 +129,31 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
                 double *resid_hist, double *true_relres, void *stream);
 
 /*
+ * Mixed-precision solve of A X = B: FP64 iterative refinement around FP32
+ * BiCGStab inner solves (no counterpart in the paper, which runs in FP64; the
+ * inner solver is the paper's merged BiCGStab, Algorithm 2).
+ *   pass j (0 <= j <= max_outer): r = b - A x in FP64 (FP64 matrix); column c
+ *   stops when ||r_c|| < rel_tol*||b_c|| (status CONVERGED) or at j = max_outer
+ *   (MAXIT); otherwise A d = fl32(r) is solved with FP32 matrix values and FP32
+ *   vectors (elementwise updates in FP32; dot products with exact FP32 products
+ *   summed in float-float per thread and in FP64 across threads; scalars alpha,
+ *   omega, rho, beta in FP64) from d = 0 until its residual estimate falls below
+ *   inner_tol*||fl32(r)|| or max_inner iterations, and x += d in FP64.
+ *   B, X0 (nullable), X: n_rows*k FP64 in space `mem`, as for bicgk_solve.
+ *   outer_iters[k]: refinement passes that updated x_c; inner_iters[k]: FP32
+ *   iterations summed over the passes; status[k]: bicgk_rhs_status of the
+ *   refinement; resid_hist[(max_outer+1)*k] (nullable): ||b_c - A x_c|| before
+ *   pass j (FP64), NaN after column c stopped; true_relres[k] (nullable): the
+ *   final ||b_c - A x_c|| / ||b_c||.
+ *   0 <= max_outer <= 1000, 1 <= max_inner, 0 < inner_tol < 1.
+ * Runs on `stream` and returns when all outputs are valid.
+ */
+int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, double rel_tol, int32_t max_outer,
+                      double inner_tol, int32_t max_inner, int mem, double *X, int32_t *outer_iters,
+                      int32_t *inner_iters, int32_t *status, double *resid_hist, double *true_relres,
+                      void *stream);
+
+/*
  * bicgk_solve without any GPU memory allocation (the paper has no counterpart;
  * this is an interface for callers that cannot allocate).
  *
@@ -163,6 +188,28 @@ int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *rowptr, cons
                         const double *vals, int32_t k, const double *B, const double *X0, double rel_tol,
                         int32_t maxit, int variant, int32_t flags, double *X, int32_t *iters, int32_t *status,
                         double *resid_hist, double *true_relres, void *stream);
+
+/* Launch-shape options of an operator (bicgk_set_option); 0 restores the default. */
+enum bicgk_option {
+  BICGK_OPT_VEC_BLOCKS_PER_SM = 1, /* blocks of 512 threads per SM for the streaming kernels (0..4;
+                                      default: the occupancy maximum, 2)                      */
+  BICGK_OPT_SPMM_BLOCKS_PER_SM = 2, /* blocks of 256 threads per SM for the SpMM (0..32; default:
+                                      the occupancy maximum)                                   */
+  BICGK_OPT_RHS_GROUPS = 3          /* 0: k >= 16 is solved as two column groups running
+                                      concurrently on two internal streams (default); 1: one
+                                      group.  Profiling mode always uses one group.            */
+};
+
+/*
+ * Set a launch-shape option of operator A (no counterpart in the paper: GPU
+ * launch configuration).  Fewer blocks per SM leave room for kernels of other
+ * streams to run alongside; two RHS groups let the FP64-bound SpMM of one group
+ * overlap the bandwidth-bound vector kernels of the other (the columns never
+ * interact, so every column's iterates are those of a solve of its group).
+ * Cached graphs are dropped and re-captured on the next solve.  Returns
+ * BICGK_E_INVALID for an unknown option or value.
+ */
+int bicgk_set_option(bicgk_op A, int option, int64_t value);
 
 /* Release the operator and all device memory it holds.  NULL is accepted. */
 int bicgk_op_destroy(bicgk_op A);

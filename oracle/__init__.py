@@ -64,6 +64,9 @@ def _load():
             lib.oracle_spmm.argtypes = [i64, vp, vp, vp, i32, vp, vp]
             lib.oracle_spmm.restype = ctypes.c_int
             lib.oracle_threads.restype = ctypes.c_int
+            lib.oracle_solve_mixed.argtypes = [i64, vp, vp, vp, i32, vp, vp, dbl, i32, dbl, i32, vp, vp, vp, vp, vp,
+                                               vp]
+            lib.oracle_solve_mixed.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -118,3 +121,31 @@ def solve(A, B: np.ndarray, X0=None, tol: float = 1e-8, maxit: int = 1000,
     if rc != 0:
         raise ValueError(f"oracle_solve: bad argument (rc={rc})")
     return Result(X, R, iters, status, hist, trr, traffic)
+
+
+class MixedResult:
+    def __init__(self, X, outer_iters, inner_iters, status, hist, true_relres):
+        self.X, self.outer_iters, self.inner_iters = X, outer_iters, inner_iters
+        self.status, self.hist, self.true_relres = status, hist, true_relres
+
+
+def solve_mixed(A, B: np.ndarray, X0=None, tol: float = 1e-10, max_outer: int = 20, inner_tol: float = 1e-5,
+                max_inner: int = 2000) -> MixedResult:
+    """FP64 iterative refinement around FP32 inner solves (Algorithm 2 in FP32 storage)."""
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B.reshape(-1, 1)
+    n, k = B.shape
+    X0c = None if X0 is None else np.ascontiguousarray(np.asarray(X0, dtype=np.float64).reshape(n, k))
+    X = np.empty((n, k))
+    outer = np.zeros(k, dtype=np.int32)
+    inner = np.zeros(k, dtype=np.int32)
+    status = np.zeros(k, dtype=np.int32)
+    hist = np.empty((max_outer + 1, k))
+    trr = np.empty(k)
+    rc = _load().oracle_solve_mixed(n, _ptr(A.rowptr), _ptr(A.colidx), _ptr(A.vals), k, _ptr(B), _ptr(X0c),
+                                    float(tol), int(max_outer), float(inner_tol), int(max_inner), _ptr(X),
+                                    _ptr(outer), _ptr(inner), _ptr(status), _ptr(hist), _ptr(trr))
+    if rc != 0:
+        raise ValueError(f"oracle_solve_mixed: bad argument (rc={rc})")
+    return MixedResult(X, outer, inner, status, hist, trr)

@@ -600,6 +600,151 @@ int oracle_solve(int variant, int64_t n, const int32_t *rowptr, const int32_t *c
   return 0;
 }
 
+/* ---------------- mixed precision: FP64 refinement around FP32 inner solves ----------------
+ *
+ * Not in the paper (its solvers run in FP64).  The inner solver is Algorithm 2 with FP32
+ * vectors and FP32 matrix values: every vector update is FP32 arithmetic with the scalars
+ * rounded to FP32; the dot products are formed in FP64 (a product of two floats is exact in
+ * double) with the compensated sum of dot(); the scalar recurrences and the stop rules
+ * (R1-R6) are FP64, as in classical_merged().  The outer loop is iterative refinement in
+ * FP64: r = b - A x, stop when (r,r) < eps^2 (R1) or after max_outer passes, else solve
+ * A d = fl32(r) from d = 0 to the relative tolerance inner_tol and add d to x. */
+
+typedef struct {
+  float *p;
+  int64_t s;
+} fcol_t;
+
+static void spmv32(const csr_t *A, const float *vals32, fcol_t x, fcol_t y) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < A->n; ++i) {
+    float acc = 0.0f;
+    for (int32_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) acc += vals32[e] * AT(x, A->colidx[e]);
+    AT(y, i) = acc;
+  }
+}
+
+static double dot32(const csr_t *A, fcol_t x, fcol_t y) {
+  double sum = 0.0, comp = 0.0;
+  for (int64_t i = 0; i < A->n; ++i) {
+    double p = (double)AT(x, i) * (double)AT(y, i); /* exact */
+    double t = sum + p;
+    if (fabs(sum) >= fabs(p))
+      comp += (sum - t) + p;
+    else
+      comp += (p - t) + sum;
+    sum = t;
+  }
+  return sum + comp;
+}
+
+/* Algorithm 2 in FP32 storage for A d = b32, d_0 = 0.  Returns the iterations formed. */
+static int inner_merged32(const csr_t *A, const float *vals32, fcol_t b, fcol_t d, fcol_t *w, double tol,
+                          int maxit) {
+  fcol_t r = w[0], r0 = w[1], p = w[2], v = w[3], s = w[4], t = w[5];
+  const int64_t n = A->n;
+  for (int64_t i = 0; i < n; ++i) {
+    AT(d, i) = 0.0f;
+    AT(r, i) = AT(b, i);
+    AT(r0, i) = AT(b, i);
+    AT(p, i) = AT(b, i);
+  }
+  double bn2 = dot32(A, b, b), rho = dot32(A, r, r);
+  double eps2 = tol * tol * bn2;
+  if (bn2 == 0.0 || !finite(rho) || rho < eps2) return 0;
+  int iters = 0;
+  for (int j = 0; j < maxit; ++j) {
+    spmv32(A, vals32, p, v);
+    double delta = dot32(A, v, r0);
+    if (!finite(delta) || delta == 0.0) return iters;
+    double alpha = rho / delta;
+    if (!finite(alpha)) return iters;
+    float af = (float)alpha;
+    for (int64_t i = 0; i < n; ++i) AT(s, i) = AT(r, i) - af * AT(v, i);
+    spmv32(A, vals32, s, t);
+    double phi = dot32(A, t, s), psi = dot32(A, t, t), theta = dot32(A, s, s);
+    if (!finite(phi) || !finite(psi) || !finite(theta)) return iters;
+    double omega = psi == 0.0 ? 0.0 : phi / psi;
+    if (!finite(omega)) return iters;
+    float of = (float)omega;
+    for (int64_t i = 0; i < n; ++i) {
+      float si = AT(s, i);
+      AT(d, i) = AT(d, i) + af * AT(p, i) + of * si;
+      AT(r, i) = si - of * AT(t, i);
+    }
+    iters = j + 1;
+    double est = theta - omega * phi;
+    if (!finite(est) || est < eps2) return iters;
+    double rho1 = dot32(A, r, r0);
+    if (!finite(rho1) || rho == 0.0 || omega == 0.0) return iters;
+    double beta = (rho1 / rho) * (alpha / omega);
+    if (!finite(beta)) return iters;
+    float bf = (float)beta;
+    for (int64_t i = 0; i < n; ++i) AT(p, i) = AT(r, i) + bf * (AT(p, i) - of * AT(v, i));
+    rho = rho1;
+  }
+  return iters;
+}
+
+/* Mixed-precision solve, column by column.  hist (nullable): (max_outer+1) x k, entry (j, c) =
+ * ||b - A x|| before pass j, NaN after the column stopped. */
+int oracle_solve_mixed(int64_t n, const int32_t *rowptr, const int32_t *colidx, const double *vals, int32_t k,
+                       const double *B, const double *X0, double tol, int32_t max_outer, double inner_tol,
+                       int32_t max_inner, double *X, int32_t *outer_iters, int32_t *inner_iters, int32_t *status,
+                       double *hist, double *true_relres) {
+  if (n < 1 || k < 1 || max_outer < 0 || max_inner < 1 || !(tol >= 0.0) || !(inner_tol > 0.0)) return -1;
+  csr_t A = {n, rowptr, colidx, vals};
+  int64_t nnz = rowptr[n];
+  float *vals32 = (float *)malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+  double *r = (double *)malloc(sizeof(double) * (size_t)n);
+  double *ax = (double *)malloc(sizeof(double) * (size_t)n);
+  float *fw = (float *)malloc(sizeof(float) * (size_t)n * 8);
+  if (!vals32 || !r || !ax || !fw) { free(vals32); free(r); free(ax); free(fw); return -2; }
+  for (int64_t e = 0; e < nnz; ++e) vals32[e] = (float)vals[e];
+  for (int32_t c = 0; c < k; ++c) {
+    col_t b = {(double *)B + c, k}, x = {X + c, k};
+    col_t rc = {r, 1}, axc = {ax, 1};
+    fcol_t b32 = {fw, 1}, d32 = {fw + n, 1};
+    fcol_t w[6];
+    for (int q = 0; q < 6; ++q) w[q] = (fcol_t){fw + (size_t)(q + 2) * n, 1};
+    for (int64_t i = 0; i < n; ++i) AT(x, i) = X0 ? X0[i * k + c] : 0.0;
+    if (hist)
+      for (int32_t j = 0; j <= max_outer; ++j) hist[(int64_t)j * k + c] = NAN;
+    double bn2 = dot(&A, b, b), eps2 = tol * tol * bn2;
+    int st = ST_MAXIT, outer = 0, inner = 0;
+    double rr = 0.0;
+    if (bn2 == 0.0) {
+      set_zero(&A, x);
+      st = ST_CONVERGED;
+    } else if (!finite(bn2)) {
+      st = ST_NONFINITE;
+    } else {
+      for (int j = 0;; ++j) {
+        spmv(&A, x, axc);
+        for (int64_t i = 0; i < n; ++i) AT(rc, i) = AT(b, i) - AT(axc, i);
+        rr = dot(&A, rc, rc);
+        if (hist) hist[(int64_t)j * k + c] = hist_value(rr);
+        if (!finite(rr)) { st = ST_NONFINITE; break; }
+        if (rr < eps2) { st = ST_CONVERGED; break; }
+        if (j >= max_outer) { st = ST_MAXIT; break; }
+        outer = j + 1;
+        for (int64_t i = 0; i < n; ++i) AT(b32, i) = (float)AT(rc, i);
+        inner += inner_merged32(&A, vals32, b32, d32, w, inner_tol, max_inner);
+        for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + (double)AT(d32, i);
+      }
+    }
+    outer_iters[c] = outer;
+    inner_iters[c] = inner;
+    status[c] = st;
+    if (true_relres) true_relres[c] = bn2 == 0.0 ? 0.0 : sqrt(rr) / sqrt(bn2);
+  }
+  free(vals32);
+  free(r);
+  free(ax);
+  free(fw);
+  return 0;
+}
+
 /* Threads the OpenMP runtime will use for the parallel loops (1 without OpenMP). */
 #ifdef _OPENMP
 #include <omp.h>

@@ -58,11 +58,16 @@ def _load():
             lib.bicgk_strerror.restype = ctypes.c_char_p
             lib.bicgk_last_cuda_error.restype = ctypes.c_char_p
             lib.bicgk_version.restype = ctypes.c_char_p
+            lib.bicgk_solve_mixed.argtypes = [vp, i32, vp, vp, dbl, i32, dbl, i32, ctypes.c_int, vp, vp, vp, vp,
+                                              vp, vp, vp]
             lib.bicgk_set_profiling.argtypes = [vp, ctypes.c_int]
+            lib.bicgk_set_option.argtypes = [vp, ctypes.c_int, i64]
             lib.bicgk_kernel_times.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_char_p),
                                                ctypes.POINTER(i64), ctypes.POINTER(dbl)]
             lib.bicgk_last_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]
-            for f in ("bicgk_csr_create", "bicgk_spmm", "bicgk_solve", "bicgk_op_destroy", "bicgk_set_profiling",
+            for f in ("bicgk_csr_create", "bicgk_spmm", "bicgk_solve", "bicgk_solve_mixed", "bicgk_op_destroy",
+                      "bicgk_set_profiling",
+                      "bicgk_set_option",
                       "bicgk_kernel_times", "bicgk_last_stats"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
@@ -186,6 +191,54 @@ def solve(handle: int, B, X0=None, tol: float = 1e-8, maxit: int = 1000, variant
     return SolveResult(X, iters, status, hist, trr)
 
 
+OPT_VEC_BLOCKS_PER_SM, OPT_SPMM_BLOCKS_PER_SM, OPT_RHS_GROUPS = 1, 2, 3
+
+
+def set_option(handle: int, option: int, value: int) -> None:
+    """Launch-shape option of an operator (see bicgk_set_option in include/bicgk.h)."""
+    _check(_load().bicgk_set_option(ctypes.c_void_p(handle), int(option), int(value)), "bicgk_set_option")
+
+
+@dataclass
+class MixedResult:
+    X: object
+    outer_iters: np.ndarray
+    inner_iters: np.ndarray
+    status: np.ndarray
+    hist: np.ndarray | None
+    true_relres: np.ndarray | None
+
+
+def solve_mixed(handle: int, B, X0=None, tol: float = 1e-10, max_outer: int = 20, inner_tol: float = 1e-5,
+                max_inner: int = 2000, X=None, want_hist: bool = True, stream=None) -> MixedResult:
+    """FP64 iterative refinement around FP32 BiCGStab inner solves (bicgk_solve_mixed)."""
+    lib = _load()
+    dev = _is_device(B)
+    if _is_torch(B):
+        if not (B.is_contiguous() and str(B.dtype).endswith("float64")):
+            raise TypeError("B must be a contiguous float64 tensor")
+        if X is None:
+            import torch
+            X = torch.empty_like(B) if dev else torch.empty_like(B, pin_memory=True)
+    else:
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        if X0 is not None:
+            X0 = np.ascontiguousarray(X0, dtype=np.float64)
+        if X is None:
+            X = np.empty_like(B)
+    k = 1 if B.ndim == 1 else B.shape[1]
+    outer = np.zeros(k, dtype=np.int32)
+    inner = np.zeros(k, dtype=np.int32)
+    status = np.zeros(k, dtype=np.int32)
+    hist = np.empty((max_outer + 1, k)) if want_hist else None
+    trr = np.empty(k)
+    rc = lib.bicgk_solve_mixed(ctypes.c_void_p(handle), k, _ptr(B), _ptr(X0), float(tol), int(max_outer),
+                               float(inner_tol), int(max_inner), MEM_DEVICE if dev else MEM_HOST, _ptr(X),
+                               _ptr(outer), _ptr(inner), _ptr(status), _ptr(hist), _ptr(trr), _stream(stream))
+    _check(rc, "bicgk_solve_mixed")
+    return MixedResult(X, outer, inner, status, hist, trr)
+
+
 def set_profiling(handle: int, on: bool) -> None:
     _check(_load().bicgk_set_profiling(ctypes.c_void_p(handle), int(bool(on))), "bicgk_set_profiling")
 
@@ -222,6 +275,9 @@ class Operator:
 
     def solve(self, B, **kw) -> SolveResult:
         return solve(self.handle, B, **kw)
+
+    def solve_mixed(self, B, **kw) -> MixedResult:
+        return solve_mixed(self.handle, B, **kw)
 
     def spmm(self, X, Y=None, stream=None):
         if Y is None:

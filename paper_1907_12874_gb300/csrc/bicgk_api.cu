@@ -41,17 +41,30 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 // One step of a kernel sequence: a streaming op, or an SpMM between workspace roles.
 struct Step {
-  int spmm;  // 0: streaming op `op`; 1: y = A x; 2: y = b - A x
+  int spmm;  // 0: streaming op `op`; 1: y = A x; 2: y = b - A x; 3: y = A x in FP32
   int op;
   int x, y, b;
 };
 Step vec(int op) { return Step{0, op, 0, 0, 0}; }
 Step spmm(int x, int y) { return Step{1, -1, x, y, 0}; }
 Step resid(int x, int y, int b) { return Step{2, -1, x, y, b}; }
+Step spmm32(int x, int y) { return Step{3, -1, x, y, 0}; }
+
+
 
 struct Seq {
   std::vector<Step> setup, body, fin;
 };
+
+// FP32 inner solve of the mixed-precision refinement: merged classical BiCGStab (Algorithm 2)
+// from d_0 = 0, so r_0 = b and the set-up needs no SpMM.
+Seq make_inner32_seq() {
+  Seq q;
+  q.setup = {vec(OP32_SETUP)};
+  q.body = {spmm32(V_P, V_V), vec(OP32_DELTA), vec(OP32_UPD_S), spmm32(V_S, V_T), vec(OP32_G1), vec(OP32_G3),
+            vec(OP32_UPD_P)};
+  return q;
+}
 
 // Kernel sequences of the six forms (one Step = one kernel launch).
 Seq make_seq(int variant) {
@@ -111,6 +124,31 @@ struct ProfEntry {
   double ms = 0.0;
 };
 
+constexpr int kMaxGroups = 2;     // column groups solved concurrently
+constexpr int kSplitMinK = 16;    // smallest k that is split into two groups
+
+// Solver state of one group of columns: N x kp vectors, per-column scalars and flags, block
+// partials, control block, history, the group's stream and its captured graphs.
+struct Workspace {
+  int ebytes = 8;            // bytes per vector element (8: FP64, 4: FP32)
+  int kp = 0;
+  int64_t vstride = 0;       // doubles between consecutive workspace vectors
+  double *d_vec = nullptr;
+  double *d_sc = nullptr;
+  int *d_fl = nullptr;
+  double *d_part = nullptr;
+  Ctl *d_ctl = nullptr;
+  Ctl *h_ctl = nullptr;      // pinned
+  double *d_hist = nullptr;
+  int64_t hist_cap = 0;      // doubles
+  double *h_hist = nullptr;  // pinned, hist_cap doubles
+  int *h_fl = nullptr;       // pinned, F_NFLAG * kMaxKp
+  double *h_sc = nullptr;    // pinned, S_NSLOT * kMaxKp
+  cudaStream_t stream = nullptr;  // the group's own stream (split solves)
+  cudaEvent_t done = nullptr;
+  std::map<int, GraphEntry> graphs;  // per variant, for this kp
+};
+
 }  // namespace
 
 struct bicgk_op_s {
@@ -119,47 +157,43 @@ struct bicgk_op_s {
   int64_t n = 0, nnz = 0;
   int32_t *d_rowptr = nullptr, *d_col = nullptr;
   double *d_val = nullptr;
+  float *d_val32 = nullptr;  // FP32 copy of the values (mixed-precision solves; made on first use)
   int stage_cap = 0;
-  // workspace for one kp
-  int kp = 0;
-  int64_t vstride = 0;  // doubles between consecutive workspace vectors
-  double *d_vec = nullptr;
-  double *d_sc = nullptr;
-  int *d_fl = nullptr;
-  double *d_part = nullptr;
-  Ctl *d_ctl = nullptr;
-  Ctl *h_ctl = nullptr;       // pinned
-  double *d_hist = nullptr;
-  int64_t hist_cap = 0;       // doubles
-  double *h_hist = nullptr;   // pinned, hist_cap doubles
-  int *h_fl = nullptr;        // pinned, F_NFLAG * kMaxKp
-  double *h_sc = nullptr;     // pinned, S_NSLOT * kMaxKp
+  Workspace ws[kMaxGroups];
+  Workspace ws32;            // FP32 inner-solve workspace of the mixed-precision refinement
   double *d_stage[2] = {nullptr, nullptr};  // caller-layout staging for host-memory calls
   int64_t stage_elems = 0;
   cudaStream_t cap_stream = nullptr;
-  std::map<std::pair<int, int>, GraphEntry> graphs;
+  cudaEvent_t fork = nullptr;
   // profiling
   bool profiling = false;
   std::map<std::string, ProfEntry> prof;
   std::vector<std::string> prof_names;
   std::vector<cudaEvent_t> ev;
+  // options (0 = default)
+  int opt_vec_blocks = 0;
+  int opt_spmm_blocks = 0;
+  int opt_groups = 0;
   // last solve statistics
   int32_t last_loop_iters = 0;
   int64_t last_launches = 0;
   int32_t last_kernels_per_iter = 0;
+  int32_t last_groups = 0;
 };
 
 namespace {
 
-KArgs make_args(bicgk_op A, int use_cond, cudaGraphConditionalHandle h) {
+KArgs make_args(bicgk_op A, const Workspace &W, int use_cond, cudaGraphConditionalHandle h,
+                const int *ext_act = nullptr) {
   KArgs a;
-  for (int r = 0; r < V_NVEC; ++r) a.v[r] = A->d_vec + (int64_t)r * A->vstride;
-  a.sc = A->d_sc;
-  a.fl = A->d_fl;
-  a.part = A->d_part;
-  a.ctl = A->d_ctl;
+  a.ext_act = ext_act;
+  for (int r = 0; r < V_NVEC; ++r) a.v[r] = W.d_vec + (int64_t)r * W.vstride;
+  a.sc = W.d_sc;
+  a.fl = W.d_fl;
+  a.part = W.d_part;
+  a.ctl = W.d_ctl;
   a.n = A->n;
-  a.kp = A->kp;
+  a.kp = W.kp;
   a.use_cond = use_cond;
   a.cond = h;
   return a;
@@ -168,11 +202,14 @@ KArgs make_args(bicgk_op A, int use_cond, cudaGraphConditionalHandle h) {
 int vec_grid(bicgk_op A, int op) {
   int nb = vec_blocks_per_sm(op);
   if (nb > 4) nb = 4;
+  if (A->opt_vec_blocks > 0 && A->opt_vec_blocks < nb) nb = A->opt_vec_blocks;
   return A->nsm * nb;
 }
 
 int spmm_grid(bicgk_op A, int kp, int mode) {
-  return A->nsm * spmm_blocks_per_sm(kp, mode, A->stage_cap);
+  int nb = spmm_blocks_per_sm(kp, mode, A->stage_cap);
+  if (A->opt_spmm_blocks > 0 && A->opt_spmm_blocks < nb) nb = A->opt_spmm_blocks;
+  return A->nsm * nb;
 }
 
 cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t s) {
@@ -185,9 +222,13 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
   sa.y = a.v[st.y];
   sa.b = st.spmm == 2 ? a.v[st.b] : nullptr;
   sa.n = A->n;
-  sa.stage_cap = A->kp <= 2 ? A->stage_cap : 0;
+  sa.stage_cap = a.kp <= 2 ? A->stage_cap : 0;
+  if (st.spmm == 3) {
+    sa.vals = A->d_val32;
+    return launch_spmm32(a.kp, sa, A->nsm * spmm32_blocks_per_sm(a.kp, sa.stage_cap), s);
+  }
   const int mode = st.spmm == 2 ? 1 : 0;
-  return launch_spmm(A->kp, mode, sa, spmm_grid(A, A->kp, mode), s);
+  return launch_spmm(a.kp, mode, sa, spmm_grid(A, a.kp, mode), s);
 }
 
 std::string step_name(const Step &st, int kp) {
@@ -195,54 +236,83 @@ std::string step_name(const Step &st, int kp) {
   return std::string(st.spmm == 2 ? "spmm_resid_k" : "spmm_k") + std::to_string(kp);
 }
 
-void drop_graphs(bicgk_op A) {
-  for (auto &kv : A->graphs) {
+void drop_graphs(Workspace &W) {
+  for (auto &kv : W.graphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
   }
-  A->graphs.clear();
+  W.graphs.clear();
 }
 
-void free_workspace(bicgk_op A) {
-  drop_graphs(A);
-  cudaFree(A->d_vec);
-  cudaFree(A->d_sc);
-  cudaFree(A->d_fl);
-  cudaFree(A->d_part);
-  A->d_vec = nullptr;
-  A->d_sc = nullptr;
-  A->d_fl = nullptr;
-  A->d_part = nullptr;
-  A->kp = 0;
+void drop_all_graphs(bicgk_op A) {
+  for (Workspace &W : A->ws) drop_graphs(W);
 }
 
-int ensure_workspace(bicgk_op A, int kp) {
-  if (A->kp == kp) return BICGK_OK;
-  free_workspace(A);
+void free_vectors(Workspace &W) {
+  drop_graphs(W);
+  cudaFree(W.d_vec);
+  cudaFree(W.d_sc);
+  cudaFree(W.d_fl);
+  cudaFree(W.d_part);
+  W.d_vec = nullptr;
+  W.d_sc = nullptr;
+  W.d_fl = nullptr;
+  W.d_part = nullptr;
+  W.kp = 0;
+}
+
+void free_workspace(Workspace &W) {
+  free_vectors(W);
+  cudaFree(W.d_ctl);
+  cudaFree(W.d_hist);
+  cudaFreeHost(W.h_ctl);
+  cudaFreeHost(W.h_hist);
+  cudaFreeHost(W.h_fl);
+  cudaFreeHost(W.h_sc);
+  if (W.done) cudaEventDestroy(W.done);
+  if (W.stream) cudaStreamDestroy(W.stream);
+  W = Workspace();
+}
+
+// Allocate (once) the control block, host staging and stream of a workspace, and its
+// vectors for kp columns (reallocated when kp changes).
+int ensure_workspace(bicgk_op A, Workspace &W, int kp) {
+  if (!W.d_ctl) {
+    CK(cudaMalloc(&W.d_ctl, sizeof(Ctl)));
+    CK(cudaMemset(W.d_ctl, 0, sizeof(Ctl)));
+    CK(cudaMallocHost(&W.h_ctl, sizeof(Ctl)));
+    CK(cudaMallocHost(&W.h_fl, sizeof(int) * F_NFLAG * kMaxKp));
+    CK(cudaMallocHost(&W.h_sc, sizeof(double) * S_NSLOT * kMaxKp));
+    CK(cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&W.done, cudaEventDisableTiming));
+  }
+  if (W.kp == kp) return BICGK_OK;
+  free_vectors(W);
   const int64_t elems = A->n * kp + 2;
-  A->vstride = (elems + 31) / 32 * 32;
-  const size_t bytes = (size_t)A->vstride * V_NVEC * sizeof(double);
-  CK(cudaMalloc(&A->d_vec, bytes));
-  CK(cudaMemset(A->d_vec, 0, bytes));
-  CK(cudaMalloc(&A->d_sc, sizeof(double) * S_NSLOT * kMaxKp));
-  CK(cudaMalloc(&A->d_fl, sizeof(int) * F_NFLAG * kMaxKp));
-  CK(cudaMalloc(&A->d_part, sizeof(double) * (size_t)A->nsm * 4 * kMaxDots * kMaxKp));
-  CK(cudaMemset(A->d_sc, 0, sizeof(double) * S_NSLOT * kMaxKp));
-  CK(cudaMemset(A->d_fl, 0, sizeof(int) * F_NFLAG * kMaxKp));
-  A->kp = kp;
+  // vectors start on 256-byte boundaries; vstride counts doubles whatever the element type
+  W.vstride = W.ebytes == 8 ? (elems + 31) / 32 * 32 : (elems + 63) / 64 * 32;
+  const size_t bytes = (size_t)W.vstride * V_NVEC * sizeof(double);
+  CK(cudaMalloc(&W.d_vec, bytes));
+  CK(cudaMemset(W.d_vec, 0, bytes));
+  CK(cudaMalloc(&W.d_sc, sizeof(double) * S_NSLOT * kMaxKp));
+  CK(cudaMalloc(&W.d_fl, sizeof(int) * F_NFLAG * kMaxKp));
+  CK(cudaMalloc(&W.d_part, sizeof(double) * ((size_t)A->nsm * 4 + kMaxRedGroups) * kMaxDots * kMaxKp));
+  CK(cudaMemset(W.d_sc, 0, sizeof(double) * S_NSLOT * kMaxKp));
+  CK(cudaMemset(W.d_fl, 0, sizeof(int) * F_NFLAG * kMaxKp));
+  W.kp = kp;
   return BICGK_OK;
 }
 
-int ensure_hist(bicgk_op A, int64_t elems) {
-  if (elems <= A->hist_cap) return BICGK_OK;
-  cudaFree(A->d_hist);
-  cudaFreeHost(A->h_hist);
-  A->d_hist = nullptr;
-  A->h_hist = nullptr;
-  A->hist_cap = 0;
-  CK(cudaMalloc(&A->d_hist, sizeof(double) * elems));
-  CK(cudaMallocHost(&A->h_hist, sizeof(double) * elems));
-  A->hist_cap = elems;
+int ensure_hist(Workspace &W, int64_t elems) {
+  if (elems <= W.hist_cap) return BICGK_OK;
+  cudaFree(W.d_hist);
+  cudaFreeHost(W.h_hist);
+  W.d_hist = nullptr;
+  W.h_hist = nullptr;
+  W.hist_cap = 0;
+  CK(cudaMalloc(&W.d_hist, sizeof(double) * elems));
+  CK(cudaMallocHost(&W.h_hist, sizeof(double) * elems));
+  W.hist_cap = elems;
   return BICGK_OK;
 }
 
@@ -258,15 +328,14 @@ int ensure_stage(bicgk_op A, int64_t elems) {
   return BICGK_OK;
 }
 
-// Capture setup + WHILE(body) + final of (variant, kp) into one graph.
-int build_graph(bicgk_op A, int variant, GraphEntry *ge) {
-  const Seq q = make_seq(variant);
+// Capture q.setup + WHILE(q.body) + q.fin for workspace W into one graph.
+int build_graph_seq(bicgk_op A, Workspace &W, const Seq &q, const int *ext_act, GraphEntry *ge) {
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   ge->graph = g;
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-  const KArgs a = make_args(A, 1, h);
+  const KArgs a = make_args(A, W, 1, h, ext_act);
   cudaStream_t cs = A->cap_stream;
   // set-up
   CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -304,19 +373,24 @@ int build_graph(bicgk_op A, int variant, GraphEntry *ge) {
     }
   }
   CK(cudaStreamEndCapture(cs, &tmp));
-  // true residual after the loop
-  CK(cudaStreamBeginCaptureToGraph(cs, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
-  for (const Step &st : q.fin) {
-    cudaError_t e = launch_step(A, st, a, cs);
-    if (e != cudaSuccess) {
-      cudaGraph_t dummy;
-      cudaStreamEndCapture(cs, &dummy);
-      return cuda_fail(e, "capture final");
+  if (!q.fin.empty()) {
+    CK(cudaStreamBeginCaptureToGraph(cs, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    for (const Step &st : q.fin) {
+      cudaError_t e = launch_step(A, st, a, cs);
+      if (e != cudaSuccess) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(cs, &dummy);
+        return cuda_fail(e, "capture final");
+      }
     }
+    CK(cudaStreamEndCapture(cs, &tmp));
   }
-  CK(cudaStreamEndCapture(cs, &tmp));
   CK(cudaGraphInstantiate(&ge->exec, g, 0));
   return BICGK_OK;
+}
+
+int build_graph(bicgk_op A, Workspace &W, int variant, GraphEntry *ge) {
+  return build_graph_seq(A, W, make_seq(variant), nullptr, ge);
 }
 
 int check_device(int *dev, int *nsm) {
@@ -339,7 +413,7 @@ void prof_record(bicgk_op A, const std::string &name, float ms) {
 }
 
 // Profiling mode: the loop runs from the host, one launch at a time, each bracketed by events.
-int run_profiled(bicgk_op A, int variant, const KArgs &a, cudaStream_t s) {
+int run_profiled(bicgk_op A, Workspace &W, int variant, const KArgs &a, cudaStream_t s) {
   const Seq q = make_seq(variant);
   const size_t nmax = q.body.size() > q.setup.size() ? q.body.size() : q.setup.size();
   while (A->ev.size() < 2 * (nmax + 2)) {
@@ -353,22 +427,22 @@ int run_profiled(bicgk_op A, int variant, const KArgs &a, cudaStream_t s) {
       CK(launch_step(A, steps[i], a, s));
       CK(cudaEventRecord(A->ev[2 * i + 1], s));
     }
-    CK(cudaMemcpyAsync(A->h_ctl, A->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(W.h_ctl, W.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     for (size_t i = 0; i < steps.size(); ++i) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, A->ev[2 * i], A->ev[2 * i + 1]));
-      prof_record(A, step_name(steps[i], A->kp), ms);
+      prof_record(A, step_name(steps[i], a.kp), ms);
     }
     return BICGK_OK;
   };
   int rc = run_list(q.setup);
   if (rc) return rc;
-  bool go = A->h_ctl->any_active && A->h_ctl->maxit > 0;
+  bool go = W.h_ctl->any_active && W.h_ctl->maxit > 0;
   while (go) {
     rc = run_list(q.body);
     if (rc) return rc;
-    go = A->h_ctl->any_active && A->h_ctl->iter < A->h_ctl->maxit;
+    go = W.h_ctl->any_active && W.h_ctl->iter < W.h_ctl->maxit;
   }
   return run_list(q.fin);
 }
@@ -377,7 +451,7 @@ int run_profiled(bicgk_op A, int variant, const KArgs &a, cudaStream_t s) {
 
 extern "C" {
 
-const char *bicgk_version(void) { return "bicgk 0.1 sm_103a"; }
+const char *bicgk_version(void) { return "bicgk 0.2 sm_103a"; }
 
 const char *bicgk_strerror(int rc) {
   switch (rc) {
@@ -442,12 +516,8 @@ int bicgk_csr_create(bicgk_op *out, int64_t n_rows, int64_t nnz, const int32_t *
       (e = cudaMemcpyAsync(A->d_rowptr, rowptr, sizeof(int32_t) * (n_rows + 1), kind, s)) != cudaSuccess ||
       (nnz && (e = cudaMemcpyAsync(A->d_col, colidx, sizeof(int32_t) * nnz, kind, s)) != cudaSuccess) ||
       (nnz && (e = cudaMemcpyAsync(A->d_val, vals, sizeof(double) * nnz, kind, s)) != cudaSuccess) ||
-      (e = cudaMallocHost(&A->h_ctl, sizeof(Ctl))) != cudaSuccess ||
-      (e = cudaMallocHost(&A->h_fl, sizeof(int) * F_NFLAG * kMaxKp)) != cudaSuccess ||
-      (e = cudaMallocHost(&A->h_sc, sizeof(double) * S_NSLOT * kMaxKp)) != cudaSuccess ||
-      (e = cudaMalloc(&A->d_ctl, sizeof(Ctl))) != cudaSuccess ||
-      (e = cudaMemsetAsync(A->d_ctl, 0, sizeof(Ctl), s)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&A->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&A->fork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     bicgk_op_destroy(A);
     return cuda_fail(e, "bicgk_csr_create");
@@ -459,19 +529,16 @@ int bicgk_csr_create(bicgk_op *out, int64_t n_rows, int64_t nnz, const int32_t *
 int bicgk_op_destroy(bicgk_op A) {
   if (!A) return BICGK_OK;
   cudaDeviceSynchronize();
-  free_workspace(A);
+  for (Workspace &W : A->ws) free_workspace(W);
+  free_workspace(A->ws32);
+  cudaFree(A->d_val32);
   cudaFree(A->d_rowptr);
   cudaFree(A->d_col);
   cudaFree(A->d_val);
-  cudaFree(A->d_ctl);
-  cudaFree(A->d_hist);
   cudaFree(A->d_stage[0]);
   cudaFree(A->d_stage[1]);
-  cudaFreeHost(A->h_ctl);
-  cudaFreeHost(A->h_hist);
-  cudaFreeHost(A->h_fl);
-  cudaFreeHost(A->h_sc);
   for (cudaEvent_t e : A->ev) cudaEventDestroy(e);
+  if (A->fork) cudaEventDestroy(A->fork);
   if (A->cap_stream) cudaStreamDestroy(A->cap_stream);
   delete A;
   return BICGK_OK;
@@ -495,14 +562,15 @@ int bicgk_spmm(bicgk_op A, int32_t k, const double *X, double *Y, void *stream) 
     CK(launch_spmm(kp, 0, sa, spmm_grid(A, kp, 0), s));
     return BICGK_OK;
   }
-  int rc = ensure_workspace(A, kp);
+  Workspace &W = A->ws[0];
+  int rc = ensure_workspace(A, W, kp);
   if (rc) return rc;
-  const KArgs a = make_args(A, 0, cudaGraphConditionalHandle{});
-  CK(launch_pack(X, nullptr, k, a, s));
+  const KArgs a = make_args(A, W, 0, cudaGraphConditionalHandle{});
+  CK(launch_pack(X, nullptr, k, k, a, s));
   sa.x = a.v[V_B];
   sa.y = a.v[V_TMP];
   CK(launch_spmm(kp, 0, sa, spmm_grid(A, kp, 0), s));
-  CK(launch_unpack_role(Y, k, a, V_TMP, 0, s));
+  CK(launch_unpack_role(Y, k, k, a, V_TMP, 0, s));
   return BICGK_OK;
 }
 
@@ -514,77 +582,254 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     return BICGK_E_INVALID;
   if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
-  const int kp = pow2_at_least(k);
-  int rc = ensure_workspace(A, kp);
-  if (rc) return rc;
-  const int64_t hist_len = (int64_t)(maxit + 1) * kp;
-  rc = ensure_hist(A, hist_len);
-  if (rc) return rc;
+  // columns are independent: split k >= kSplitMinK into two groups solved concurrently, so that
+  // one group's FP64-bound SpMM overlaps the other group's bandwidth-bound vector kernels
+  const int ngroups = (!A->profiling && A->opt_groups != 1 && k >= kSplitMinK) ? 2 : 1;
+  int c0[kMaxGroups + 1] = {0, ngroups == 2 ? k / 2 : k, k};
+  c0[ngroups] = k;
+  int rc;
+  for (int g = 0; g < ngroups; ++g) {
+    const int kg = c0[g + 1] - c0[g];
+    const int kpg = pow2_at_least(kg);
+    if ((rc = ensure_workspace(A, A->ws[g], kpg))) return rc;
+    if ((rc = ensure_hist(A->ws[g], (int64_t)(maxit + 1) * kpg))) return rc;
+  }
   const Seq q = make_seq(variant);
   // inputs
   const double *dB = B, *dX0 = X0;
+  double *dX = X;
   if (mem == BICGK_MEM_HOST) {
-    rc = ensure_stage(A, A->n * k);
-    if (rc) return rc;
+    if ((rc = ensure_stage(A, A->n * k))) return rc;
     CK(cudaMemcpyAsync(A->d_stage[0], B, sizeof(double) * A->n * k, cudaMemcpyHostToDevice, s));
     dB = A->d_stage[0];
     if (X0) {
       CK(cudaMemcpyAsync(A->d_stage[1], X0, sizeof(double) * A->n * k, cudaMemcpyHostToDevice, s));
       dX0 = A->d_stage[1];
     }
+    dX = A->d_stage[0];  // X overwrites the staged B after both groups have packed it
   }
-  Ctl *hc = A->h_ctl;
+  if (ngroups > 1) CK(cudaEventRecord(A->fork, s));
+  int64_t launches = 0;
+  for (int g = 0; g < ngroups; ++g) {
+    Workspace &W = A->ws[g];
+    cudaStream_t gs = ngroups > 1 ? W.stream : s;
+    if (ngroups > 1) CK(cudaStreamWaitEvent(gs, A->fork, 0));
+    const int kg = c0[g + 1] - c0[g];
+    const int64_t hist_len = (int64_t)(maxit + 1) * W.kp;
+    Ctl *hc = W.h_ctl;
+    memset(hc, 0, sizeof(Ctl));
+    hc->tol = rel_tol;
+    hc->hist = W.d_hist;
+    hc->maxit = maxit;
+    hc->k = kg;
+    hc->kp = W.kp;
+    hc->flags = flags;
+    CK(cudaMemcpyAsync(W.d_ctl, hc, sizeof(Ctl), cudaMemcpyHostToDevice, gs));
+    const KArgs a0 = make_args(A, W, 0, cudaGraphConditionalHandle{});
+    CK(launch_reset(a0, hist_len, gs));
+    CK(launch_pack(dB + c0[g], dX0 ? dX0 + c0[g] : nullptr, k, kg, a0, gs));
+    launches += 2;  // reset, pack
+    if (A->profiling) {
+      if ((rc = run_profiled(A, W, variant, a0, gs))) return rc;
+    } else {
+      auto it = W.graphs.find(variant);
+      if (it == W.graphs.end()) {
+        GraphEntry ge;
+        if ((rc = build_graph(A, W, variant, &ge))) {
+          if (ge.exec) cudaGraphExecDestroy(ge.exec);
+          if (ge.graph) cudaGraphDestroy(ge.graph);
+          return rc;
+        }
+        it = W.graphs.emplace(variant, ge).first;
+      }
+      CK(cudaGraphLaunch(it->second.exec, gs));
+    }
+    if (ngroups > 1 && mem == BICGK_MEM_HOST) {
+      // the staged B is overwritten by X only after every group has packed its columns
+      CK(cudaEventRecord(W.done, gs));
+    }
+  }
+  for (int g = 0; g < ngroups; ++g) {
+    Workspace &W = A->ws[g];
+    cudaStream_t gs = ngroups > 1 ? W.stream : s;
+    if (ngroups > 1 && mem == BICGK_MEM_HOST)
+      for (int h = 0; h < ngroups; ++h)
+        if (h != g) CK(cudaStreamWaitEvent(gs, A->ws[h].done, 0));
+    const int kg = c0[g + 1] - c0[g];
+    const int64_t hist_len = (int64_t)(maxit + 1) * W.kp;
+    const KArgs a0 = make_args(A, W, 0, cudaGraphConditionalHandle{});
+    CK(launch_unpack_role(dX + c0[g], k, kg, a0, V_X, 1, gs));
+    CK(cudaMemcpyAsync(W.h_ctl, W.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, gs));
+    CK(cudaMemcpyAsync(W.h_fl, W.d_fl, sizeof(int) * F_NFLAG * kMaxKp, cudaMemcpyDeviceToHost, gs));
+    CK(cudaMemcpyAsync(W.h_sc, W.d_sc, sizeof(double) * S_NSLOT * kMaxKp, cudaMemcpyDeviceToHost, gs));
+    if (resid_hist)
+      CK(cudaMemcpyAsync(W.h_hist, W.d_hist, sizeof(double) * hist_len, cudaMemcpyDeviceToHost, gs));
+    if (ngroups > 1) {
+      CK(cudaEventRecord(W.done, gs));
+      CK(cudaStreamWaitEvent(s, W.done, 0));
+    }
+    launches += 1;  // unpack
+  }
+  if (mem == BICGK_MEM_HOST) CK(cudaMemcpyAsync(X, dX, sizeof(double) * A->n * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int32_t loop_iters = 0;
+  for (int g = 0; g < ngroups; ++g) {
+    Workspace &W = A->ws[g];
+    const int kg = c0[g + 1] - c0[g];
+    for (int c = 0; c < kg; ++c) {
+      iters[c0[g] + c] = W.h_fl[F_ITERS * kMaxKp + c];
+      status[c0[g] + c] = W.h_fl[F_STATUS * kMaxKp + c];
+      if (true_relres) true_relres[c0[g] + c] = W.h_sc[S_TRUE * kMaxKp + c];
+    }
+    if (resid_hist)
+      for (int64_t j = 0; j <= maxit; ++j)
+        for (int c = 0; c < kg; ++c) resid_hist[j * k + c0[g] + c] = W.h_hist[j * W.kp + c];
+    if (W.h_ctl->loop_iters > loop_iters) loop_iters = W.h_ctl->loop_iters;
+    launches += (int64_t)q.setup.size() + (int64_t)W.h_ctl->loop_iters * q.body.size() + q.fin.size();
+  }
+  A->last_loop_iters = loop_iters;
+  A->last_kernels_per_iter = (int32_t)q.body.size();
+  A->last_launches = launches;
+  A->last_groups = ngroups;
+  return BICGK_OK;
+}
+
+
+int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, double rel_tol, int32_t max_outer,
+                      double inner_tol, int32_t max_inner, int mem, double *X, int32_t *outer_iters,
+                      int32_t *inner_iters, int32_t *status, double *resid_hist, double *true_relres,
+                      void *stream) {
+  if (!A || !B || !X || !outer_iters || !inner_iters || !status || k < 1 || !(rel_tol >= 0.0) ||
+      !(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 0 || max_outer > 1000 || max_inner < 1 ||
+      max_inner > 10000000 || (mem != BICGK_MEM_HOST && mem != BICGK_MEM_DEVICE))
+    return BICGK_E_INVALID;
+  if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int kp = pow2_at_least(k);
+  Workspace &W = A->ws[0];
+  Workspace &V = A->ws32;
+  V.ebytes = 4;
+  int rc;
+  if ((rc = ensure_workspace(A, W, kp)) || (rc = ensure_workspace(A, V, kp)) ||
+      (rc = ensure_hist(W, (int64_t)(max_outer + 1) * kp)) || (rc = ensure_hist(V, (int64_t)(max_inner + 1) * kp)))
+    return rc;
+  if (!A->d_val32) {
+    CK(cudaMalloc(&A->d_val32, sizeof(float) * A->nnz + 16));
+    CK(launch_to_float(A->d_val, A->d_val32, A->nnz, s));
+  }
+  const double *dB = B, *dX0 = X0;
+  double *dX = X;
+  if (mem == BICGK_MEM_HOST) {
+    if ((rc = ensure_stage(A, A->n * k))) return rc;
+    CK(cudaMemcpyAsync(A->d_stage[0], B, sizeof(double) * A->n * k, cudaMemcpyHostToDevice, s));
+    dB = A->d_stage[0];
+    if (X0) {
+      CK(cudaMemcpyAsync(A->d_stage[1], X0, sizeof(double) * A->n * k, cudaMemcpyHostToDevice, s));
+      dX0 = A->d_stage[1];
+    }
+    dX = A->d_stage[0];
+  }
+  // outer (FP64) state
+  Ctl *hc = W.h_ctl;
   memset(hc, 0, sizeof(Ctl));
   hc->tol = rel_tol;
-  hc->hist = A->d_hist;
-  hc->maxit = maxit;
+  hc->hist = W.d_hist;
+  hc->maxit = max_outer;
   hc->k = k;
   hc->kp = kp;
-  hc->flags = flags;
-  CK(cudaMemcpyAsync(A->d_ctl, hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-  const KArgs a0 = make_args(A, 0, cudaGraphConditionalHandle{});
-  CK(launch_reset(a0, hist_len, s));
-  CK(launch_pack(dB, dX0, k, a0, s));
+  CK(cudaMemcpyAsync(W.d_ctl, hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  const KArgs ao = make_args(A, W, 0, cudaGraphConditionalHandle{});
+  KArgs air = ao;  // outer steps that touch the FP32 blocks: b32 in V_Q, d in V_Y
+  const KArgs ai0 = make_args(A, V, 0, cudaGraphConditionalHandle{});
+  air.v[V_Q] = ai0.v[V_B];
+  air.v[V_Y] = ai0.v[V_X];
+  CK(launch_reset(ao, (int64_t)(max_outer + 1) * kp, s));
+  CK(launch_pack(dB, dX0, k, k, ao, s));
+  CK(launch_vec(OP_IR_SETUP, ao, vec_grid(A, OP_IR_SETUP), s));
   int64_t launches = 3;
-  if (A->profiling) {
-    rc = run_profiled(A, variant, a0, s);
-    if (rc) return rc;
-  } else {
-    auto key = std::make_pair(variant, kp);
-    auto it = A->graphs.find(key);
-    if (it == A->graphs.end()) {
-      GraphEntry ge;
-      rc = build_graph(A, variant, &ge);
-      if (rc) {
-        if (ge.exec) cudaGraphExecDestroy(ge.exec);
-        if (ge.graph) cudaGraphDestroy(ge.graph);
-        return rc;
-      }
-      it = A->graphs.emplace(key, ge).first;
+  // inner FP32 solve graph (columns the outer loop still refines: the outer active flags)
+  const int *ext_act = W.d_fl + F_ACT * kMaxKp;
+  const Seq qi = make_inner32_seq();
+  auto it = V.graphs.find(-1);
+  if (it == V.graphs.end()) {
+    GraphEntry ge;
+    if ((rc = build_graph_seq(A, V, qi, ext_act, &ge))) {
+      if (ge.exec) cudaGraphExecDestroy(ge.exec);
+      if (ge.graph) cudaGraphDestroy(ge.graph);
+      return rc;
     }
-    CK(cudaGraphLaunch(it->second.exec, s));
+    it = V.graphs.emplace(-1, ge).first;
   }
-  // outputs
-  double *dX = mem == BICGK_MEM_HOST ? A->d_stage[0] : X;
-  CK(launch_unpack_role(dX, k, a0, V_X, 1, s));
+  std::vector<int32_t> inner_total(k, 0);
+  const Step res = resid(V_X, V_R, V_B);
+  for (int pass = 0;; ++pass) {
+    CK(launch_step(A, res, ao, s));                                    // r = b - A x (FP64)
+    CK(launch_vec(OP_IR_RESID, air, vec_grid(A, OP_IR_RESID), s));     // (r,r), stop test, b32 = fl32(r)
+    CK(cudaMemcpyAsync(W.h_ctl, W.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    launches += 2;
+    if (pass > 0)
+      for (int c = 0; c < k; ++c) inner_total[c] += V.h_fl[F_ITERS * kMaxKp + c];
+    if (!W.h_ctl->any_active) break;
+    Ctl *hi = V.h_ctl;
+    memset(hi, 0, sizeof(Ctl));
+    hi->tol = inner_tol;
+    hi->hist = V.d_hist;
+    hi->maxit = max_inner;
+    hi->k = k;
+    hi->kp = kp;
+    CK(cudaMemcpyAsync(V.d_ctl, hi, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(launch_reset(ai0, (int64_t)(max_inner + 1) * kp, s));
+    CK(cudaGraphLaunch(it->second.exec, s));                           // FP32 inner solve of A d = r
+    CK(launch_vec(OP_IR_UPDATE, air, vec_grid(A, OP_IR_UPDATE), s));   // x += d (FP64)
+    CK(cudaMemcpyAsync(V.h_fl, V.d_fl, sizeof(int) * F_NFLAG * kMaxKp, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(V.h_ctl, V.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    launches += 2;
+  }
+  CK(launch_unpack_role(dX, k, k, ao, V_X, 1, s));
   if (mem == BICGK_MEM_HOST) CK(cudaMemcpyAsync(X, dX, sizeof(double) * A->n * k, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(A->h_ctl, A->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(A->h_fl, A->d_fl, sizeof(int) * F_NFLAG * kMaxKp, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(A->h_sc, A->d_sc, sizeof(double) * S_NSLOT * kMaxKp, cudaMemcpyDeviceToHost, s));
-  if (resid_hist) CK(cudaMemcpyAsync(A->h_hist, A->d_hist, sizeof(double) * hist_len, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(W.h_fl, W.d_fl, sizeof(int) * F_NFLAG * kMaxKp, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(W.h_sc, W.d_sc, sizeof(double) * S_NSLOT * kMaxKp, cudaMemcpyDeviceToHost, s));
+  if (resid_hist)
+    CK(cudaMemcpyAsync(W.h_hist, W.d_hist, sizeof(double) * (max_outer + 1) * kp, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   for (int c = 0; c < k; ++c) {
-    iters[c] = A->h_fl[F_ITERS * kMaxKp + c];
-    status[c] = A->h_fl[F_STATUS * kMaxKp + c];
-    if (true_relres) true_relres[c] = A->h_sc[S_TRUE * kMaxKp + c];
+    status[c] = W.h_fl[F_STATUS * kMaxKp + c];
+    outer_iters[c] = W.h_fl[F_ITERS * kMaxKp + c];
+    inner_iters[c] = inner_total[c];
+    if (true_relres) true_relres[c] = W.h_sc[S_TRUE * kMaxKp + c];
   }
   if (resid_hist)
-    for (int64_t j = 0; j <= maxit; ++j)
-      for (int c = 0; c < k; ++c) resid_hist[j * k + c] = A->h_hist[j * kp + c];
-  A->last_loop_iters = A->h_ctl->loop_iters;
-  A->last_kernels_per_iter = (int32_t)q.body.size();
-  launches += (int64_t)q.setup.size() + (int64_t)A->last_loop_iters * q.body.size() + q.fin.size();
-  A->last_launches = launches;
+    for (int64_t j = 0; j <= max_outer; ++j)
+      for (int c = 0; c < k; ++c) resid_hist[j * k + c] = W.h_hist[j * kp + c];
+  A->last_loop_iters = 0;
+  for (int c = 0; c < k; ++c) A->last_loop_iters = inner_total[c] > A->last_loop_iters ? inner_total[c] : A->last_loop_iters;
+  A->last_kernels_per_iter = (int32_t)qi.body.size();
+  A->last_launches = launches + 1;
+  A->last_groups = 1;
+  return BICGK_OK;
+}
+
+int bicgk_set_option(bicgk_op A, int option, int64_t value) {
+  if (!A) return BICGK_E_INVALID;
+  switch (option) {
+    case BICGK_OPT_VEC_BLOCKS_PER_SM:
+      if (value < 0 || value > 4) return BICGK_E_INVALID;
+      A->opt_vec_blocks = (int)value;
+      break;
+    case BICGK_OPT_SPMM_BLOCKS_PER_SM:
+      if (value < 0 || value > 32) return BICGK_E_INVALID;
+      A->opt_spmm_blocks = (int)value;
+      break;
+    case BICGK_OPT_RHS_GROUPS:
+      if (value < 0 || value > 2) return BICGK_E_INVALID;
+      A->opt_groups = (int)value;
+      break;
+    default:
+      return BICGK_E_INVALID;
+  }
+  drop_all_graphs(A);  // grid sizes are baked into the captured graphs
+  drop_graphs(A->ws32);
   return BICGK_OK;
 }
 
@@ -671,7 +916,7 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
   const size_t b_vec = round256(sizeof(double) * (size_t)vstride * V_NVEC);
   const size_t b_sc = round256(sizeof(double) * S_NSLOT * kMaxKp);
   const size_t b_fl = round256(sizeof(int) * F_NFLAG * kMaxKp);
-  const size_t b_part = round256(sizeof(double) * (size_t)nsm * 4 * kMaxDots * kMaxKp);
+  const size_t b_part = round256(sizeof(double) * ((size_t)nsm * 4 + kMaxRedGroups) * kMaxDots * kMaxKp);
   const size_t b_ctl = round256(sizeof(Ctl));
   const size_t b_hist = round256(sizeof(double) * (size_t)hist_len);
   const size_t need = b_vec + b_sc + b_fl + b_part + b_ctl + b_hist;
@@ -697,32 +942,33 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
   A.d_col = const_cast<int32_t *>(colidx);
   A.d_val = const_cast<double *>(vals);
   A.stage_cap = 0;  // the k <= 2 SpMM reads CSR entries from global memory (same arithmetic)
-  A.kp = kp;
-  A.vstride = vstride;
-  A.d_vec = reinterpret_cast<double *>(base);
-  A.d_sc = reinterpret_cast<double *>(base + b_vec);
-  A.d_fl = reinterpret_cast<int *>(base + b_vec + b_sc);
-  A.d_part = reinterpret_cast<double *>(base + b_vec + b_sc + b_fl);
-  A.d_ctl = reinterpret_cast<Ctl *>(base + b_vec + b_sc + b_fl + b_part);
-  A.d_hist = reinterpret_cast<double *>(base + b_vec + b_sc + b_fl + b_part + b_ctl);
+  Workspace W;
+  W.kp = kp;
+  W.vstride = vstride;
+  W.d_vec = reinterpret_cast<double *>(base);
+  W.d_sc = reinterpret_cast<double *>(base + b_vec);
+  W.d_fl = reinterpret_cast<int *>(base + b_vec + b_sc);
+  W.d_part = reinterpret_cast<double *>(base + b_vec + b_sc + b_fl);
+  W.d_ctl = reinterpret_cast<Ctl *>(base + b_vec + b_sc + b_fl + b_part);
+  W.d_hist = reinterpret_cast<double *>(base + b_vec + b_sc + b_fl + b_part + b_ctl);
   // control block: the reduction ticket and the iteration counter start at zero
   Ctl hc;
   memset(&hc, 0, sizeof(hc));
   hc.tol = rel_tol;
-  hc.hist = A.d_hist;
+  hc.hist = W.d_hist;
   hc.maxit = maxit;
   hc.k = k;
   hc.kp = kp;
   hc.flags = flags;
-  CK(cudaMemcpyAsync(A.d_ctl, &hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-  const KArgs a = make_args(&A, 0, cudaGraphConditionalHandle{});
-  CK(launch_reset(a, hist_len, s));     // history = NaN, per-column scalars and flags = 0
-  CK(launch_pack(B, X0, k, a, s));      // B and X0 in, padding columns and pad elements = 0
+  CK(cudaMemcpyAsync(W.d_ctl, &hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  const KArgs a = make_args(&A, W, 0, cudaGraphConditionalHandle{});
+  CK(launch_reset(a, hist_len, s));        // history = NaN, per-column scalars and flags = 0
+  CK(launch_pack(B, X0, k, k, a, s));      // B and X0 in, padding columns and pad elements = 0
   const Seq q = make_seq(variant);
   Ctl poll;
   auto run = [&](const std::vector<Step> &steps) -> int {
     for (const Step &st : steps) CK(launch_step(&A, st, a, s));
-    CK(cudaMemcpyAsync(&poll, A.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&poll, W.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return BICGK_OK;
   };
@@ -735,13 +981,13 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
     go = poll.any_active && poll.iter < maxit;
   }
   for (const Step &st : q.fin) CK(launch_step(&A, st, a, s));
-  CK(launch_unpack_role(X, k, a, V_X, 1, s));
-  CK(cudaMemcpyAsync(iters, A.d_fl + F_ITERS * kMaxKp, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(status, A.d_fl + F_STATUS * kMaxKp, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s));
+  CK(launch_unpack_role(X, k, k, a, V_X, 1, s));
+  CK(cudaMemcpyAsync(iters, W.d_fl + F_ITERS * kMaxKp, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(status, W.d_fl + F_STATUS * kMaxKp, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s));
   if (true_relres)
-    CK(cudaMemcpyAsync(true_relres, A.d_sc + S_TRUE * kMaxKp, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(true_relres, W.d_sc + S_TRUE * kMaxKp, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   if (resid_hist)
-    CK(cudaMemcpy2DAsync(resid_hist, sizeof(double) * k, A.d_hist, sizeof(double) * kp, sizeof(double) * k,
+    CK(cudaMemcpy2DAsync(resid_hist, sizeof(double) * k, W.d_hist, sizeof(double) * kp, sizeof(double) * k,
                          (size_t)maxit + 1, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return BICGK_OK;

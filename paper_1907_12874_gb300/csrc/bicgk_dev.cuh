@@ -20,6 +20,8 @@ constexpr int kMaxDots = 4;       // largest number of dot products fused in one
 constexpr int kSpmmThreads = 256; // threads per block of the SpMM kernels
 constexpr int kSpmmTileRows = 256;      // rows per staged tile (kp <= 2 path)
 constexpr int kSpmmStageMax = 4096;     // largest staged tile (CSR entries)
+constexpr int kRedGroup = 16;           // blocks per first-level group of the grid reduction
+constexpr int kMaxRedGroups = 64;       // group tickets (grids up to 1024 blocks)
 
 // Per-column FP64 scalar slots.
 enum Slot : int {
@@ -43,7 +45,8 @@ struct Ctl {
   int flags;      // bicgk_flags
   int any_active; // some column still iterating
   int loop_iters; // iterations the loop completed
-  unsigned int ticket; // arrival counter of the grid reduction (reset by the last block)
+  unsigned int ticket; // arrival counter of the grid reduction's second level (reset by its last block)
+  unsigned int gticket[kMaxRedGroups]; // arrival counters of the first level, one per group of blocks
 };
 
 // Vector roles in the workspace.
@@ -55,12 +58,13 @@ struct KArgs {
   double *v[V_NVEC];
   double *sc;    // [S_NSLOT][kMaxKp]
   int *fl;       // [F_NFLAG][kMaxKp]
-  double *part;  // [grid][kMaxDots][kMaxKp] per-block partial sums
+  double *part;  // [grid + groups][kMaxDots][kMaxKp]: per-block partial sums, then per-group sums
   Ctl *ctl;
   int64_t n;     // rows
   int kp;
   int use_cond;  // 1 inside the captured graph (the loop is a conditional WHILE node)
   cudaGraphConditionalHandle cond;
+  const int *ext_act;  // inner solves of the refinement: columns the outer loop still iterates
 };
 
 // Streaming kernel identifiers (one per fused vector operation of the listings).
@@ -79,6 +83,10 @@ enum Op : int {
   OP_PU_X, OP_PU_R, OP_PU_TMP, OP_PU_W, OP_DOT_R0R, OP_DOT_R0Z, OP_DOT_R0W, OP_DOT_R0S,
   // final true residual norm
   OP_TRUE_RES,
+  // mixed-precision refinement: FP32 inner solve (merged classical BiCGStab, Algorithm 2)
+  OP32_SETUP, OP32_DELTA, OP32_UPD_S, OP32_G1, OP32_G3, OP32_UPD_P,
+  // mixed-precision refinement: FP64 outer steps (V_Q / V_Y point to the FP32 b and d blocks)
+  OP_IR_SETUP, OP_IR_RESID, OP_IR_UPDATE,
   OP_COUNT
 };
 
@@ -93,24 +101,32 @@ cudaError_t launch_vec(int op, const KArgs &a, int grid, cudaStream_t s);
 int vec_blocks_per_sm(int op);
 
 // SpMM: y = A x (mode 0) or y = b - A x (mode 1) for kp in {1,2,4,...,64}.
+// vals, x, y, b point to double (launch_spmm) or float (launch_spmm32) arrays.
 struct SpmmArgs {
   const int32_t *rowptr;
   const int32_t *colidx;
-  const double *vals;
-  const double *x;
-  double *y;
-  const double *b;
+  const void *vals;
+  const void *x;
+  void *y;
+  const void *b;
   int64_t n;
   int stage_cap;  // staged CSR entries per tile (kp <= 2); 0 = read entries directly
 };
 cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s);
 int spmm_blocks_per_sm(int kp, int mode, int stage_cap);
+// FP32 y = A x (values, x and y float; one FP32 FMA per nonzero and column).
+cudaError_t launch_spmm32(int kp, const SpmmArgs &a, int grid, cudaStream_t s);
+int spmm32_blocks_per_sm(int kp, int stage_cap);
 
-// Pack a user block (ld = k) into the workspace layout (ld = kp, zero padding); X0 may be null.
-cudaError_t launch_pack(const double *B, const double *X0, int k, const KArgs &a, cudaStream_t s);
-// Unpack workspace role `role` (ld = kp) into a user block (ld = k); with use_xzero, columns
-// with b_c = 0 are written as zeros.
-cudaError_t launch_unpack_role(double *X, int k, const KArgs &a, int role, int use_xzero, cudaStream_t s);
+// Pack columns [0, ncols) of a caller block with leading dimension ld into the workspace layout
+// (ld = kp, zero padding); X0 may be null.
+cudaError_t launch_pack(const double *B, const double *X0, int ld, int ncols, const KArgs &a, cudaStream_t s);
+// Unpack workspace role `role` (ld = kp) into columns [0, ncols) of a caller block with leading
+// dimension ld; with use_xzero, columns with b_c = 0 are written as zeros.
+cudaError_t launch_unpack_role(double *X, int ld, int ncols, const KArgs &a, int role, int use_xzero,
+                               cudaStream_t s);
+// dst = (float)src elementwise.
+cudaError_t launch_to_float(const double *src, float *dst, int64_t n, cudaStream_t s);
 // Fill the history with NaN and clear the per-column state.
 cudaError_t launch_reset(const KArgs &a, int64_t hist_len, cudaStream_t s);
 

@@ -1,4 +1,5 @@
-// CSR sparse matrix times a block of k RHS-interleaved vectors:
+// CSR sparse matrix times a block of k RHS-interleaved vectors, FP64 (and FP32 for the inner
+// solves of the mixed-precision refinement):
 //   y_ic = sum_j a_ij x_jc           (mode 0: the SpMV of Algorithms 1-6)
 //   y_ic = b_ic - sum_j a_ij x_jc    (mode 1: r_0 = b - A x_0 and the final
 //                                     true residual)
@@ -26,27 +27,43 @@ namespace bicgk {
 
 namespace {
 
-template <int KP, int MODE>
+// Element type T (double: the FP64 path; float: the FP32 inner solves of the mixed-precision
+// refinement) and its two-wide vector type.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+  using type = double2;
+  __device__ static type make(double x, double y) { return make_double2(x, y); }
+};
+template <>
+struct Vec2<float> {
+  using type = float2;
+  __device__ static type make(float x, float y) { return make_float2(x, y); }
+};
+
+template <typename T, int KP, int MODE>
 __global__ void __launch_bounds__(kSpmmThreads) spmm_group_kernel(const SpmmArgs a) {
   static_assert(KP >= 4, "group kernel needs kp >= 4");
+  using T2 = typename Vec2<T>::type;
   constexpr int L = KP / 2;                   // lanes per row
   constexpr int RPP = kSpmmThreads / L;       // rows per pass of a block
   const int g = threadIdx.x / L, cl = threadIdx.x % L;
   const int32_t *__restrict__ rp = a.rowptr;
   const int32_t *__restrict__ ci = a.colidx;
-  const double *__restrict__ va = a.vals;
-  const double2 *__restrict__ x2 = reinterpret_cast<const double2 *>(a.x);
-  double2 *__restrict__ y2 = reinterpret_cast<double2 *>(a.y);
+  const T *__restrict__ va = static_cast<const T *>(a.vals);
+  const T2 *__restrict__ x2 = static_cast<const T2 *>(a.x);
+  T2 *__restrict__ y2 = static_cast<T2 *>(a.y);
   const int64_t stride = (int64_t)gridDim.x * RPP;
   for (int64_t r = (int64_t)blockIdx.x * RPP + g; r < a.n; r += stride) {
     const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
-    double2 acc = make_double2(0.0, 0.0);
+    T2 acc = Vec2<T>::make(0, 0);
     int e = e0;
     for (; e + 1 < e1; e += 2) {
       const int j0 = __ldg(ci + e), j1 = __ldg(ci + e + 1);
-      const double a0 = __ldg(va + e), a1 = __ldg(va + e + 1);
-      const double2 u0 = __ldg(x2 + (int64_t)j0 * L + cl);
-      const double2 u1 = __ldg(x2 + (int64_t)j1 * L + cl);
+      const T a0 = __ldg(va + e), a1 = __ldg(va + e + 1);
+      const T2 u0 = __ldg(x2 + (int64_t)j0 * L + cl);
+      const T2 u1 = __ldg(x2 + (int64_t)j1 * L + cl);
       acc.x = fma(a0, u0.x, acc.x);
       acc.y = fma(a0, u0.y, acc.y);
       acc.x = fma(a1, u1.x, acc.x);
@@ -54,30 +71,32 @@ __global__ void __launch_bounds__(kSpmmThreads) spmm_group_kernel(const SpmmArgs
     }
     if (e < e1) {
       const int j0 = __ldg(ci + e);
-      const double a0 = __ldg(va + e);
-      const double2 u0 = __ldg(x2 + (int64_t)j0 * L + cl);
+      const T a0 = __ldg(va + e);
+      const T2 u0 = __ldg(x2 + (int64_t)j0 * L + cl);
       acc.x = fma(a0, u0.x, acc.x);
       acc.y = fma(a0, u0.y, acc.y);
     }
     if constexpr (MODE == 1) {
-      const double2 bv = reinterpret_cast<const double2 *>(a.b)[r * L + cl];
-      acc = make_double2(bv.x - acc.x, bv.y - acc.y);
+      const T2 bv = static_cast<const T2 *>(a.b)[r * L + cl];
+      acc = Vec2<T>::make(bv.x - acc.x, bv.y - acc.y);
     }
     y2[r * L + cl] = acc;
   }
 }
 
 // One lane per row, CSR entries of each 256-row tile staged in shared memory.
-template <int KP, int MODE>
+template <typename T, int KP, int MODE>
 __global__ void __launch_bounds__(kSpmmThreads) spmm_row_kernel(const SpmmArgs a) {
   static_assert(KP == 1 || KP == 2, "row kernel handles kp <= 2");
-  extern __shared__ unsigned char smem_raw[];
+  using T2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cap = a.stage_cap;
-  double *s_val = reinterpret_cast<double *>(smem_raw);
+  T *s_val = reinterpret_cast<T *>(smem_raw);
   int32_t *s_col = reinterpret_cast<int32_t *>(s_val + cap);
   const int32_t *__restrict__ rp = a.rowptr;
   const int32_t *__restrict__ ci = a.colidx;
-  const double *__restrict__ va = a.vals;
+  const T *__restrict__ va = static_cast<const T *>(a.vals);
+  const T *__restrict__ xs = static_cast<const T *>(a.x);
   const int64_t ntiles = (a.n + kSpmmTileRows - 1) / kSpmmTileRows;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t r0 = t * kSpmmTileRows;
@@ -95,90 +114,90 @@ __global__ void __launch_bounds__(kSpmmThreads) spmm_row_kernel(const SpmmArgs a
     if (r < r1) {
       const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
       if constexpr (KP == 1) {
-        double acc = 0.0;
+        T acc = 0;
         if (staged)
-          for (int e = e0; e < e1; ++e) acc = fma(s_val[e - te0], __ldg(a.x + s_col[e - te0]), acc);
+          for (int e = e0; e < e1; ++e) acc = fma(s_val[e - te0], __ldg(xs + s_col[e - te0]), acc);
         else
-          for (int e = e0; e < e1; ++e) acc = fma(__ldg(va + e), __ldg(a.x + __ldg(ci + e)), acc);
-        if constexpr (MODE == 1) acc = a.b[r] - acc;
-        a.y[r] = acc;
+          for (int e = e0; e < e1; ++e) acc = fma(__ldg(va + e), __ldg(xs + __ldg(ci + e)), acc);
+        if constexpr (MODE == 1) acc = static_cast<const T *>(a.b)[r] - acc;
+        static_cast<T *>(a.y)[r] = acc;
       } else {
-        const double2 *__restrict__ x2 = reinterpret_cast<const double2 *>(a.x);
-        double2 acc = make_double2(0.0, 0.0);
+        const T2 *__restrict__ x2 = static_cast<const T2 *>(a.x);
+        T2 acc = Vec2<T>::make(0, 0);
         if (staged) {
           for (int e = e0; e < e1; ++e) {
-            const double av = s_val[e - te0];
-            const double2 u = __ldg(x2 + s_col[e - te0]);
+            const T av = s_val[e - te0];
+            const T2 u = __ldg(x2 + s_col[e - te0]);
             acc.x = fma(av, u.x, acc.x);
             acc.y = fma(av, u.y, acc.y);
           }
         } else {
           for (int e = e0; e < e1; ++e) {
-            const double av = __ldg(va + e);
-            const double2 u = __ldg(x2 + __ldg(ci + e));
+            const T av = __ldg(va + e);
+            const T2 u = __ldg(x2 + __ldg(ci + e));
             acc.x = fma(av, u.x, acc.x);
             acc.y = fma(av, u.y, acc.y);
           }
         }
         if constexpr (MODE == 1) {
-          const double2 bv = reinterpret_cast<const double2 *>(a.b)[r];
-          acc = make_double2(bv.x - acc.x, bv.y - acc.y);
+          const T2 bv = static_cast<const T2 *>(a.b)[r];
+          acc = Vec2<T>::make(bv.x - acc.x, bv.y - acc.y);
         }
-        reinterpret_cast<double2 *>(a.y)[r] = acc;
+        static_cast<T2 *>(a.y)[r] = acc;
       }
     }
     __syncthreads();
   }
 }
 
-template <int KP, int MODE>
+template <typename T, int KP, int MODE>
 cudaError_t launch_kp(const SpmmArgs &a, int grid, cudaStream_t s) {
   if constexpr (KP <= 2) {
-    const size_t smem = (size_t)a.stage_cap * (sizeof(double) + sizeof(int32_t));
-    spmm_row_kernel<KP, MODE><<<grid, kSpmmThreads, smem, s>>>(a);
+    const size_t smem = (size_t)a.stage_cap * (sizeof(T) + sizeof(int32_t));
+    spmm_row_kernel<T, KP, MODE><<<grid, kSpmmThreads, smem, s>>>(a);
   } else {
-    spmm_group_kernel<KP, MODE><<<grid, kSpmmThreads, 0, s>>>(a);
+    spmm_group_kernel<T, KP, MODE><<<grid, kSpmmThreads, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
 
-template <int KP, int MODE>
+template <typename T, int KP, int MODE>
 int occ_kp(int stage_cap) {
   int nb = 0;
   cudaError_t e;
   if constexpr (KP <= 2)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_row_kernel<KP, MODE>, kSpmmThreads,
-                                                      (size_t)stage_cap * (sizeof(double) + sizeof(int32_t)));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_row_kernel<T, KP, MODE>, kSpmmThreads,
+                                                      (size_t)stage_cap * (sizeof(T) + sizeof(int32_t)));
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_group_kernel<KP, MODE>, kSpmmThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_group_kernel<T, KP, MODE>, kSpmmThreads, 0);
   if (e != cudaSuccess || nb < 1) return 1;
   return nb;
 }
 
-template <int MODE>
+template <typename T, int MODE>
 cudaError_t launch_mode(int kp, const SpmmArgs &a, int grid, cudaStream_t s) {
   switch (kp) {
-    case 1: return launch_kp<1, MODE>(a, grid, s);
-    case 2: return launch_kp<2, MODE>(a, grid, s);
-    case 4: return launch_kp<4, MODE>(a, grid, s);
-    case 8: return launch_kp<8, MODE>(a, grid, s);
-    case 16: return launch_kp<16, MODE>(a, grid, s);
-    case 32: return launch_kp<32, MODE>(a, grid, s);
-    case 64: return launch_kp<64, MODE>(a, grid, s);
+    case 1: return launch_kp<T, 1, MODE>(a, grid, s);
+    case 2: return launch_kp<T, 2, MODE>(a, grid, s);
+    case 4: return launch_kp<T, 4, MODE>(a, grid, s);
+    case 8: return launch_kp<T, 8, MODE>(a, grid, s);
+    case 16: return launch_kp<T, 16, MODE>(a, grid, s);
+    case 32: return launch_kp<T, 32, MODE>(a, grid, s);
+    case 64: return launch_kp<T, 64, MODE>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int MODE>
+template <typename T, int MODE>
 int occ_mode(int kp, int stage_cap) {
   switch (kp) {
-    case 1: return occ_kp<1, MODE>(stage_cap);
-    case 2: return occ_kp<2, MODE>(stage_cap);
-    case 4: return occ_kp<4, MODE>(stage_cap);
-    case 8: return occ_kp<8, MODE>(stage_cap);
-    case 16: return occ_kp<16, MODE>(stage_cap);
-    case 32: return occ_kp<32, MODE>(stage_cap);
-    case 64: return occ_kp<64, MODE>(stage_cap);
+    case 1: return occ_kp<T, 1, MODE>(stage_cap);
+    case 2: return occ_kp<T, 2, MODE>(stage_cap);
+    case 4: return occ_kp<T, 4, MODE>(stage_cap);
+    case 8: return occ_kp<T, 8, MODE>(stage_cap);
+    case 16: return occ_kp<T, 16, MODE>(stage_cap);
+    case 32: return occ_kp<T, 32, MODE>(stage_cap);
+    case 64: return occ_kp<T, 64, MODE>(stage_cap);
     default: return 1;
   }
 }
@@ -186,11 +205,17 @@ int occ_mode(int kp, int stage_cap) {
 }  // namespace
 
 cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s) {
-  return mode == 0 ? launch_mode<0>(kp, a, grid, s) : launch_mode<1>(kp, a, grid, s);
+  return mode == 0 ? launch_mode<double, 0>(kp, a, grid, s) : launch_mode<double, 1>(kp, a, grid, s);
 }
 
 int spmm_blocks_per_sm(int kp, int mode, int stage_cap) {
-  return mode == 0 ? occ_mode<0>(kp, stage_cap) : occ_mode<1>(kp, stage_cap);
+  return mode == 0 ? occ_mode<double, 0>(kp, stage_cap) : occ_mode<double, 1>(kp, stage_cap);
 }
+
+cudaError_t launch_spmm32(int kp, const SpmmArgs &a, int grid, cudaStream_t s) {
+  return launch_mode<float, 0>(kp, a, grid, s);
+}
+
+int spmm32_blocks_per_sm(int kp, int stage_cap) { return occ_mode<float, 0>(kp, stage_cap); }
 
 }  // namespace bicgk

@@ -20,6 +20,8 @@
 //   R5 zero denominator of omega -> omega = 0, other exact-zero divisors ->
 //      BREAKDOWN, non-finite scalars -> NONFINITE;
 //   R6 merged estimates (theta - omega*phi etc.) feed the stop test.
+#include <type_traits>
+
 #include "bicgk_dev.cuh"
 
 namespace bicgk {
@@ -50,7 +52,60 @@ __device__ __forceinline__ double2 sel2(bool u0, bool u1, double2 nv, double2 ov
 // Per-thread scalars of its two columns.
 struct Sc2 {
   double2 al, om, be;
+  float2 alf, omf, bef;  // the same scalars rounded to FP32 (FP32 inner solves)
   bool u0, u1;
+};
+
+// Float-float accumulator of one FP32 dot product per column (the FP32 inner solves): the
+// products are split exactly (p + e = u*w) and summed with an error-free two-sum, so a thread's
+// partial sum carries about 48 bits; it becomes one FP64 value before the FP64 grid reduction.
+struct FF2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float u, float w) {
+  const float p = __fmul_rn(u, w);
+  const float e = fmaf(u, w, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fadd_rn(s, -hi);
+  const float err = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bb)), __fadd_rn(p, -bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+__device__ __forceinline__ void dot_ff(FF2 &acc, float2 u, float2 w) {
+  ff_add(acc.hi.x, acc.lo.x, u.x, w.x);
+  ff_add(acc.hi.y, acc.lo.y, u.y, w.y);
+}
+__device__ __forceinline__ double2 to_d2(const double2 &a) { return a; }
+__device__ __forceinline__ double2 to_d2(const FF2 &a) {
+  return make_double2((double)a.hi.x + (double)a.lo.x, (double)a.hi.y + (double)a.lo.y);
+}
+__device__ __forceinline__ void acc_zero(double2 &a) { a = make_double2(0.0, 0.0); }
+__device__ __forceinline__ void acc_zero(FF2 &a) {
+  a.hi = make_float2(0.f, 0.f);
+  a.lo = make_float2(0.f, 0.f);
+}
+__device__ __forceinline__ float2 ld2f(const double *p, int64_t i) {
+  return reinterpret_cast<const float2 *>(p)[i];
+}
+__device__ __forceinline__ void st2f(double *p, int64_t i, float2 v) { reinterpret_cast<float2 *>(p)[i] = v; }
+__device__ __forceinline__ float2 fma2f(float2 s, float2 x, float2 y) {
+  return make_float2(fmaf(s.x, x.x, y.x), fmaf(s.y, x.y, y.y));
+}
+__device__ __forceinline__ float2 neg2f(float2 s) { return make_float2(-s.x, -s.y); }
+__device__ __forceinline__ float2 sel2f(bool u0, bool u1, float2 nv, float2 ov) {
+  return make_float2(u0 ? nv.x : ov.x, u1 ? nv.y : ov.y);
+}
+
+// Vector and accumulator types of an op (FP64 ops leave them at the default).
+template <class D, class = void>
+struct OpTypes {
+  using V2 = double2;
+  using Acc = double2;
+};
+template <class D>
+struct OpTypes<D, std::void_t<typename D::V2>> {
+  using V2 = typename D::V2;
+  using Acc = typename D::Acc;
 };
 
 // ------------------------------------------------------------------ scalar rules
@@ -69,9 +124,9 @@ __device__ __forceinline__ double sub_rn(double x, double y) { return __dadd_rn(
 enum Fin : int {
   FIN_NONE = 0, FIN_SETUP, FIN_RW0, FIN_DELTA, FIN_G1, FIN_RHO, FIN_STORE_D0, FIN_STORE_D1, FIN_STORE_D2,
   FIN_PSI, FIN_RR, FIN_R4_MERGED, FIN_R4_PLAIN, FIN_PG1_MERGED, FIN_PG1_PLAIN, FIN_PG3_MERGED,
-  FIN_PG3_PLAIN, FIN_TRUE
+  FIN_PG3_PLAIN, FIN_TRUE, FIN_IR_SETUP, FIN_IR_RESID
 };
-enum Ctl_ : int { CTL_NONE = 0, CTL_START = 1, CTL_END_ITER = 2 };
+enum Ctl_ : int { CTL_NONE = 0, CTL_START = 1, CTL_END_ITER = 2, CTL_OUTER = 3 };
 
 // Column c, executed by thread c of the last block.  s[d*kp + c] = dot d of column c.
 template <int FIN>
@@ -91,7 +146,7 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
     FL(F_ITERS, c) = 0;
     FL(F_XUPD, c) = 0;
     FL(F_XZERO, c) = 0;
-    if (c >= ctl->k) {  // padding column: finished before the loop
+    if (c >= ctl->k || (a.ext_act && !a.ext_act[c])) {  // padding column (or finished outer column)
       FL(F_ACT, c) = 0;
       FL(F_STATUS, c) = ST_CONVERGED;
       return;
@@ -261,6 +316,39 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
     // ||b - A x|| / ||b|| of the final iterate
     const double bn2 = SC(S_BN2, c);
     SC(S_TRUE, c) = bn2 == 0.0 ? 0.0 : __ddiv_rn(__dsqrt_rn(s[c]), __dsqrt_rn(bn2));
+  } else if constexpr (FIN == FIN_IR_SETUP) {
+    // refinement set-up: ||b||^2, eps^2 = tol^2 ||b||^2, zero and padding columns
+    const double bn2 = s[c];
+    SC(S_BN2, c) = bn2;
+    SC(S_EPS2, c) = __dmul_rn(__dmul_rn(ctl->tol, ctl->tol), bn2);
+    SC(S_TRUE, c) = 0.0;
+    FL(F_ITERS, c) = 0;
+    FL(F_XZERO, c) = 0;
+    int act = 1, st = ST_MAXIT;
+    if (c >= ctl->k) {
+      act = 0;
+      st = ST_CONVERGED;
+    } else if (bn2 == 0.0) {
+      FL(F_XZERO, c) = 1;
+      act = 0;
+      st = ST_CONVERGED;
+    } else if (!fin1(bn2)) {
+      act = 0;
+      st = ST_NONFINITE;
+    }
+    FL(F_ACT, c) = act;
+    FL(F_STATUS, c) = st;
+  } else if constexpr (FIN == FIN_IR_RESID) {
+    // refinement pass j: true residual r = b - A x in FP64; stop, or refine once more
+    if (!FL(F_ACT, c)) return;
+    const int j = ctl->iter;
+    const double rr = s[c], bn2 = SC(S_BN2, c);
+    ctl->hist[(int64_t)j * kp + c] = hist_value(rr);
+    SC(S_TRUE, c) = __ddiv_rn(__dsqrt_rn(rr), __dsqrt_rn(bn2));
+    if (!fin1(rr)) col_stop(a, c, ST_NONFINITE);
+    else if (rr < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
+    else if (j >= ctl->maxit) col_stop(a, c, ST_MAXIT);
+    else FL(F_ITERS, c) = j + 1;
   }
 }
 
@@ -275,7 +363,10 @@ __device__ void fin_ctl(const KArgs &a) {
     for (int c = 0; c < a.kp; ++c) any |= FL(F_ACT, c);
     ctl->any_active = any;
     int go;
-    if constexpr (CTL == CTL_START) {
+    if constexpr (CTL == CTL_OUTER) {
+      ctl->iter += 1;  // refinement passes: the host drives this loop
+      return;
+    } else if constexpr (CTL == CTL_START) {
       go = any && ctl->maxit > 0;
     } else {
       const int j = ctl->iter + 1;
@@ -629,6 +720,96 @@ template <> struct OpDef<OP_DOT_R0S> : DotOp<V_R0, V_S, FIN_PG3_PLAIN, CTL_END_I
 // ---- final residual norm (V_TMP holds b - A x)
 template <> struct OpDef<OP_TRUE_RES> : DotOp<V_TMP, V_TMP, FIN_TRUE, CTL_NONE> {};
 
+// ---- mixed-precision refinement, FP32 inner solve (roles hold float arrays)
+struct Op32 {
+  using V2 = float2;
+  using Acc = FF2;
+};
+template <>
+struct OpDef<OP32_SETUP> : Op32 {  // d_0 = 0, r_0 = b, r^_0 = r_0, p_0 = r_0; (b,b), (r_0,r_0)
+  static constexpr int ND = 2, FIN = FIN_SETUP, CTL = CTL_START, NL = 1;
+  __device__ static void load(const KArgs &a, int64_t i, float2 (&v)[NL]) { v[0] = ld2f(V(V_B), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const float2 (&v)[NL], const Sc2 &, FF2 (&acc)[ND]) {
+    st2f(V(V_X), i, make_float2(0.f, 0.f));
+    st2f(V(V_R), i, v[0]);
+    st2f(V(V_R0), i, v[0]);
+    st2f(V(V_P), i, v[0]);
+    dot_ff(acc[0], v[0], v[0]);
+    dot_ff(acc[1], v[0], v[0]);
+  }
+};
+template <>
+struct OpDef<OP32_DELTA> : Op32 {  // delta = (v, r^_0)
+  static constexpr int ND = 1, FIN = FIN_DELTA, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, float2 (&v)[NL]) { v[0] = ld2f(V(V_V), i); v[1] = ld2f(V(V_R0), i); }
+  __device__ static void comp(const KArgs &, int64_t, const float2 (&v)[NL], const Sc2 &, FF2 (&acc)[ND]) {
+    dot_ff(acc[0], v[0], v[1]);
+  }
+};
+template <>
+struct OpDef<OP32_UPD_S> : Op32 {  // s = r - alpha v
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, float2 (&v)[NL]) { v[0] = ld2f(V(V_R), i); v[1] = ld2f(V(V_V), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const float2 (&v)[NL], const Sc2 &s, FF2 (&)[1]) {
+    st2f(V(V_S), i, fma2f(neg2f(s.alf), v[1], v[0]));
+  }
+};
+template <>
+struct OpDef<OP32_G1> : Op32 {  // phi = (t,s), psi = (t,t), theta = (s,s)
+  static constexpr int ND = 3, FIN = FIN_G1, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, float2 (&v)[NL]) { v[0] = ld2f(V(V_T), i); v[1] = ld2f(V(V_S), i); }
+  __device__ static void comp(const KArgs &, int64_t, const float2 (&v)[NL], const Sc2 &, FF2 (&acc)[ND]) {
+    dot_ff(acc[0], v[0], v[1]);
+    dot_ff(acc[1], v[0], v[0]);
+    dot_ff(acc[2], v[1], v[1]);
+  }
+};
+template <>
+struct OpDef<OP32_G3> : Op32 {  // d += alpha p + omega s; r = s - omega t; rho = (r, r^_0)
+  static constexpr int ND = 1, FIN = FIN_RHO, CTL = CTL_END_ITER, NL = 5;
+  __device__ static void load(const KArgs &a, int64_t i, float2 (&v)[NL]) {
+    v[0] = ld2f(V(V_X), i); v[1] = ld2f(V(V_P), i); v[2] = ld2f(V(V_S), i); v[3] = ld2f(V(V_T), i); v[4] = ld2f(V(V_R0), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const float2 (&v)[NL], const Sc2 &s, FF2 (&acc)[ND]) {
+    const float2 xn = fma2f(s.omf, v[2], fma2f(s.alf, v[1], v[0]));
+    if (s.u0 | s.u1) st2f(V(V_X), i, sel2f(s.u0, s.u1, xn, v[0]));
+    const float2 r = fma2f(neg2f(s.omf), v[3], v[2]);
+    st2f(V(V_R), i, r);
+    dot_ff(acc[0], r, v[4]);
+  }
+};
+template <>
+struct OpDef<OP32_UPD_P> : Op32 {  // p = r + beta (p - omega v)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, float2 (&v)[NL]) { v[0] = ld2f(V(V_R), i); v[1] = ld2f(V(V_P), i); v[2] = ld2f(V(V_V), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const float2 (&v)[NL], const Sc2 &s, FF2 (&)[1]) {
+    st2f(V(V_P), i, fma2f(s.bef, fma2f(neg2f(s.omf), v[2], v[1]), v[0]));
+  }
+};
+
+// ---- mixed-precision refinement, FP64 outer steps (V_Q: FP32 b of the inner solve, V_Y: its d)
+template <> struct OpDef<OP_IR_SETUP> : DotOp<V_B, V_B, FIN_IR_SETUP, CTL_NONE> {};
+template <>
+struct OpDef<OP_IR_RESID> {  // (r, r) of r = b - A x; the inner right-hand side b32 = fl32(r)
+  static constexpr int ND = 1, FIN = FIN_IR_RESID, CTL = CTL_OUTER, NL = 1;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_R), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &, double2 (&acc)[ND]) {
+    st2f(V(V_Q), i, make_float2((float)v[0].x, (float)v[0].y));
+    dot_acc(acc[0], v[0], v[0]);
+  }
+};
+template <>
+struct OpDef<OP_IR_UPDATE> {  // x += d for the columns this pass refines
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 1;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_X), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    if (!(s.u0 | s.u1)) return;
+    const float2 d = ld2f(V(V_Y), i);
+    const double2 xn = make_double2(v[0].x + (double)d.x, v[0].y + (double)d.y);
+    st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+  }
+};
+
 #undef V
 
 // ------------------------------------------------------------------ the kernel
@@ -685,14 +866,47 @@ __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND :
     for (int w = 0; w < kVecThreads / 32; ++w) s += sm.red[w][d][c];
     mypart[d * kMaxKp + c] = s;
   }
+  // Fixed-order sum of the block partials; no block ever waits for another.  With few partial
+  // sums (grid x outputs <= kOneLevelMax) the last block to arrive adds them all in block order.
+  // With many, that single block's FP64 additions would dominate, so the sum goes in two
+  // levels: the last block of each group of kRedGroup blocks adds its group (ascending block
+  // order) into a group partial, and the last group to finish adds the group partials.
+  constexpr int kStride = kMaxDots * kMaxKp;
+  constexpr int kOneLevelMax = 8192;
+  const int nblk = gridDim.x;
+  const bool two_level = nblk * nout > kOneLevelMax;
+  const int ngrp = two_level ? (nblk + kRedGroup - 1) / kRedGroup : 1;
+  const double *top = a.part;  // partials the final block adds: block partials or group partials
   __threadfence();
   __syncthreads();
+  if (two_level) {
+    const int g = blockIdx.x / kRedGroup;
+    const int g0 = g * kRedGroup;
+    const int gsz = (g0 + kRedGroup < nblk) ? kRedGroup : nblk - g0;
+    if (threadIdx.x == 0) sm.ticket = atomicAdd(&a.ctl->gticket[g], 1u);
+    __syncthreads();
+    if (sm.ticket != (unsigned)gsz - 1) return;
+    __threadfence();
+    double *gpart = a.part + (size_t)(nblk + g) * kStride;
+    for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+      const int d = t / kp, c = t - d * kp;
+      const double *src = a.part + (size_t)g0 * kStride + d * kMaxKp + c;
+      double s = 0.0;
+#pragma unroll 4
+      for (int b = 0; b < gsz; ++b) s += __ldcg(src + (size_t)b * kStride);
+      gpart[d * kMaxKp + c] = s;
+    }
+    if (threadIdx.x == 0) a.ctl->gticket[g] = 0;
+    __threadfence();
+    __syncthreads();
+    top = a.part + (size_t)nblk * kStride;
+  }
   if (threadIdx.x == 0) sm.ticket = atomicAdd(&a.ctl->ticket, 1u);
   __syncthreads();
-  if (sm.ticket != gridDim.x - 1) return;
+  const int ntop = two_level ? ngrp : nblk;
+  if (sm.ticket != (unsigned)ngrp - 1 + (two_level ? 0 : nblk - 1)) return;
   __threadfence();
-  // last block: fixed-order sum of the block partials
-  int tpo = 32;
+  int tpo = 32;  // lanes per output in the final sum (strided, then a butterfly)
   while (tpo > 1 && tpo * nout > (int)blockDim.x) tpo >>= 1;
   const int groups = blockDim.x / tpo;
   for (int o0 = 0; o0 < nout; o0 += groups) {
@@ -700,7 +914,8 @@ __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND :
     double s = 0.0;
     if (o < nout) {
       const int d = o / kp, c = o - d * kp;
-      for (int b = sub; b < (int)gridDim.x; b += tpo) s += __ldcg(a.part + (size_t)b * (kMaxDots * kMaxKp) + d * kMaxKp + c);
+#pragma unroll 4
+      for (int b = sub; b < ntop; b += tpo) s += __ldcg(top + (size_t)b * kStride + d * kMaxKp + c);
     }
     for (int m = tpo >> 1; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
     if (o < nout && sub == 0) sm.sums[o] = s;
@@ -727,55 +942,70 @@ __global__ void __launch_bounds__(kVecThreads, 2) vec_kernel(const KArgs a) {
   s.al = make_double2(SC(S_ALPHA, c0), SC(S_ALPHA, c1));
   s.om = make_double2(SC(S_OMEGA, c0), SC(S_OMEGA, c1));
   s.be = make_double2(SC(S_BETA, c0), SC(S_BETA, c1));
-  s.u0 = FL(F_XUPD, c0) != 0;
-  s.u1 = FL(F_XUPD, c1) != 0;
-  double2 acc[ND > 0 ? ND : 1];
+  s.alf = make_float2((float)s.al.x, (float)s.al.y);
+  s.omf = make_float2((float)s.om.x, (float)s.om.y);
+  s.bef = make_float2((float)s.be.x, (float)s.be.y);
+  // the x-update mask: columns that form x_{j+1} (refinement update: columns the pass refines)
+  const int mflag = OP == OP_IR_UPDATE ? F_ACT : F_XUPD;
+  s.u0 = FL(mflag, c0) != 0;
+  s.u1 = FL(mflag, c1) != 0;
+  using V2 = typename OpTypes<D>::V2;
+  using Acc = typename OpTypes<D>::Acc;
+  Acc acc[ND > 0 ? ND : 1];
 #pragma unroll
-  for (int d = 0; d < (ND > 0 ? ND : 1); ++d) acc[d] = make_double2(0.0, 0.0);
+  for (int d = 0; d < (ND > 0 ? ND : 1); ++d) acc_zero(acc[d]);
   // chunks of two doubles; an odd total (kp == 1, odd n) ends in a zero pad element
   const int64_t n2 = (a.n * kp + 1) >> 1;
   int64_t i = gtid;
   for (; i + stride < n2; i += 2 * stride) {
-    double2 va[D::NL], vb[D::NL];
+    V2 va[D::NL], vb[D::NL];
     D::load(a, i, va);
     D::load(a, i + stride, vb);
     D::comp(a, i, va, s, acc);
     D::comp(a, i + stride, vb, s, acc);
   }
   if (i < n2) {
-    double2 va[D::NL];
+    V2 va[D::NL];
     D::load(a, i, va);
     D::comp(a, i, va, s, acc);
   }
-  if constexpr (ND > 0) reduce_and_finalize<D>(a, acc);
+  if constexpr (ND > 0) {
+    double2 accd[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) accd[d] = to_d2(acc[d]);
+    reduce_and_finalize<D>(a, accd);
+  }
 }
 
 // ------------------------------------------------------------------ pack / unpack / reset
 
-__global__ void pack_kernel(const double *__restrict__ B, const double *__restrict__ X0, int k, KArgs a) {
+// Columns [0, ncols) of a caller block with leading dimension ld (B, X0 already offset to the
+// first column of this group) into the workspace layout (ld = kp, zero padding columns).
+__global__ void pack_kernel(const double *__restrict__ B, const double *__restrict__ X0, int ld, int ncols,
+                            KArgs a) {
   const int kp = a.kp;
   const int64_t m = a.n * kp;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
     const int64_t i = e / kp;
     const int c = (int)(e - i * kp);
-    const bool real = c < k;
-    a.v[V_B][e] = real ? B[i * k + c] : 0.0;
-    a.v[V_X][e] = (real && X0) ? X0[i * k + c] : 0.0;
+    const bool real = c < ncols;
+    a.v[V_B][e] = real ? B[i * ld + c] : 0.0;
+    a.v[V_X][e] = (real && X0) ? X0[i * ld + c] : 0.0;
   }
   // zero pad element of odd-length blocks (kp == 1): every role
   if ((m & 1) && blockIdx.x == 0 && threadIdx.x < V_NVEC) a.v[threadIdx.x][m] = 0.0;
 }
 
-__global__ void unpack_kernel(double *__restrict__ X, int k, KArgs a, int role, int use_xzero) {
+__global__ void unpack_kernel(double *__restrict__ X, int ld, int ncols, KArgs a, int role, int use_xzero) {
   const int kp = a.kp;
-  const int64_t m = a.n * k;
+  const int64_t m = a.n * ncols;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const double *src = a.v[role];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    const int64_t i = e / k;
-    const int c = (int)(e - i * k);
-    X[e] = (use_xzero && FL(F_XZERO, c)) ? 0.0 : src[i * kp + c];
+    const int64_t i = e / ncols;
+    const int c = (int)(e - i * ncols);
+    X[i * ld + c] = (use_xzero && FL(F_XZERO, c)) ? 0.0 : src[i * kp + c];
   }
 }
 
@@ -861,6 +1091,15 @@ const OpInfo kOps[OP_COUNT] = {
     OPI(OP_DOT_R0W, "dot_sigma", 2, 0),
     OPI(OP_DOT_R0S, "dot_delta", 2, 0),
     OPI(OP_TRUE_RES, "dot_true_residual", 1, 0),
+    OPI(OP32_SETUP, "fp32_setup", 1, 4),
+    OPI(OP32_DELTA, "fp32_dot_delta", 2, 0),
+    OPI(OP32_UPD_S, "fp32_upd_s", 2, 1),
+    OPI(OP32_G1, "fp32_merged_phi_psi_theta", 2, 0),
+    OPI(OP32_G3, "fp32_merged_x_r_rho", 5, 2),
+    OPI(OP32_UPD_P, "fp32_upd_p", 3, 1),
+    OPI(OP_IR_SETUP, "ir_dot_b", 1, 0),
+    OPI(OP_IR_RESID, "ir_resid_to_fp32", 1, 1),
+    OPI(OP_IR_UPDATE, "ir_update_x", 2, 1),
 };
 #undef OPI
 
@@ -879,14 +1118,27 @@ cudaError_t launch_vec(int op, const KArgs &a, int grid, cudaStream_t s) {
 }
 int vec_blocks_per_sm(int op) { return (op >= 0 && op < OP_COUNT) ? kOps[op].occ() : 1; }
 
-cudaError_t launch_pack(const double *B, const double *X0, int k, const KArgs &a, cudaStream_t s) {
-  pack_kernel<<<1024, 256, 0, s>>>(B, X0, k, a);
+cudaError_t launch_pack(const double *B, const double *X0, int ld, int ncols, const KArgs &a, cudaStream_t s) {
+  pack_kernel<<<1024, 256, 0, s>>>(B, X0, ld, ncols, a);
   return cudaGetLastError();
 }
-cudaError_t launch_unpack_role(double *X, int k, const KArgs &a, int role, int use_xzero, cudaStream_t s) {
-  unpack_kernel<<<1024, 256, 0, s>>>(X, k, a, role, use_xzero);
+cudaError_t launch_unpack_role(double *X, int ld, int ncols, const KArgs &a, int role, int use_xzero,
+                               cudaStream_t s) {
+  unpack_kernel<<<1024, 256, 0, s>>>(X, ld, ncols, a, role, use_xzero);
   return cudaGetLastError();
 }
+namespace {
+__global__ void to_float_kernel(const double *__restrict__ src, float *__restrict__ dst, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) dst[e] = (float)src[e];
+}
+}  // namespace
+
+cudaError_t launch_to_float(const double *src, float *dst, int64_t n, cudaStream_t s) {
+  if (n > 0) to_float_kernel<<<1024, 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reset(const KArgs &a, int64_t hist_len, cudaStream_t s) {
   reset_kernel<<<64, 256, 0, s>>>(a, hist_len);
   return cudaGetLastError();

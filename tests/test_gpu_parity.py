@@ -271,3 +271,24 @@ def test_bad_csr_rejected(bk, cuda):
         bk.csr_create(rowptr, np.array([0, 1], dtype=np.int32), np.ones(2))
     with pytest.raises(bk.BicgkError):
         bk.csr_create(np.array([0, 1, 2], dtype=np.int32), np.array([0, 5], dtype=np.int32), np.ones(2))
+
+
+def test_rhs_groups_match_single_group(bk, cuda):
+    """k >= 16 runs as two concurrent column groups; it must agree with one group (and the oracle)."""
+    torch = cuda
+    A = I.convdiff7(12, peclet=True)
+    B = I.rhs(A.n, 20, 4)                       # groups of 10 + 10 columns (kp 16) vs one group (kp 32)
+    Bd = torch.from_numpy(B).cuda()
+    with bk.Operator(A) as one, bk.Operator(A) as two:
+        bk.set_option(one.handle, bk.OPT_RHS_GROUPS, 1)
+        for flags, maxit, tol in ((1, 8, 0.0), (0, 500, 1e-8)):
+            r1 = one.solve(Bd, tol=tol, maxit=maxit, flags=flags)
+            r2 = two.solve(Bd, tol=tol, maxit=maxit, flags=flags)
+            assert bk.last_stats(two.handle)["kernel_launches"] > bk.last_stats(one.handle)["kernel_launches"]
+            X1, X2 = r1.X.cpu().numpy(), r2.X.cpu().numpy()
+            assert np.all(np.abs(r1.iters - r2.iters) <= 1) and np.array_equal(r1.status, r2.status)
+            assert np.all(_colerr(X2, X1) <= (1e-12 if flags else 1e-10))
+        rh = two.solve(B, tol=1e-8, maxit=500)  # host buffers, two groups: same as the device call
+        assert np.array_equal(rh.X, r2.X.cpu().numpy()) and np.array_equal(rh.iters, r2.iters)
+    ro = oracle.solve(A, B, tol=1e-8, maxit=500)
+    _compare(r2, X2, ro)

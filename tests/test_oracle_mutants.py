@@ -37,6 +37,8 @@ MUTANTS = {
                                   "double wn = AT(y, i) - omega * AT(t, i);"),
     "spmv skips the last entry": ("e < A->rowptr[i + 1]; ++e) acc +=", "e < A->rowptr[i + 1] - 1; ++e) acc +="),
     "stop test 10x too loose": ("est < eps2)", "est < 100.0 * eps2)"),
+    "refinement subtracts d": ("AT(x, i) = AT(x, i) + (double)AT(d32, i);", "AT(x, i) = AT(x, i) - (double)AT(d32, i);"),
+    "fp32 inner r update sign": ("AT(r, i) = si - of * AT(t, i);", "AT(r, i) = si + of * AT(t, i);"),
 }
 
 
@@ -49,6 +51,7 @@ def _compile(src: str, tag: str):
     lib = ctypes.CDLL(so)
     i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
     lib.oracle_solve.argtypes = [ctypes.c_int, i64, vp, vp, vp, i32, vp, vp, dbl, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.oracle_solve_mixed.argtypes = [i64, vp, vp, vp, i32, vp, vp, dbl, i32, dbl, i32, vp, vp, vp, vp, vp, vp]
     return lib
 
 
@@ -97,6 +100,15 @@ def _pins_pass(lib) -> bool:
             return False
         if (tr[0], tr[1]) != (3 * 2 * TABLE2[v][0], 3 * 2 * TABLE2[v][1]):
             return False
+    # mixed-precision refinement: FP64 accuracy from FP32 inner solves
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    X = np.empty_like(B)
+    oi, ii, st = np.zeros(2, np.int32), np.zeros(2, np.int32), np.zeros(2, np.int32)
+    hist, trr = np.empty((31, 2)), np.empty(2)
+    lib.oracle_solve_mixed(A.n, p(A.rowptr), p(A.colidx), p(A.vals), 2, p(B), None, 1e-13, 30, 1e-5, 500, p(X),
+                           p(oi), p(ii), p(st), p(hist), p(trr))
+    if not np.all(st == 0) or np.max(np.linalg.norm(X - Xd, axis=0) / np.linalg.norm(Xd, axis=0)) > 1e-9:
+        return False
     return True
 
 

@@ -275,3 +275,50 @@ def test_vector_traffic_matches_table2():
         assert copies == m * g["preconditioner_copies_per_iteration"][v] + setup_copies
         setup_spmv = 1 + (2 if v.startswith("pipelined") else 0) + 1   # r_0, (w_0, t_0), true residual
         assert spmv == m * g["spmv_per_iteration"] + setup_spmv
+
+
+# ------------------------------------------------------------------ mixed-precision refinement
+
+def test_mixed_reaches_fp64_accuracy_lapack():
+    """FP32 inner solves inside FP64 refinement still reach the FP64 solution (LAPACK)."""
+    for A in (I.perturbed27(4, seed=2), I.convdiff7(5, peclet=True)):
+        B = I.rhs(A.n, 2, 7)
+        D = A.to_dense()
+        Xd = np.linalg.solve(D, B)
+        r = oracle.solve_mixed(A, B, tol=1e-13, max_outer=30, inner_tol=1e-5)
+        assert np.all(r.status == oracle.CONVERGED)
+        assert np.all(r.outer_iters >= 2)              # one FP32 solve cannot reach 1e-13
+        err = np.linalg.norm(r.X - Xd, axis=0) / np.linalg.norm(Xd, axis=0)
+        assert np.all(err <= 10 * np.linalg.cond(D) * 1e-13), err
+
+
+def test_mixed_each_pass_contracts_by_the_inner_tolerance():
+    """||r_{j+1}|| <= ~inner_tol ||r_j||: x += d with d solving A d = r to inner_tol."""
+    A = I.perturbed27(8, seed=4)
+    B = I.rhs(A.n, 3, 5)
+    r = oracle.solve_mixed(A, B, tol=1e-12, max_outer=20, inner_tol=1e-4)
+    assert np.all(r.status == oracle.CONVERGED)
+    for c in range(3):
+        h = r.hist[: r.outer_iters[c] + 1, c]
+        assert np.all(h[1:] / h[:-1] < 1e-3), h
+    gap = np.linalg.norm(B - A.to_scipy() @ r.X, axis=0) / np.linalg.norm(B, axis=0)
+    np.testing.assert_allclose(gap, r.true_relres, rtol=1e-6)
+    assert np.all(gap < 1e-12)
+
+
+def test_mixed_edge_columns():
+    A = I.convdiff7(5)
+    B = I.rhs(A.n, 3, 1)
+    B[:, 1] = 0.0
+    X0 = np.ones_like(B)
+    r = oracle.solve_mixed(A, B, X0=X0, tol=1e-10, max_outer=10)
+    assert r.status[1] == oracle.CONVERGED and r.outer_iters[1] == 0 and np.all(r.X[:, 1] == 0)
+    r0 = oracle.solve_mixed(A, B, X0=X0, tol=1e-10, max_outer=0)
+    assert r0.status[0] == oracle.MAXIT and r0.outer_iters[0] == 0
+    np.testing.assert_array_equal(r0.X[:, 0], 1.0)
+    n = 40
+    A2 = I.CSR(np.arange(n + 1), np.arange(n), np.full(n, 2.0))
+    B2 = I.rhs(n, 2, 3)
+    r2 = oracle.solve_mixed(A2, B2, tol=1e-15, max_outer=10)
+    assert np.all(r2.status == oracle.CONVERGED) and np.all(r2.outer_iters <= 3)
+    assert np.all(np.linalg.norm(r2.X - B2 / 2, axis=0) <= 2e-15 * np.linalg.norm(B2 / 2, axis=0))
