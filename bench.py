@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-mixed", action="store_true",
                    help="skip the mixed-precision comparison (27-point 128^3, k = 32, rel tol 1e-10)")
     p.add_argument("--mixed-grid", type=int, default=128)
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the batching comparison (64 systems, grids 16^3..64^3, 1..8 RHS)")
     p.add_argument("--eager", action="store_true",
                    help="run every solve in the library's host-loop mode (same kernels, one launch at a time, "
                         "CUDA events around each) instead of the CUDA graph; profilers cannot see kernels inside "
@@ -310,6 +312,45 @@ def mixed_section(args, bicgk, inputs, torch, dev):
     return res
 
 
+def batch_section(args, bicgk, inputs, torch, dev, nsys=64):
+    """64 independent 7-point convection-diffusion systems, grids U{16..64}^3, k U{1..8}, rel tol 1e-8.
+
+    Autotuned launch shapes; the batched graph (one launch for all systems) against the
+    per-system launch loop (bicgk_solve per system) with the same shapes; CUDA events.
+    """
+    u = inputs.uniform01(11, 2 * nsys)
+    grids = [int(16 + np.floor(x * 49)) for x in u[:nsys]]
+    ks = [int(1 + np.floor(x * 8)) for x in u[nsys:]]
+    csrs = [inputs.convdiff7(n) for n in grids]
+    Bs = [torch.from_numpy(inputs.rhs(c.n, k, 200 + i)).to(dev) for i, (c, k) in enumerate(zip(csrs, ks))]
+    Xs = [torch.empty_like(b) for b in Bs]
+    res = {"workload": f"{nsys} convdiff7 systems, grids U{{16..64}}^3, k U{{1..8}}, rel tol 1e-8, classical_merged",
+           "rows_total": int(sum(c.n for c in csrs)), "rhs_total": int(sum(ks))}
+    with bicgk.Batch(csrs, ks) as bt:
+        t0 = time.perf_counter()
+        bt.tune(reps=5)
+        torch.cuda.synchronize()
+        res["tune_s"] = time.perf_counter() - t0
+        out = {}
+        for name, mode in (("graph", bicgk.BATCH_GRAPH), ("loop", bicgk.BATCH_LOOP)):
+            bt.solve(Bs, Xs, tol=1e-8, maxit=5000, mode=mode)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            reps = 3
+            for _ in range(reps):
+                _, iters, status, trr = bt.solve(Bs, Xs, tol=1e-8, maxit=5000, mode=mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out[name] = {"ms": ms, "rhs_iterations_per_s": float(iters.sum()) / (ms / 1e3),
+                         "kernel_launches": bt.last_launches(), "converged": bool((status == 0).all()),
+                         "max_true_relres": float(trr.max())}
+        res.update(out)
+        res["graph_speedup_vs_loop"] = out["loop"]["ms"] / out["graph"]["ms"]
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -448,6 +489,10 @@ def main():
     # mixed precision (FP32 inner solves in FP64 refinement) vs FP64 on the same GPU
     if not args.no_mixed and rank == 0:
         out["mixed_precision"] = mixed_section(args, bicgk, inputs, torch, dev)
+
+    # batch of 64 uneven systems: one graph launch vs the per-system launch loop
+    if not args.no_batch and rank == 0:
+        out["batching"] = batch_section(args, bicgk, inputs, torch, dev)
 
     # CPU oracle on the host cores (rank 0, N = 1 only)
     if not args.no_cpu and rank == 0 and world == 1:

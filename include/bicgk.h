@@ -211,6 +211,39 @@ enum bicgk_option {
  */
 int bicgk_set_option(bicgk_op A, int option, int64_t value);
 
+/*
+ * Batches: many independent systems of uneven size and RHS count, solved together (no
+ * counterpart in the paper; a GPU systems extension that does not change the method).
+ *
+ * bicgk_batch_create: system i is the CSR matrix (n_rows[i], nnz[i], rowptr[i], colidx[i],
+ *   vals[i]) in space `mem` (validated and copied as by bicgk_csr_create) with k[i] right-hand
+ *   sides (1..BICGK_MAX_K).  1 <= nsys <= 4096.
+ * bicgk_batch_tune: autotuner.  For every system, times its streaming kernel (group 3 of
+ *   Algorithm 2) over grid sizes of 1..64 double2 chunks per thread, and its SpMM over
+ *   1..64 passes of rows per block (rows per CTA) and 2 or 4 columns per lane (RHS-tile width,
+ *   kp >= 8), `reps` launches each, and keeps the fastest.  Writes the chosen grid sizes and
+ *   tile widths to the nullable arrays [nsys].  The shapes apply to both solve modes.
+ * bicgk_batch_solve: B[i], X0[i] (X0 nullable, or entries nullable), X[i] are DEVICE arrays of
+ *   n_rows[i]*k[i] FP64 in the layout of bicgk_solve; every other argument as there.  iters,
+ *   status, true_relres (nullable) are host arrays of sum(k) entries, systems in order.
+ *   mode BICGK_BATCH_GRAPH: one CUDA-graph launch with an independent branch (set-up,
+ *   conditional WHILE loop, true residual) per system; BICGK_BATCH_LOOP: bicgk_solve on each
+ *   system in turn (the per-system launch loop).  Residual histories are not returned.
+ * bicgk_batch_last_launches: kernels the last bicgk_batch_solve launched.
+ */
+typedef struct bicgk_batch_s *bicgk_batch;
+enum bicgk_batch_mode { BICGK_BATCH_GRAPH = 0, BICGK_BATCH_LOOP = 1 };
+int bicgk_batch_create(bicgk_batch *out, int32_t nsys, const int64_t *n_rows, const int64_t *nnz,
+                       const int32_t *const *rowptr, const int32_t *const *colidx, const double *const *vals,
+                       const int32_t *k, int mem, void *stream);
+int bicgk_batch_tune(bicgk_batch b, int32_t reps, int32_t *vec_grid_out, int32_t *spmm_grid_out,
+                     int32_t *spmm_cpl_out, void *stream);
+int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const *X0, double *const *X,
+                      double rel_tol, int32_t maxit, int variant, int32_t flags, int mode, int32_t *iters,
+                      int32_t *status, double *true_relres, void *stream);
+int bicgk_batch_last_launches(bicgk_batch b, int64_t *kernel_launches);
+int bicgk_batch_destroy(bicgk_batch b);
+
 /* Release the operator and all device memory it holds.  NULL is accepted. */
 int bicgk_op_destroy(bicgk_op A);
 

@@ -60,6 +60,16 @@ def _load():
             lib.bicgk_version.restype = ctypes.c_char_p
             lib.bicgk_solve_mixed.argtypes = [vp, i32, vp, vp, dbl, i32, dbl, i32, ctypes.c_int, vp, vp, vp, vp,
                                               vp, vp, vp]
+            pp = ctypes.POINTER(ctypes.c_void_p)
+            lib.bicgk_batch_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, pp, pp, pp, vp, ctypes.c_int, vp]
+            lib.bicgk_batch_tune.argtypes = [vp, i32, vp, vp, vp, vp]
+            lib.bicgk_batch_solve.argtypes = [vp, pp, pp, pp, dbl, i32, ctypes.c_int, i32, ctypes.c_int, vp, vp,
+                                              vp, vp]
+            lib.bicgk_batch_last_launches.argtypes = [vp, ctypes.POINTER(i64)]
+            lib.bicgk_batch_destroy.argtypes = [vp]
+            for f in ("bicgk_batch_create", "bicgk_batch_tune", "bicgk_batch_solve", "bicgk_batch_last_launches",
+                      "bicgk_batch_destroy"):
+                getattr(lib, f).restype = ctypes.c_int
             lib.bicgk_set_profiling.argtypes = [vp, ctypes.c_int]
             lib.bicgk_set_option.argtypes = [vp, ctypes.c_int, i64]
             lib.bicgk_kernel_times.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_char_p),
@@ -289,6 +299,87 @@ class Operator:
     def close(self):
         if getattr(self, "handle", None):
             op_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+BATCH_GRAPH, BATCH_LOOP = 0, 1
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = None if t is None else (t.data_ptr() if _is_torch(t) else t.ctypes.data)
+    return arr
+
+
+class Batch:
+    """Many independent CSR systems (uneven sizes, 1..64 RHS each) solved together (bicgk_batch_*).
+
+    csrs: list of objects with rowptr/colidx/vals (numpy, host) and ks: RHS count per system.
+    """
+
+    def __init__(self, csrs, ks, stream=None):
+        lib = _load()
+        self.ks = [int(k) for k in ks]
+        self.n = [int(c.rowptr.shape[0] - 1) for c in csrs]
+        rowptr = [np.ascontiguousarray(c.rowptr, dtype=np.int32) for c in csrs]
+        colidx = [np.ascontiguousarray(c.colidx, dtype=np.int32) for c in csrs]
+        vals = [np.ascontiguousarray(c.vals, dtype=np.float64) for c in csrs]
+        n = np.array(self.n, dtype=np.int64)
+        nnz = np.array([c.shape[0] for c in colidx], dtype=np.int64)
+        k = np.array(self.ks, dtype=np.int32)
+        h = ctypes.c_void_p()
+        rc = lib.bicgk_batch_create(ctypes.byref(h), len(csrs), _ptr(n), _ptr(nnz), _ptr_array(rowptr),
+                                    _ptr_array(colidx), _ptr_array(vals), _ptr(k), MEM_HOST, _stream(stream))
+        _check(rc, "bicgk_batch_create")
+        self.handle = h.value
+
+    def tune(self, reps: int = 5, stream=None) -> dict:
+        m = len(self.ks)
+        g, sg, cpl = np.zeros(m, np.int32), np.zeros(m, np.int32), np.zeros(m, np.int32)
+        _check(_load().bicgk_batch_tune(ctypes.c_void_p(self.handle), int(reps), _ptr(g), _ptr(sg), _ptr(cpl),
+                                        _stream(stream)), "bicgk_batch_tune")
+        return {"vec_grid": g, "spmm_grid": sg, "spmm_cols_per_lane": cpl}
+
+    def solve(self, Bs, Xs=None, X0s=None, tol: float = 1e-8, maxit: int = 1000, variant="classical_merged",
+              flags: int = 0, mode: int = BATCH_GRAPH, stream=None):
+        """Bs: list of CUDA tensors (n_i, k_i).  Returns (Xs, iters, status, true_relres) with the
+        per-column arrays concatenated in system order."""
+        import torch
+        if Xs is None:
+            Xs = [torch.empty_like(b) for b in Bs]
+        tot = sum(self.ks)
+        iters = np.zeros(tot, np.int32)
+        status = np.zeros(tot, np.int32)
+        trr = np.empty(tot)
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        x0 = None if X0s is None else _ptr_array(X0s)
+        rc = _load().bicgk_batch_solve(ctypes.c_void_p(self.handle), _ptr_array(Bs), x0, _ptr_array(Xs),
+                                       float(tol), int(maxit), v, int(flags), int(mode), _ptr(iters),
+                                       _ptr(status), _ptr(trr), _stream(stream))
+        _check(rc, "bicgk_batch_solve")
+        return Xs, iters, status, trr
+
+    def last_launches(self) -> int:
+        n = ctypes.c_int64()
+        _check(_load().bicgk_batch_last_launches(ctypes.c_void_p(self.handle), ctypes.byref(n)), "last_launches")
+        return n.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(_load().bicgk_batch_destroy(ctypes.c_void_p(self.handle)), "bicgk_batch_destroy")
             self.handle = None
 
     def __enter__(self):

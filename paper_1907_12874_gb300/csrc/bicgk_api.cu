@@ -130,6 +130,7 @@ constexpr int kSplitMinK = 16;    // smallest k that is split into two groups
 // Solver state of one group of columns: N x kp vectors, per-column scalars and flags, block
 // partials, control block, history, the group's stream and its captured graphs.
 struct Workspace {
+  bool shared_state = false; // d_sc, d_fl, d_ctl point into a batch's arrays (not owned)
   int ebytes = 8;            // bytes per vector element (8: FP64, 4: FP32)
   int kp = 0;
   int64_t vstride = 0;       // doubles between consecutive workspace vectors
@@ -174,6 +175,10 @@ struct bicgk_op_s {
   int opt_vec_blocks = 0;
   int opt_spmm_blocks = 0;
   int opt_groups = 0;
+  // launch shapes chosen by the batch autotuner (0 = the per-SM rule above)
+  int grid_vec_abs = 0;
+  int grid_spmm_abs = 0;
+  int spmm_cpl = 2;
   // last solve statistics
   int32_t last_loop_iters = 0;
   int64_t last_launches = 0;
@@ -200,6 +205,7 @@ KArgs make_args(bicgk_op A, const Workspace &W, int use_cond, cudaGraphCondition
 }
 
 int vec_grid(bicgk_op A, int op) {
+  if (A->grid_vec_abs > 0) return A->grid_vec_abs;
   int nb = vec_blocks_per_sm(op);
   if (nb > 4) nb = 4;
   if (A->opt_vec_blocks > 0 && A->opt_vec_blocks < nb) nb = A->opt_vec_blocks;
@@ -207,6 +213,7 @@ int vec_grid(bicgk_op A, int op) {
 }
 
 int spmm_grid(bicgk_op A, int kp, int mode) {
+  if (A->grid_spmm_abs > 0) return A->grid_spmm_abs;
   int nb = spmm_blocks_per_sm(kp, mode, A->stage_cap);
   if (A->opt_spmm_blocks > 0 && A->opt_spmm_blocks < nb) nb = A->opt_spmm_blocks;
   return A->nsm * nb;
@@ -223,6 +230,7 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
   sa.b = st.spmm == 2 ? a.v[st.b] : nullptr;
   sa.n = A->n;
   sa.stage_cap = a.kp <= 2 ? A->stage_cap : 0;
+  sa.cols_per_lane = a.kp >= 8 ? A->spmm_cpl : 2;
   if (st.spmm == 3) {
     sa.vals = A->d_val32;
     return launch_spmm32(a.kp, sa, A->nsm * spmm32_blocks_per_sm(a.kp, sa.stage_cap), s);
@@ -251,8 +259,10 @@ void drop_all_graphs(bicgk_op A) {
 void free_vectors(Workspace &W) {
   drop_graphs(W);
   cudaFree(W.d_vec);
-  cudaFree(W.d_sc);
-  cudaFree(W.d_fl);
+  if (!W.shared_state) {
+    cudaFree(W.d_sc);
+    cudaFree(W.d_fl);
+  }
   cudaFree(W.d_part);
   W.d_vec = nullptr;
   W.d_sc = nullptr;
@@ -263,7 +273,7 @@ void free_vectors(Workspace &W) {
 
 void free_workspace(Workspace &W) {
   free_vectors(W);
-  cudaFree(W.d_ctl);
+  if (!W.shared_state) cudaFree(W.d_ctl);
   cudaFree(W.d_hist);
   cudaFreeHost(W.h_ctl);
   cudaFreeHost(W.h_hist);
@@ -862,6 +872,368 @@ int bicgk_last_stats(bicgk_op A, int32_t *loop_iters, int64_t *kernel_launches, 
   if (loop_iters) *loop_iters = A->last_loop_iters;
   if (kernel_launches) *kernel_launches = A->last_launches;
   if (kernels_per_iter) *kernels_per_iter = A->last_kernels_per_iter;
+  return BICGK_OK;
+}
+
+}  // extern "C"
+
+
+// ----------------------------------------------------------------------------
+// Batches of independent systems (uneven sizes and RHS counts) in one graph.
+//
+// Every system keeps its own operator (CSR copy, launch shapes) and a batch workspace whose
+// control block, flags and scalars live in batch-wide arrays, so one upload and one readback
+// serve all systems.  The batched graph holds one independent branch per system: reset, pack
+// (caller pointers read from a device table), the form's set-up, a conditional WHILE node over
+// one iteration, the true residual and unpack.  One launch runs every branch; the branches have
+// no edges between them, so the GPU overlaps the systems' kernels.
+struct bicgk_batch_s {
+  int nsys = 0;
+  std::vector<bicgk_op> ops;
+  std::vector<int> k;
+  std::vector<Workspace> ws;  // batch workspaces (shared state)
+  Ctl *d_ctl = nullptr, *h_ctl = nullptr;
+  int *d_fl = nullptr, *h_fl = nullptr;
+  double *d_sc = nullptr, *h_sc = nullptr;
+  BatchIO *d_io = nullptr, *h_io = nullptr;
+  int64_t hist_iters = 0;     // history capacity of every system, in iterations + 1
+  std::map<int, GraphEntry> graphs;
+  int64_t last_launches = 0;
+};
+
+namespace {
+
+void batch_drop_graphs(bicgk_batch b) {
+  for (auto &kv : b->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  b->graphs.clear();
+}
+
+int batch_ensure(bicgk_batch b, int32_t maxit) {
+  const int64_t need = (int64_t)maxit + 1;
+  for (int i = 0; i < b->nsys; ++i) {
+    Workspace &W = b->ws[i];
+    bicgk_op A = b->ops[i];
+    const int kp = pow2_at_least(b->k[i]);
+    if (W.kp != kp) {
+      const int64_t elems = A->n * kp + 2;
+      W.vstride = (elems + 31) / 32 * 32;
+      const size_t bytes = (size_t)W.vstride * V_NVEC * sizeof(double);
+      CK(cudaMalloc(&W.d_vec, bytes));
+      CK(cudaMemset(W.d_vec, 0, bytes));
+      CK(cudaMalloc(&W.d_part, sizeof(double) * ((size_t)A->nsm * 4 + kMaxRedGroups) * kMaxDots * kMaxKp));
+      W.kp = kp;
+    }
+  }
+  if (need > b->hist_iters) {
+    for (int i = 0; i < b->nsys; ++i) {
+      Workspace &W = b->ws[i];
+      cudaFree(W.d_hist);
+      W.d_hist = nullptr;
+      CK(cudaMalloc(&W.d_hist, sizeof(double) * need * W.kp));
+      W.hist_cap = need * W.kp;
+    }
+    b->hist_iters = need;
+    batch_drop_graphs(b);  // the history length is baked into the reset nodes
+  }
+  return BICGK_OK;
+}
+
+int batch_build_graph(bicgk_batch b, int variant, GraphEntry *ge) {
+  const Seq q = make_seq(variant);
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  ge->graph = g;
+  cudaStream_t cs = b->ops[0]->cap_stream;
+  cudaGraph_t tmp;
+  for (int i = 0; i < b->nsys; ++i) {
+    bicgk_op A = b->ops[i];
+    Workspace &W = b->ws[i];
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    const KArgs a = make_args(A, W, 1, h);
+    CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_reset(a, W.hist_cap, cs);
+    if (e == cudaSuccess) e = launch_pack_io(b->d_io + i, b->k[i], a, cs);
+    for (size_t t = 0; e == cudaSuccess && t < q.setup.size(); ++t) e = launch_step(A, q.setup[t], a, cs);
+    if (e != cudaSuccess) {
+      cudaStreamEndCapture(cs, &tmp);
+      return cuda_fail(e, "batch capture set-up");
+    }
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+    std::vector<cudaGraphNode_t> leaves(deps, deps + ndeps);
+    CK(cudaStreamEndCapture(cs, &tmp));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, g, leaves.data(), nullptr, leaves.size(), &p));
+    CK(cudaStreamBeginCaptureToGraph(cs, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    for (size_t t = 0; e == cudaSuccess && t < q.body.size(); ++t) e = launch_step(A, q.body[t], a, cs);
+    if (e != cudaSuccess) {
+      cudaStreamEndCapture(cs, &tmp);
+      return cuda_fail(e, "batch capture body");
+    }
+    CK(cudaStreamEndCapture(cs, &tmp));
+    CK(cudaStreamBeginCaptureToGraph(cs, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    for (size_t t = 0; e == cudaSuccess && t < q.fin.size(); ++t) e = launch_step(A, q.fin[t], a, cs);
+    if (e == cudaSuccess) e = launch_unpack_io(b->d_io + i, b->k[i], a, cs);
+    if (e != cudaSuccess) {
+      cudaStreamEndCapture(cs, &tmp);
+      return cuda_fail(e, "batch capture final");
+    }
+    CK(cudaStreamEndCapture(cs, &tmp));
+  }
+  CK(cudaGraphInstantiate(&ge->exec, g, 0));
+  return BICGK_OK;
+}
+
+// Mean time of `reps` launches of one kernel configuration (CUDA events on stream s).
+template <class F>
+int time_launches(F launch, int reps, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+  CK(launch());  // warm
+  CK(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) CK(launch());
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  CK(cudaEventElapsedTime(ms, e0, e1));
+  *ms /= reps;
+  return BICGK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bicgk_batch_create(bicgk_batch *out, int32_t nsys, const int64_t *n_rows, const int64_t *nnz,
+                       const int32_t *const *rowptr, const int32_t *const *colidx, const double *const *vals,
+                       const int32_t *k, int mem, void *stream) {
+  if (!out || nsys < 1 || nsys > 4096 || !n_rows || !nnz || !rowptr || !colidx || !vals || !k) return BICGK_E_INVALID;
+  *out = nullptr;
+  for (int i = 0; i < nsys; ++i)
+    if (k[i] < 1) return BICGK_E_INVALID;
+    else if (k[i] > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
+  bicgk_batch b = new bicgk_batch_s();
+  b->nsys = nsys;
+  b->k.assign(k, k + nsys);
+  b->ops.assign(nsys, nullptr);
+  b->ws.resize(nsys);
+  int rc = BICGK_OK;
+  for (int i = 0; i < nsys && rc == BICGK_OK; ++i)
+    rc = bicgk_csr_create(&b->ops[i], n_rows[i], nnz[i], rowptr[i], colidx[i], vals[i], mem, stream);
+  cudaError_t e = cudaSuccess;
+  if (rc == BICGK_OK) {
+    if ((e = cudaMalloc(&b->d_ctl, sizeof(Ctl) * nsys)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_fl, sizeof(int) * F_NFLAG * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_sc, sizeof(double) * S_NSLOT * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_io, sizeof(BatchIO) * nsys)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_ctl, sizeof(Ctl) * nsys)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_fl, sizeof(int) * F_NFLAG * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_sc, sizeof(double) * S_NSLOT * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_io, sizeof(BatchIO) * nsys)) != cudaSuccess ||
+        (e = cudaMemset(b->d_ctl, 0, sizeof(Ctl) * nsys)) != cudaSuccess ||
+        (e = cudaMemset(b->d_fl, 0, sizeof(int) * F_NFLAG * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMemset(b->d_sc, 0, sizeof(double) * S_NSLOT * kMaxKp * nsys)) != cudaSuccess)
+      rc = cuda_fail(e, "bicgk_batch_create");
+  }
+  if (rc != BICGK_OK) {
+    bicgk_batch_destroy(b);
+    return rc;
+  }
+  for (int i = 0; i < nsys; ++i) {
+    Workspace &W = b->ws[i];
+    W.shared_state = true;
+    W.d_ctl = b->d_ctl + i;
+    W.d_fl = b->d_fl + (size_t)i * F_NFLAG * kMaxKp;
+    W.d_sc = b->d_sc + (size_t)i * S_NSLOT * kMaxKp;
+  }
+  *out = b;
+  return BICGK_OK;
+}
+
+int bicgk_batch_destroy(bicgk_batch b) {
+  if (!b) return BICGK_OK;
+  cudaDeviceSynchronize();
+  batch_drop_graphs(b);
+  for (Workspace &W : b->ws) {
+    cudaFree(W.d_vec);
+    cudaFree(W.d_part);
+    cudaFree(W.d_hist);
+  }
+  for (bicgk_op A : b->ops) bicgk_op_destroy(A);
+  cudaFree(b->d_ctl);
+  cudaFree(b->d_fl);
+  cudaFree(b->d_sc);
+  cudaFree(b->d_io);
+  cudaFreeHost(b->h_ctl);
+  cudaFreeHost(b->h_fl);
+  cudaFreeHost(b->h_sc);
+  cudaFreeHost(b->h_io);
+  delete b;
+  return BICGK_OK;
+}
+
+int bicgk_batch_tune(bicgk_batch b, int32_t reps, int32_t *vec_grid_out, int32_t *spmm_grid_out,
+                     int32_t *spmm_cpl_out, void *stream) {
+  if (!b || reps < 1 || reps > 1000) return BICGK_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = batch_ensure(b, 1);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int i = 0; i < b->nsys && rc == BICGK_OK; ++i) {
+    bicgk_op A = b->ops[i];
+    Workspace &W = b->ws[i];
+    // a control block with every column inactive: the timed kernels change no solver state
+    Ctl *hc = b->h_ctl + i;
+    memset(hc, 0, sizeof(Ctl));
+    hc->hist = W.d_hist;
+    hc->maxit = 1 << 30;
+    hc->k = b->k[i];
+    hc->kp = W.kp;
+    CK(cudaMemcpyAsync(W.d_ctl, hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(W.d_fl, 0, sizeof(int) * F_NFLAG * kMaxKp, s));
+    const KArgs a = make_args(A, W, 0, cudaGraphConditionalHandle{});
+    const int64_t chunks = (A->n * W.kp + 1) / 2;
+    // streaming kernels: grid for u double2 chunks per thread (rows per CTA), timed on group 3
+    A->grid_vec_abs = 0;
+    const int gmax = vec_grid(A, OP_G3);
+    int best_vec = gmax;
+    float best = 1e30f;
+    for (int u = 1; u <= 64; u *= 2) {
+      int g = (int)((chunks + (int64_t)kVecThreads * u - 1) / ((int64_t)kVecThreads * u));
+      if (g > gmax) g = gmax;
+      if (g < 1) g = 1;
+      float ms = 0.f;
+      rc = time_launches([&] { return launch_vec(OP_G3, a, g, s); }, reps, s, e0, e1, &ms);
+      if (rc) break;
+      if (ms < best * 0.98f) {
+        best = ms;
+        best_vec = g;
+      }
+      if (g == 1) break;
+    }
+    // SpMM: rows per CTA and RHS-tile width (columns per lane)
+    A->grid_spmm_abs = 0;
+    A->spmm_cpl = 2;
+    const int smax = spmm_grid(A, W.kp, 0);
+    int best_spmm = smax, best_cpl = 2;
+    best = 1e30f;
+    for (int cpl = 2; cpl <= (W.kp >= 8 ? 4 : 2) && rc == BICGK_OK; cpl *= 2) {
+      const int rpp = W.kp <= 2 ? kSpmmTileRows : kSpmmThreads / (W.kp / cpl);
+      for (int r = 1; r <= 64; r *= 2) {
+        int g = (int)((A->n + (int64_t)rpp * r - 1) / ((int64_t)rpp * r));
+        if (g > smax) g = smax;
+        if (g < 1) g = 1;
+        A->spmm_cpl = cpl;
+        A->grid_spmm_abs = g;
+        float ms = 0.f;
+        rc = time_launches([&] { return launch_step(A, spmm(V_P, V_V), a, s); }, reps, s, e0, e1, &ms);
+        if (rc) break;
+        if (ms < best * 0.98f) {
+          best = ms;
+          best_spmm = g;
+          best_cpl = cpl;
+        }
+        if (g == 1) break;
+      }
+    }
+    A->grid_vec_abs = best_vec;
+    A->grid_spmm_abs = best_spmm;
+    A->spmm_cpl = best_cpl;
+    drop_all_graphs(A);
+    if (vec_grid_out) vec_grid_out[i] = best_vec;
+    if (spmm_grid_out) spmm_grid_out[i] = best_spmm;
+    if (spmm_cpl_out) spmm_cpl_out[i] = best_cpl;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  batch_drop_graphs(b);
+  return rc;
+}
+
+int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const *X0, double *const *X,
+                      double rel_tol, int32_t maxit, int variant, int32_t flags, int mode, int32_t *iters,
+                      int32_t *status, double *true_relres, void *stream) {
+  if (!b || !B || !X || !iters || !status || !(rel_tol >= 0.0) || maxit < 0 || maxit > 10000000 || variant < 0 ||
+      variant > 5 || (flags & ~1) || (mode != BICGK_BATCH_GRAPH && mode != BICGK_BATCH_LOOP))
+    return BICGK_E_INVALID;
+  for (int i = 0; i < b->nsys; ++i)
+    if (!B[i] || !X[i]) return BICGK_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  int64_t off = 0, launches = 0;
+  if (mode == BICGK_BATCH_LOOP) {  // one bicgk_solve per system
+    for (int i = 0; i < b->nsys; ++i) {
+      if ((rc = bicgk_solve(b->ops[i], b->k[i], B[i], X0 ? X0[i] : nullptr, rel_tol, maxit, variant, flags,
+                            BICGK_MEM_DEVICE, X[i], iters + off, status + off, nullptr,
+                            true_relres ? true_relres + off : nullptr, stream)))
+        return rc;
+      launches += b->ops[i]->last_launches;
+      off += b->k[i];
+    }
+    b->last_launches = launches;
+    return BICGK_OK;
+  }
+  if ((rc = batch_ensure(b, maxit))) return rc;
+  for (int i = 0; i < b->nsys; ++i) {
+    Ctl *hc = b->h_ctl + i;
+    memset(hc, 0, sizeof(Ctl));
+    hc->tol = rel_tol;
+    hc->hist = b->ws[i].d_hist;
+    hc->maxit = maxit;
+    hc->k = b->k[i];
+    hc->kp = b->ws[i].kp;
+    hc->flags = flags;
+    b->h_io[i].B = B[i];
+    b->h_io[i].X0 = X0 ? X0[i] : nullptr;
+    b->h_io[i].X = X[i];
+  }
+  CK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(Ctl) * b->nsys, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(b->d_io, b->h_io, sizeof(BatchIO) * b->nsys, cudaMemcpyHostToDevice, s));
+  auto it = b->graphs.find(variant);
+  if (it == b->graphs.end()) {
+    GraphEntry ge;
+    if ((rc = batch_build_graph(b, variant, &ge))) {
+      if (ge.exec) cudaGraphExecDestroy(ge.exec);
+      if (ge.graph) cudaGraphDestroy(ge.graph);
+      return rc;
+    }
+    it = b->graphs.emplace(variant, ge).first;
+  }
+  CK(cudaGraphLaunch(it->second.exec, s));
+  CK(cudaMemcpyAsync(b->h_fl, b->d_fl, sizeof(int) * F_NFLAG * kMaxKp * b->nsys, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(b->h_sc, b->d_sc, sizeof(double) * S_NSLOT * kMaxKp * b->nsys, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(Ctl) * b->nsys, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const Seq q = make_seq(variant);
+  for (int i = 0; i < b->nsys; ++i) {
+    const int *fl = b->h_fl + (size_t)i * F_NFLAG * kMaxKp;
+    const double *sc = b->h_sc + (size_t)i * S_NSLOT * kMaxKp;
+    for (int c = 0; c < b->k[i]; ++c) {
+      iters[off + c] = fl[F_ITERS * kMaxKp + c];
+      status[off + c] = fl[F_STATUS * kMaxKp + c];
+      if (true_relres) true_relres[off + c] = sc[S_TRUE * kMaxKp + c];
+    }
+    off += b->k[i];
+    launches += 2 + (int64_t)q.setup.size() + (int64_t)b->h_ctl[i].loop_iters * q.body.size() + q.fin.size() + 1;
+  }
+  b->last_launches = launches;
+  return BICGK_OK;
+}
+
+int bicgk_batch_last_launches(bicgk_batch b, int64_t *kernel_launches) {
+  if (!b || !kernel_launches) return BICGK_E_INVALID;
+  *kernel_launches = b->last_launches;
   return BICGK_OK;
 }
 

@@ -111,6 +111,7 @@ struct SpmmArgs {
   const void *b;
   int64_t n;
   int stage_cap;  // staged CSR entries per tile (kp <= 2); 0 = read entries directly
+  int cols_per_lane = 2;  // RHS-tile width of a lane (kp >= 8 also accepts 4)
 };
 cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s);
 int spmm_blocks_per_sm(int kp, int mode, int stage_cap);
@@ -125,6 +126,16 @@ cudaError_t launch_pack(const double *B, const double *X0, int ld, int ncols, co
 // dimension ld; with use_xzero, columns with b_c = 0 are written as zeros.
 cudaError_t launch_unpack_role(double *X, int ld, int ncols, const KArgs &a, int role, int use_xzero,
                                cudaStream_t s);
+// Caller blocks of one batched system, read by the kernels through a device pointer so a
+// captured graph serves every call (the host rewrites the table before each launch).
+struct BatchIO {
+  const double *B;
+  const double *X0;  // nullable
+  double *X;
+};
+// pack / unpack through a BatchIO entry (ld = ncols = the system's k)
+cudaError_t launch_pack_io(const BatchIO *io, int k, const KArgs &a, cudaStream_t s);
+cudaError_t launch_unpack_io(const BatchIO *io, int k, const KArgs &a, cudaStream_t s);
 // dst = (float)src elementwise.
 cudaError_t launch_to_float(const double *src, float *dst, int64_t n, cudaStream_t s);
 // Fill the history with NaN and clear the per-column state.

@@ -42,11 +42,12 @@ struct Vec2<float> {
   __device__ static type make(float x, float y) { return make_float2(x, y); }
 };
 
-template <typename T, int KP, int MODE>
+template <typename T, int KP, int MODE, int CPL>
 __global__ void __launch_bounds__(kSpmmThreads) spmm_group_kernel(const SpmmArgs a) {
-  static_assert(KP >= 4, "group kernel needs kp >= 4");
+  static_assert(KP >= 4 && KP >= CPL && (CPL == 2 || CPL == 4), "group kernel: kp >= 4, 2 or 4 columns per lane");
   using T2 = typename Vec2<T>::type;
-  constexpr int L = KP / 2;                   // lanes per row
+  constexpr int L = KP / CPL;                 // lanes per row
+  constexpr int H = CPL / 2;                  // two-wide vectors per lane
   constexpr int RPP = kSpmmThreads / L;       // rows per pass of a block
   const int g = threadIdx.x / L, cl = threadIdx.x % L;
   const int32_t *__restrict__ rp = a.rowptr;
@@ -57,30 +58,46 @@ __global__ void __launch_bounds__(kSpmmThreads) spmm_group_kernel(const SpmmArgs
   const int64_t stride = (int64_t)gridDim.x * RPP;
   for (int64_t r = (int64_t)blockIdx.x * RPP + g; r < a.n; r += stride) {
     const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
-    T2 acc = Vec2<T>::make(0, 0);
+    T2 acc[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) acc[h] = Vec2<T>::make(0, 0);
     int e = e0;
     for (; e + 1 < e1; e += 2) {
       const int j0 = __ldg(ci + e), j1 = __ldg(ci + e + 1);
       const T a0 = __ldg(va + e), a1 = __ldg(va + e + 1);
-      const T2 u0 = __ldg(x2 + (int64_t)j0 * L + cl);
-      const T2 u1 = __ldg(x2 + (int64_t)j1 * L + cl);
-      acc.x = fma(a0, u0.x, acc.x);
-      acc.y = fma(a0, u0.y, acc.y);
-      acc.x = fma(a1, u1.x, acc.x);
-      acc.y = fma(a1, u1.y, acc.y);
+      T2 u0[H], u1[H];
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        u0[h] = __ldg(x2 + (int64_t)j0 * (KP / 2) + cl * H + h);
+        u1[h] = __ldg(x2 + (int64_t)j1 * (KP / 2) + cl * H + h);
+      }
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        acc[h].x = fma(a0, u0[h].x, acc[h].x);
+        acc[h].y = fma(a0, u0[h].y, acc[h].y);
+        acc[h].x = fma(a1, u1[h].x, acc[h].x);
+        acc[h].y = fma(a1, u1[h].y, acc[h].y);
+      }
     }
     if (e < e1) {
       const int j0 = __ldg(ci + e);
       const T a0 = __ldg(va + e);
-      const T2 u0 = __ldg(x2 + (int64_t)j0 * L + cl);
-      acc.x = fma(a0, u0.x, acc.x);
-      acc.y = fma(a0, u0.y, acc.y);
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const T2 u0 = __ldg(x2 + (int64_t)j0 * (KP / 2) + cl * H + h);
+        acc[h].x = fma(a0, u0.x, acc[h].x);
+        acc[h].y = fma(a0, u0.y, acc[h].y);
+      }
     }
-    if constexpr (MODE == 1) {
-      const T2 bv = static_cast<const T2 *>(a.b)[r * L + cl];
-      acc = Vec2<T>::make(bv.x - acc.x, bv.y - acc.y);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int64_t o = r * (KP / 2) + cl * H + h;
+      if constexpr (MODE == 1) {
+        const T2 bv = static_cast<const T2 *>(a.b)[o];
+        acc[h] = Vec2<T>::make(bv.x - acc[h].x, bv.y - acc[h].y);
+      }
+      y2[o] = acc[h];
     }
-    y2[r * L + cl] = acc;
   }
 }
 
@@ -155,8 +172,13 @@ cudaError_t launch_kp(const SpmmArgs &a, int grid, cudaStream_t s) {
   if constexpr (KP <= 2) {
     const size_t smem = (size_t)a.stage_cap * (sizeof(T) + sizeof(int32_t));
     spmm_row_kernel<T, KP, MODE><<<grid, kSpmmThreads, smem, s>>>(a);
+  } else if constexpr (KP >= 8) {
+    if (a.cols_per_lane == 4)
+      spmm_group_kernel<T, KP, MODE, 4><<<grid, kSpmmThreads, 0, s>>>(a);
+    else
+      spmm_group_kernel<T, KP, MODE, 2><<<grid, kSpmmThreads, 0, s>>>(a);
   } else {
-    spmm_group_kernel<T, KP, MODE><<<grid, kSpmmThreads, 0, s>>>(a);
+    spmm_group_kernel<T, KP, MODE, 2><<<grid, kSpmmThreads, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -169,7 +191,7 @@ int occ_kp(int stage_cap) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_row_kernel<T, KP, MODE>, kSpmmThreads,
                                                       (size_t)stage_cap * (sizeof(T) + sizeof(int32_t)));
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_group_kernel<T, KP, MODE>, kSpmmThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_group_kernel<T, KP, MODE, 2>, kSpmmThreads, 0);
   if (e != cudaSuccess || nb < 1) return 1;
   return nb;
 }

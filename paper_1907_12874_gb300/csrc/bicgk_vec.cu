@@ -1128,11 +1128,52 @@ cudaError_t launch_unpack_role(double *X, int ld, int ncols, const KArgs &a, int
   return cudaGetLastError();
 }
 namespace {
+__global__ void pack_io_kernel(const BatchIO *io, int k, KArgs a) {
+  const double *B = io->B, *X0 = io->X0;
+  const int kp = a.kp;
+  const int64_t m = a.n * kp;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int64_t i = e / kp;
+    const int c = (int)(e - i * kp);
+    const bool real = c < k;
+    a.v[V_B][e] = real ? B[i * k + c] : 0.0;
+    a.v[V_X][e] = (real && X0) ? X0[i * k + c] : 0.0;
+  }
+  if ((m & 1) && blockIdx.x == 0 && threadIdx.x < V_NVEC) a.v[threadIdx.x][m] = 0.0;
+}
+
+__global__ void unpack_io_kernel(const BatchIO *io, int k, KArgs a) {
+  double *X = io->X;
+  const int kp = a.kp;
+  const int64_t m = a.n * k;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int64_t i = e / k;
+    const int c = (int)(e - i * k);
+    X[e] = FL(F_XZERO, c) ? 0.0 : a.v[V_X][i * kp + c];
+  }
+}
+
+int small_grid(int64_t work) {  // blocks of 256 threads for a one-off pass over `work` elements
+  int64_t g = (work + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
+}
+
 __global__ void to_float_kernel(const double *__restrict__ src, float *__restrict__ dst, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) dst[e] = (float)src[e];
 }
 }  // namespace
+
+cudaError_t launch_pack_io(const BatchIO *io, int k, const KArgs &a, cudaStream_t s) {
+  pack_io_kernel<<<small_grid(a.n * a.kp), 256, 0, s>>>(io, k, a);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack_io(const BatchIO *io, int k, const KArgs &a, cudaStream_t s) {
+  unpack_io_kernel<<<small_grid(a.n * k), 256, 0, s>>>(io, k, a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_to_float(const double *src, float *dst, int64_t n, cudaStream_t s) {
   if (n > 0) to_float_kernel<<<1024, 256, 0, s>>>(src, dst, n);
