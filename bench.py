@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-mixed", action="store_true",
                    help="skip the mixed-precision comparison (27-point 128^3, k = 32, rel tol 1e-10)")
     p.add_argument("--mixed-grid", type=int, default=128)
+    p.add_argument("--no-adjoint", action="store_true",
+                   help="skip the differentiable solve (64^3, k = 8: forward + adjoint backward)")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batching comparison (64 systems, grids 16^3..64^3, 1..8 RHS)")
     p.add_argument("--eager", action="store_true",
@@ -351,6 +353,52 @@ def batch_section(args, bicgk, inputs, torch, dev, nsys=64):
     return res
 
 
+def adjoint_section(args, bicgk, inputs, torch, dev):
+    """64^3 convection-diffusion, 8 RHS, loss = sum(w * X): forward + backward wall time (CUDA events).
+
+    The backward solves A^T Lambda = w with BiCGStab on the transposed operator and forms
+    dL/dA on the pattern; compared with the forward solve alone (plain FP64 BiCGStab).
+    """
+    from paper_1907_12874_gb300 import autograd
+    A = inputs.convdiff7(64)
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    ci = torch.from_numpy(A.colidx).to(dev)
+    B = torch.from_numpy(inputs.rhs(A.n, 8, 5)).to(dev)
+    W = torch.from_numpy(inputs.rhs(A.n, 8, 6)).to(dev)
+
+    def step():
+        vals = torch.from_numpy(A.vals.copy()).to(dev).requires_grad_(True)
+        Bt = B.clone().requires_grad_(True)
+        X = autograd.solve(vals, Bt, rp, ci, tol=1e-8, maxit=5000)
+        (W * X).sum().backward()
+        return X, vals.grad, Bt.grad
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 3
+    for _ in range(reps):
+        X, gv, gB = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_fb = e0.elapsed_time(e1) / reps
+    with bicgk.Operator(A) as op:
+        op.solve(B, tol=1e-8, maxit=5000, want_hist=False)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            op.solve(B, tol=1e-8, maxit=5000, want_hist=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_f = e0.elapsed_time(e1) / reps
+    S = A.to_scipy()
+    adj_res = float(np.linalg.norm(S.T @ gB.cpu().numpy() - W.cpu().numpy()) / np.linalg.norm(W.cpu().numpy()))
+    return {"workload": "convdiff7 64^3 (262,144 rows, 1,810,432 nnz), k=8, loss = sum(w*X), rel tol 1e-8",
+            "forward_backward_ms": ms_fb, "forward_solve_ms": ms_f, "backward_over_forward": ms_fb / ms_f - 1.0,
+            "adjoint_relres": adj_res, "grad_vals_finite": bool(torch.isfinite(gv).all())}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -493,6 +541,10 @@ def main():
     # batch of 64 uneven systems: one graph launch vs the per-system launch loop
     if not args.no_batch and rank == 0:
         out["batching"] = batch_section(args, bicgk, inputs, torch, dev)
+
+    # differentiable solve: forward BiCGStab + adjoint BiCGStab on A^T + gradient on the pattern
+    if not args.no_adjoint and rank == 0:
+        out["differentiation"] = adjoint_section(args, bicgk, inputs, torch, dev)
 
     # CPU oracle on the host cores (rank 0, N = 1 only)
     if not args.no_cpu and rank == 0 and world == 1:

@@ -129,6 +129,25 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
                 double *resid_hist, double *true_relres, void *stream);
 
 /*
+ * Transpose products for the adjoint (differentiation) path.  No counterpart in the paper.
+ *
+ * bicgk_op_transpose: *AT receives a new operator for A^T (same size and nonzeros, built from
+ *   A's device CSR by a stable counting sort on the host: row j of A^T lists the rows i of A
+ *   holding column j in ascending order).  Release it with bicgk_op_destroy().
+ * bicgk_spmm_t: Y = A^T X for device blocks of n_rows*k FP64 (ld = k).
+ *   method BICGK_TRANSPOSE_EXPLICIT: the SpMM kernel on a transposed copy that A builds on the
+ *   first call and keeps (atomic-free, deterministic); BICGK_TRANSPOSE_ATOMIC: a scatter over the
+ *   rows of A with FP64 atomic adds (no extra memory; the summation order is not fixed).
+ * bicgk_sddmm: G[e] = alpha * sum_c L[i*k+c] * X[j*k+c] for every entry e = (i, j) of A, in CSR
+ *   order (device arrays; G has nnz entries).  With L the adjoint solution of A^T L = dLoss/dX,
+ *   X the solution and alpha = -1 this is dLoss/dA on the sparsity pattern.
+ */
+enum bicgk_transpose_method { BICGK_TRANSPOSE_EXPLICIT = 0, BICGK_TRANSPOSE_ATOMIC = 1 };
+int bicgk_op_transpose(bicgk_op A, bicgk_op *AT, void *stream);
+int bicgk_spmm_t(bicgk_op A, int32_t k, const double *X, double *Y, int method, void *stream);
+int bicgk_sddmm(bicgk_op A, int32_t k, const double *L, const double *X, double alpha, double *G, void *stream);
+
+/*
  * Mixed-precision solve of A X = B: FP64 iterative refinement around FP32
  * BiCGStab inner solves (no counterpart in the paper, which runs in FP64; the
  * inner solver is the paper's merged BiCGStab, Algorithm 2).

@@ -149,3 +149,17 @@ def solve_mixed(A, B: np.ndarray, X0=None, tol: float = 1e-10, max_outer: int = 
     if rc != 0:
         raise ValueError(f"oracle_solve_mixed: bad argument (rc={rc})")
     return MixedResult(X, outer, inner, status, hist, trr)
+
+
+def adjoint_dense(A, B: np.ndarray, W: np.ndarray):
+    """Gradients of L = sum(W * X), X = A^-1 B, by dense LAPACK solves (reference for the adjoint path).
+
+    Lambda = A^-T W;  dL/dB = Lambda;  dL/dA_ij = -sum_c Lambda_ic X_jc on the nonzero pattern
+    (from dX = -A^-1 dA X + A^-1 dB).  Returns (X, dB, dvals) with dvals in CSR entry order.
+    """
+    D = A.to_dense()
+    X = np.linalg.solve(D, B)
+    lam = np.linalg.solve(D.T, W)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    dvals = -np.einsum("ec,ec->e", lam[rows], X[A.colidx])
+    return X, lam, dvals

@@ -70,6 +70,11 @@ def _load():
             for f in ("bicgk_batch_create", "bicgk_batch_tune", "bicgk_batch_solve", "bicgk_batch_last_launches",
                       "bicgk_batch_destroy"):
                 getattr(lib, f).restype = ctypes.c_int
+            lib.bicgk_op_transpose.argtypes = [vp, ctypes.POINTER(vp), vp]
+            lib.bicgk_spmm_t.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp]
+            lib.bicgk_sddmm.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
+            for f in ("bicgk_op_transpose", "bicgk_spmm_t", "bicgk_sddmm"):
+                getattr(lib, f).restype = ctypes.c_int
             lib.bicgk_set_profiling.argtypes = [vp, ctypes.c_int]
             lib.bicgk_set_option.argtypes = [vp, ctypes.c_int, i64]
             lib.bicgk_kernel_times.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_char_p),
@@ -288,6 +293,35 @@ class Operator:
 
     def solve_mixed(self, B, **kw) -> MixedResult:
         return solve_mixed(self.handle, B, **kw)
+
+    def transpose(self, stream=None) -> "Operator":
+        """A new Operator for A^T (see bicgk_op_transpose)."""
+        h = ctypes.c_void_p()
+        _check(_load().bicgk_op_transpose(ctypes.c_void_p(self.handle), ctypes.byref(h), _stream(stream)),
+               "bicgk_op_transpose")
+        t = Operator.__new__(Operator)
+        t.n, t.nnz, t.handle = self.n, self.nnz, h.value
+        return t
+
+    def spmm_t(self, X, Y=None, method: int = 0, stream=None):
+        """Y = A^T X (method 0: explicit transpose, 1: atomic scatter)."""
+        if Y is None:
+            import torch
+            Y = torch.empty_like(X)
+        k = 1 if X.dim() == 1 else X.shape[1]
+        _check(_load().bicgk_spmm_t(ctypes.c_void_p(self.handle), k, _ptr(X), _ptr(Y), int(method), _stream(stream)),
+               "bicgk_spmm_t")
+        return Y
+
+    def sddmm(self, L, X, alpha: float = 1.0, G=None, stream=None):
+        """G[e] = alpha * sum_c L[i, c] X[j, c] over the entries e = (i, j) of A."""
+        if G is None:
+            import torch
+            G = torch.empty(self.nnz, dtype=X.dtype, device=X.device)
+        k = 1 if X.dim() == 1 else X.shape[1]
+        _check(_load().bicgk_sddmm(ctypes.c_void_p(self.handle), k, _ptr(L), _ptr(X), float(alpha), _ptr(G),
+                                   _stream(stream)), "bicgk_sddmm")
+        return G
 
     def spmm(self, X, Y=None, stream=None):
         if Y is None:

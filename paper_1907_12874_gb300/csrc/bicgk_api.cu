@@ -162,6 +162,7 @@ struct bicgk_op_s {
   int stage_cap = 0;
   Workspace ws[kMaxGroups];
   Workspace ws32;            // FP32 inner-solve workspace of the mixed-precision refinement
+  bicgk_op trans = nullptr;  // operator of A^T (atomic-free transpose products; made on first use)
   double *d_stage[2] = {nullptr, nullptr};  // caller-layout staging for host-memory calls
   int64_t stage_elems = 0;
   cudaStream_t cap_stream = nullptr;
@@ -539,6 +540,7 @@ int bicgk_csr_create(bicgk_op *out, int64_t n_rows, int64_t nnz, const int32_t *
 int bicgk_op_destroy(bicgk_op A) {
   if (!A) return BICGK_OK;
   cudaDeviceSynchronize();
+  if (A->trans) bicgk_op_destroy(A->trans);
   for (Workspace &W : A->ws) free_workspace(W);
   free_workspace(A->ws32);
   cudaFree(A->d_val32);
@@ -817,6 +819,54 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
   A->last_kernels_per_iter = (int32_t)qi.body.size();
   A->last_launches = launches + 1;
   A->last_groups = 1;
+  return BICGK_OK;
+}
+
+
+int bicgk_op_transpose(bicgk_op A, bicgk_op *AT, void *stream) {
+  if (!A || !AT) return BICGK_E_INVALID;
+  *AT = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->n, nnz = A->nnz;
+  std::vector<int32_t> rp(n + 1), ci(nnz), rpt(n + 2, 0), cit(nnz);
+  std::vector<double> va(nnz), vat(nnz);
+  CK(cudaMemcpyAsync(rp.data(), A->d_rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+  if (nnz) {
+    CK(cudaMemcpyAsync(ci.data(), A->d_col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(va.data(), A->d_val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  // counting sort by column, stable in the row index: row j of A^T lists the rows i of A
+  // that hold column j, ascending
+  for (int64_t e = 0; e < nnz; ++e) rpt[ci[e] + 2]++;
+  for (int64_t j = 0; j < n; ++j) rpt[j + 2] += rpt[j + 1];
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      const int32_t pos = rpt[ci[e] + 1]++;
+      cit[pos] = (int32_t)i;
+      vat[pos] = va[e];
+    }
+  return bicgk_csr_create(AT, n, nnz, rpt.data(), cit.data(), vat.data(), BICGK_MEM_HOST, stream);
+}
+
+int bicgk_spmm_t(bicgk_op A, int32_t k, const double *X, double *Y, int method, void *stream) {
+  if (!A || !X || !Y || k < 1 || X == Y || (method != BICGK_TRANSPOSE_EXPLICIT && method != BICGK_TRANSPOSE_ATOMIC))
+    return BICGK_E_INVALID;
+  if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
+  if (method == BICGK_TRANSPOSE_ATOMIC) {
+    CK(launch_spmm_t_atomic(A->d_rowptr, A->d_col, A->d_val, X, Y, A->n, k, (cudaStream_t)stream));
+    return BICGK_OK;
+  }
+  if (!A->trans) {
+    int rc = bicgk_op_transpose(A, &A->trans, stream);
+    if (rc) return rc;
+  }
+  return bicgk_spmm(A->trans, k, X, Y, stream);
+}
+
+int bicgk_sddmm(bicgk_op A, int32_t k, const double *L, const double *X, double alpha, double *G, void *stream) {
+  if (!A || !L || !X || !G || k < 1) return BICGK_E_INVALID;
+  CK(launch_sddmm(A->d_rowptr, A->d_col, L, X, alpha, G, A->n, k, (cudaStream_t)stream));
   return BICGK_OK;
 }
 

@@ -115,6 +115,12 @@ struct SpmmArgs {
 };
 cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s);
 int spmm_blocks_per_sm(int kp, int mode, int stage_cap);
+// y = A^T x (ld = k) by an atomic scatter over the rows of A.
+cudaError_t launch_spmm_t_atomic(const int32_t *rowptr, const int32_t *colidx, const double *vals, const double *x,
+                                 double *y, int64_t n, int k, cudaStream_t s);
+// g_e = alpha * sum_c l_ic x_jc over the entries e = (i, j) of A (ld = k).
+cudaError_t launch_sddmm(const int32_t *rowptr, const int32_t *colidx, const double *l, const double *x, double alpha,
+                         double *g, int64_t n, int k, cudaStream_t s);
 // FP32 y = A x (values, x and y float; one FP32 FMA per nonzero and column).
 cudaError_t launch_spmm32(int kp, const SpmmArgs &a, int grid, cudaStream_t s);
 int spmm32_blocks_per_sm(int kp, int stage_cap);

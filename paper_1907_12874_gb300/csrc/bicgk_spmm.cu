@@ -224,7 +224,61 @@ int occ_mode(int kp, int stage_cap) {
   }
 }
 
+// y = A^T x by scattering over the rows of A: y_jc += a_ij x_ic with FP64 atomics (y zeroed
+// first).  No transposed copy is needed; the summation order into y_jc is not fixed.
+__global__ void spmm_t_atomic_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                     const double *__restrict__ va, const double *__restrict__ x,
+                                     double *__restrict__ y, int64_t n, int k) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t total = n * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int64_t i = t / k;
+    const int c = (int)(t - i * k);
+    const double xi = x[t];
+    for (int e = __ldg(rp + i); e < __ldg(rp + i + 1); ++e) atomicAdd(y + (int64_t)__ldg(ci + e) * k + c, __ldg(va + e) * xi);
+  }
+}
+
+// Sampled product on the pattern of A: g_e = alpha * sum_c l_ic x_jc for every entry e = (i, j)
+// (the gradient of a loss with respect to the matrix values, with l the adjoint solution).
+// One thread per row, k FMAs per entry in column order; ld = k for both blocks.
+__global__ void sddmm_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const double *__restrict__ l, const double *__restrict__ x, double alpha,
+                             double *__restrict__ g, int64_t n, int k) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double *li = l + i * k;
+    for (int e = __ldg(rp + i); e < __ldg(rp + i + 1); ++e) {
+      const double *xj = x + (int64_t)__ldg(ci + e) * k;
+      double acc = 0.0;
+      for (int c = 0; c < k; ++c) acc = fma(__ldg(li + c), __ldg(xj + c), acc);
+      g[e] = alpha * acc;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_spmm_t_atomic(const int32_t *rowptr, const int32_t *colidx, const double *vals, const double *x,
+                                 double *y, int64_t n, int k, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * n * k, s);
+  if (e != cudaSuccess) return e;
+  const int64_t total = n * k;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid < 1) grid = 1;
+  spmm_t_atomic_kernel<<<grid, 256, 0, s>>>(rowptr, colidx, vals, x, y, n, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sddmm(const int32_t *rowptr, const int32_t *colidx, const double *l, const double *x, double alpha,
+                         double *g, int64_t n, int k, cudaStream_t s) {
+  int grid = (int)((n + 255) / 256);
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid < 1) grid = 1;
+  sddmm_kernel<<<grid, 256, 0, s>>>(rowptr, colidx, l, x, alpha, g, n, k);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s) {
   return mode == 0 ? launch_mode<double, 0>(kp, a, grid, s) : launch_mode<double, 1>(kp, a, grid, s);

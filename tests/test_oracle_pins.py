@@ -322,3 +322,30 @@ def test_mixed_edge_columns():
     r2 = oracle.solve_mixed(A2, B2, tol=1e-15, max_outer=10)
     assert np.all(r2.status == oracle.CONVERGED) and np.all(r2.outer_iters <= 3)
     assert np.all(np.linalg.norm(r2.X - B2 / 2, axis=0) <= 2e-15 * np.linalg.norm(B2 / 2, axis=0))
+
+
+# ------------------------------------------------------------------ adjoint reference
+
+def test_adjoint_dense_matches_central_differences():
+    """dL/dB and dL/dA of L = sum(W * A^-1 B) against central differences of the dense solve."""
+    A = I.convdiff7(3, peclet=True)
+    B = I.rhs(A.n, 2, 4)
+    W = I.rhs(A.n, 2, 5)
+    X, dB, dvals = oracle.adjoint_dense(A, B, W)
+    h = 1e-6
+
+    def loss(vals, Bm):
+        M = I.CSR(A.rowptr, A.colidx, vals)
+        return float(np.sum(W * np.linalg.solve(M.to_dense(), Bm)))
+    for e in (0, 5, A.nnz // 2, A.nnz - 1):
+        vp, vm = A.vals.copy(), A.vals.copy()
+        vp[e] += h
+        vm[e] -= h
+        fd = (loss(vp, B) - loss(vm, B)) / (2 * h)
+        assert abs(fd - dvals[e]) <= 1e-7 * (1 + abs(fd)), (e, fd, dvals[e])
+    for (i, c) in ((0, 0), (7, 1), (A.n - 1, 0)):
+        Bp, Bm = B.copy(), B.copy()
+        Bp[i, c] += h
+        Bm[i, c] -= h
+        fd = (loss(A.vals, Bp) - loss(A.vals, Bm)) / (2 * h)
+        assert abs(fd - dB[i, c]) <= 1e-7 * (1 + abs(fd))
