@@ -34,7 +34,14 @@ VARIANTS = {
     "reordered_merged": REORDERED_MERGED,
     "pipelined_plain": PIPELINED_BASIC,
     "pipelined_merged": PIPELINED_MERGED,
+    "precond_plain": 6,
+    "precond_merged": 7,
+    "ppipe_plain": 8,
+    "ppipe_merged": 9,
+    "improved_plain": 10,
+    "improved_merged": 11,
 }
+JACOBI = 2
 CONVERGED, MAXIT, BREAKDOWN, NONFINITE = range(4)
 NO_STOP_TEST = 1
 

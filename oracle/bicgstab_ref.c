@@ -14,6 +14,16 @@
  *   - Algorithm 6  (merged Reordered BiCGStab, M^-1 = identity applied as a
  *                   vector copy, as in the paper's benchmarks, Sec. 2.3)
  *                                                   -> reordered_*()
+ *   - Algorithm 5  (merged preconditioned BiCGStab)  -> precond_*()
+ *   - Algorithm 7  (merged preconditioned Pipelined BiCGStab; the listing's
+ *                   "w^_0 = M^-1 w^_0" is read as w^_0 = M^-1 w_0 and its
+ *                   "w^_j = M^-1 w_j, t_j = A w^_j" after the w-update as
+ *                   w^_{j+1}, t_{j+1})                -> ppipe_*()
+ *   - Algorithm 3  (merged Improved BiCGStab, with f_0 = A^T r_0 and the two
+ *                   corrections as printed in the listing) -> improved_*()
+ *   The preconditioner is the identity applied as a copy (Sec. 2.3) or, with
+ *   ORACLE_JACOBI, the Jacobi matrix M = diag(A) (a zero or missing diagonal
+ *   entry counts as 1).
  *   - "basic" forms: one BLAS-like loop per vector operation, the
  *     4-vector update of Algorithm 4 split into two calls (Table 2 and its
  *     footnote); "merged" forms: one loop per merged line of the listings.
@@ -67,6 +77,12 @@
 #define ORACLE_REORDERED_MERGED 3
 #define ORACLE_PIPELINED_BASIC 4
 #define ORACLE_PIPELINED_MERGED 5
+#define ORACLE_PRECOND_BASIC 6
+#define ORACLE_PRECOND_MERGED 7
+#define ORACLE_PPIPE_BASIC 8
+#define ORACLE_PPIPE_MERGED 9
+#define ORACLE_IMPROVED_BASIC 10
+#define ORACLE_IMPROVED_MERGED 11
 
 #define ST_CONVERGED 0
 #define ST_MAXIT 1
@@ -74,6 +90,7 @@
 #define ST_NONFINITE 3
 
 #define ORACLE_NO_STOP_TEST 1
+#define ORACLE_JACOBI 2 /* M = diag(A) instead of the identity (Algorithms 5, 6, 7) */
 
 typedef struct {
   int64_t n;
@@ -139,11 +156,27 @@ static void acc_add(acc_t *a, double p) {
 }
 static double acc_val(const acc_t *a) { return a->sum + a->comp; }
 
-/* M^{-1} = identity, applied as a copy y = x (Sec. 2.3). */
+/* Inverse Jacobi diagonal of the current solve (NULL: M = identity). */
+static const double *g_invdiag = NULL;
+
+/* y = M^{-1} x: the identity applied as a copy (Sec. 2.3), or x_i / a_ii (Jacobi). */
 static void precond_copy(const csr_t *A, col_t x, col_t y) {
   g_tr.copies++;
+  if (g_invdiag) {
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < A->n; ++i) AT(y, i) = AT(x, i);
+    for (int64_t i = 0; i < A->n; ++i) AT(y, i) = AT(x, i) * g_invdiag[i];
+  } else {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < A->n; ++i) AT(y, i) = AT(x, i);
+  }
+}
+
+/* y = A^T x: y_j = sum_i a_ij x_i, accumulated over i ascending. */
+static void spmv_t(const csr_t *A, col_t x, col_t y) {
+  g_tr.spmv++;
+  for (int64_t j = 0; j < A->n; ++j) AT(y, j) = 0.0;
+  for (int64_t i = 0; i < A->n; ++i)
+    for (int32_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) AT(y, A->colidx[e]) += A->vals[e] * AT(x, i);
 }
 
 static void set_zero(const csr_t *A, col_t y) {
@@ -515,6 +548,349 @@ static void pipelined(const csr_t *A, col_t b, col_t x, col_t r, col_t *w, doubl
   out->status = ST_MAXIT;
 }
 
+
+/* ---------------- Algorithm 5: preconditioned BiCGStab ---------------- */
+static void precond(const csr_t *A, col_t b, col_t x, col_t r, col_t *w, double tol, int maxit, int flags,
+                    int merged, double *hist, int64_t hs, res_t *out) {
+  col_t r0 = w[0], p = w[1], v = w[2], s = w[3], t = w[4], ph = w[5], sh = w[6];
+  double rho, eps2;
+  if (setup(A, b, x, r, v, tol, flags, &rho, &eps2, hist, hs, out)) return;
+  const int64_t n = A->n;
+  for (int64_t i = 0; i < n; ++i) { AT(r0, i) = AT(r, i); AT(p, i) = AT(r, i); }
+  for (int j = 0; j < maxit; ++j) {
+    precond_copy(A, p, ph);                /* p^_j = M^-1 p_j */
+    spmv(A, ph, v);                        /* v_j = A p^_j */
+    double delta = dot(A, v, r0); rw(2, 0);
+    if (!finite(delta)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    if (delta == 0.0) { out->iters = j; out->status = ST_BREAKDOWN; return; }
+    double alpha = rho / delta;
+    if (!finite(alpha)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    for (int64_t i = 0; i < n; ++i) AT(s, i) = AT(r, i) - alpha * AT(v, i);
+    rw(2, 1);
+    precond_copy(A, s, sh);                /* s^_j = M^-1 s_j */
+    spmv(A, sh, t);                        /* t_j = A s^_j */
+    double phi, psi, theta = 0.0;
+    if (merged) {
+      acc_t a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
+      for (int64_t i = 0; i < n; ++i) {
+        double ti = AT(t, i), si = AT(s, i);
+        acc_add(&a1, ti * si);
+        acc_add(&a2, ti * ti);
+        acc_add(&a3, si * si);
+      }
+      rw(2, 0);
+      phi = acc_val(&a1); psi = acc_val(&a2); theta = acc_val(&a3);
+    } else {
+      phi = dot(A, t, s); rw(2, 0);
+      psi = dot(A, t, t); rw(1, 0);
+    }
+    if (!finite(phi) || !finite(psi) || !finite(theta)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    double omega = psi == 0.0 ? 0.0 : phi / psi;
+    if (!finite(omega)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    int status = -1;
+    double rho1 = 0.0;
+    if (merged) {
+      double est = theta - omega * phi;
+      hist[(j + 1) * hs] = hist_value(est);
+      if (!finite(est)) status = ST_NONFINITE;
+      else if (!(flags & ORACLE_NO_STOP_TEST) && est < eps2) status = ST_CONVERGED;
+      if (status >= 0) { /* break branch: x and r, two lines */
+        for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(ph, i) + omega * AT(sh, i);
+        rw(3, 1);
+        for (int64_t i = 0; i < n; ++i) AT(r, i) = AT(s, i) - omega * AT(t, i);
+        rw(2, 1);
+        out->iters = j + 1;
+        out->status = status;
+        return;
+      }
+      /* r_{j+1} = s - omega t with rho_{j+1} = (r_{j+1}, r_0) in one pass */
+      acc_t ar = {0, 0};
+      for (int64_t i = 0; i < n; ++i) {
+        double ri = AT(s, i) - omega * AT(t, i);
+        AT(r, i) = ri;
+        acc_add(&ar, ri * AT(r0, i));
+      }
+      rw(3, 1);
+      rho1 = acc_val(&ar);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(ph, i) + omega * AT(sh, i);
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(r, i) = AT(s, i) - omega * AT(t, i);
+      rw(2, 1);
+      out->iters = j + 1;
+      double rr = dot(A, r, r); rw(1, 0);
+      hist[(j + 1) * hs] = hist_value(rr);
+      if (!finite(rr)) { out->status = ST_NONFINITE; return; }
+      if (!(flags & ORACLE_NO_STOP_TEST) && rr < eps2) { out->status = ST_CONVERGED; return; }
+      rho1 = dot(A, r, r0); rw(2, 0);
+    }
+    double beta = 0.0;
+    if (!finite(rho1)) status = ST_NONFINITE;
+    else if (rho == 0.0 || omega == 0.0) status = ST_BREAKDOWN;
+    else {
+      beta = (rho1 / rho) * (alpha / omega);
+      if (!finite(beta)) status = ST_NONFINITE;
+    }
+    if (merged) { /* x_{j+1} = x_j + alpha p^ + omega s^ (its own line, after beta) */
+      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(ph, i) + omega * AT(sh, i);
+      rw(3, 1);
+      out->iters = j + 1;
+    }
+    if (status >= 0) { out->status = status; return; }
+    for (int64_t i = 0; i < n; ++i) AT(p, i) = AT(r, i) + beta * (AT(p, i) - omega * AT(v, i));
+    rw(3, 1);
+    rho = rho1;
+  }
+  out->status = ST_MAXIT;
+}
+
+/* ---------------- Algorithm 7: preconditioned Pipelined BiCGStab ---------------- */
+static void ppipe(const csr_t *A, col_t b, col_t x, col_t r, col_t *w, double tol, int maxit, int flags,
+                  int merged, double *hist, int64_t hs, res_t *out) {
+  col_t r0 = w[0], wv = w[1], t = w[2], ph = w[3], sh = w[4], zh = w[5], qh = w[6], rh = w[7], wh = w[8];
+  col_t s = w[9], z = w[10], q = w[11], y = w[12], v = w[13], tmp = w[14];
+  double rho, eps2;
+  if (setup(A, b, x, r, v, tol, flags, &rho, &eps2, hist, hs, out)) return;
+  const int64_t n = A->n;
+  for (int64_t i = 0; i < n; ++i) AT(r0, i) = AT(r, i);
+  precond_copy(A, r, rh);  /* r^_0 = M^-1 r_0 */
+  spmv(A, rh, wv);         /* w_0 = A r^_0 */
+  precond_copy(A, wv, wh); /* w^_0 = M^-1 w_0 */
+  spmv(A, wh, t);          /* t_0 = A w^_0 */
+  double rw0 = dot(A, r0, wv);
+  if (!finite(rw0)) { out->status = ST_NONFINITE; return; }
+  if (rw0 == 0.0) { out->status = ST_BREAKDOWN; return; }
+  double alpha = rho / rw0;
+  if (!finite(alpha)) { out->status = ST_NONFINITE; return; }
+  double beta = 0.0, omega = 0.0;
+  set_zero(A, ph); set_zero(A, sh); set_zero(A, zh); set_zero(A, s); set_zero(A, z); set_zero(A, v);
+  for (int j = 0; j < maxit; ++j) {
+    double theta, phi, pi;
+    if (merged) {
+      /* p^, s^, q^ in one pass */
+      for (int64_t i = 0; i < n; ++i) {
+        double shi = AT(sh, i), rhi = AT(rh, i);
+        AT(ph, i) = rhi + beta * (AT(ph, i) - omega * shi);
+        double sn = AT(wh, i) + beta * (shi - omega * AT(zh, i));
+        AT(sh, i) = sn;
+        AT(qh, i) = rhi - alpha * sn;
+      }
+      rw(5, 3);
+      /* s, z, q, y with theta = (q,y), phi = (y,y), pi = (q,q) in one pass */
+      acc_t a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0};
+      for (int64_t i = 0; i < n; ++i) {
+        double wi = AT(wv, i), si = AT(s, i), zi = AT(z, i);
+        double sn = wi + beta * (si - omega * zi);
+        double zn = AT(t, i) + beta * (zi - omega * AT(v, i));
+        double qn = AT(r, i) - alpha * sn;
+        double yn = wi - alpha * zn;
+        AT(s, i) = sn; AT(z, i) = zn; AT(q, i) = qn; AT(y, i) = yn;
+        acc_add(&a1, qn * yn);
+        acc_add(&a2, yn * yn);
+        acc_add(&a3, qn * qn);
+      }
+      rw(6, 4);
+      theta = acc_val(&a1); phi = acc_val(&a2); pi = acc_val(&a3);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(ph, i) = AT(rh, i) + beta * (AT(ph, i) - omega * AT(sh, i));
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(sh, i) = AT(wh, i) + beta * (AT(sh, i) - omega * AT(zh, i));
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(qh, i) = AT(rh, i) - alpha * AT(sh, i);
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(s, i) = AT(wv, i) + beta * (AT(s, i) - omega * AT(z, i));
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(z, i) = AT(t, i) + beta * (AT(z, i) - omega * AT(v, i));
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(q, i) = AT(r, i) - alpha * AT(s, i);
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(y, i) = AT(wv, i) - alpha * AT(z, i);
+      rw(2, 1);
+      theta = dot(A, q, y); rw(2, 0);
+      phi = dot(A, y, y); rw(1, 0);
+      pi = dot(A, q, q); rw(1, 0);
+    }
+    precond_copy(A, z, zh); /* z^_j = M^-1 z_j */
+    spmv(A, zh, v);         /* v_j = A z^_j */
+    if (!finite(theta) || !finite(phi) || !finite(pi)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    omega = phi == 0.0 ? 0.0 : theta / phi;
+    if (!finite(omega)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    double est = pi - omega * theta;
+    hist[(j + 1) * hs] = hist_value(est);
+    int stop = !finite(est) || (!(flags & ORACLE_NO_STOP_TEST) && est < eps2);
+    if (stop) { /* break branch: x and r */
+      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(ph, i) + omega * AT(qh, i);
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(r, i) = AT(q, i) - omega * AT(y, i);
+      rw(2, 1);
+      out->iters = j + 1;
+      out->status = finite(est) ? ST_CONVERGED : ST_NONFINITE;
+      return;
+    }
+    double rho1, psi, sigma, delta;
+    if (merged) {
+      /* x and r^ in one pass */
+      for (int64_t i = 0; i < n; ++i) {
+        double qhi = AT(qh, i);
+        AT(x, i) = AT(x, i) + alpha * AT(ph, i) + omega * qhi;
+        AT(rh, i) = qhi - omega * (AT(wh, i) - alpha * AT(zh, i));
+      }
+      rw(5, 2);
+      /* r, w and rho, psi, sigma, delta in one pass */
+      acc_t a1 = {0, 0}, a2 = {0, 0}, a3 = {0, 0}, a4 = {0, 0};
+      for (int64_t i = 0; i < n; ++i) {
+        double yi = AT(y, i);
+        double rn = AT(q, i) - omega * yi;
+        double wn = yi - omega * (AT(t, i) - alpha * AT(v, i));
+        AT(r, i) = rn; AT(wv, i) = wn;
+        double r0i = AT(r0, i);
+        acc_add(&a1, r0i * rn);
+        acc_add(&a2, r0i * AT(z, i));
+        acc_add(&a3, r0i * wn);
+        acc_add(&a4, r0i * AT(s, i));
+      }
+      rw(7, 2);
+      rho1 = acc_val(&a1); psi = acc_val(&a2); sigma = acc_val(&a3); delta = acc_val(&a4);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(ph, i) + omega * AT(qh, i);
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(tmp, i) = AT(wh, i) - alpha * AT(zh, i);  /* 4-vector op: 2 calls */
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(rh, i) = AT(qh, i) - omega * AT(tmp, i);
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(r, i) = AT(q, i) - omega * AT(y, i);
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(tmp, i) = AT(t, i) - alpha * AT(v, i);    /* 4-vector op: 2 calls */
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(wv, i) = AT(y, i) - omega * AT(tmp, i);
+      rw(2, 1);
+      rho1 = dot(A, r0, r); rw(2, 0);
+      psi = dot(A, r0, z); rw(2, 0);
+      sigma = dot(A, r0, wv); rw(2, 0);
+      delta = dot(A, r0, s); rw(2, 0);
+    }
+    out->iters = j + 1;
+    precond_copy(A, wv, wh); /* w^_{j+1} = M^-1 w_{j+1} */
+    spmv(A, wh, t);          /* t_{j+1} = A w^_{j+1} */
+    if (!finite(rho1) || !finite(psi) || !finite(sigma) || !finite(delta)) { out->status = ST_NONFINITE; return; }
+    if (rho == 0.0 || omega == 0.0) { out->status = ST_BREAKDOWN; return; }
+    beta = (alpha / omega) * (rho1 / rho);
+    double den = sigma + beta * delta - beta * omega * psi;
+    if (!finite(beta) || !finite(den)) { out->status = ST_NONFINITE; return; }
+    if (den == 0.0) { out->status = ST_BREAKDOWN; return; }
+    alpha = rho1 / den;
+    if (!finite(alpha)) { out->status = ST_NONFINITE; return; }
+    rho = rho1;
+  }
+  out->status = ST_MAXIT;
+}
+
+/* ---------------- Algorithm 3: Improved BiCGStab ---------------- */
+static void improved(const csr_t *A, col_t b, col_t x, col_t r, col_t *w, double tol, int maxit, int flags,
+                     int merged, double *hist, int64_t hs, res_t *out) {
+  col_t r0 = w[0], u = w[1], f0 = w[2], q = w[3], v = w[4], z = w[5], s = w[6], t = w[7];
+  double phi, eps2;
+  if (setup(A, b, x, r, v, tol, flags, &phi, &eps2, hist, hs, out)) return;  /* phi_0 = (r_0, r_0) */
+  const int64_t n = A->n;
+  for (int64_t i = 0; i < n; ++i) AT(r0, i) = AT(r, i);
+  spmv(A, r, u);    /* u_0 = A r_0 */
+  spmv_t(A, r, f0); /* f_0 = A^T r_0 */
+  set_zero(A, q); set_zero(A, v); set_zero(A, z);
+  double sigma_prev = 0.0, pi = 0.0, tau = 0.0;
+  double sigma = dot(A, r0, u);
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  for (int j = 0; j < maxit; ++j) {
+    /* scalar recurrences of the iteration (divisions guarded as in R5) */
+    double rho1 = phi - omega * sigma_prev + omega * alpha * pi;
+    if (!finite(rho1) || !finite(sigma)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    if (rho == 0.0 || omega == 0.0) { out->iters = j; out->status = ST_BREAKDOWN; return; }
+    double delta1 = (rho1 / rho) * alpha;
+    double beta1 = delta1 / omega;
+    double tau1 = sigma + beta1 * tau - delta1 * pi;
+    if (!finite(delta1) || !finite(beta1) || !finite(tau1)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    if (tau1 == 0.0) { out->iters = j; out->status = ST_BREAKDOWN; return; }
+    double alpha1 = rho1 / tau1;
+    if (!finite(alpha1)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    double cz = beta1 * (alpha1 / alpha), cv = alpha1 * delta1;
+    if (merged) {
+      /* z, v, s in one pass */
+      for (int64_t i = 0; i < n; ++i) {
+        double ri = AT(r, i), vi = AT(v, i);
+        AT(z, i) = alpha1 * ri + cz * AT(z, i) - cv * vi;
+        double vn = AT(u, i) + beta1 * vi - delta1 * AT(q, i);
+        AT(v, i) = vn;
+        AT(s, i) = ri - alpha1 * vn;
+      }
+      rw(5, 3);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(z, i) = alpha1 * AT(r, i) + cz * AT(z, i) - cv * AT(v, i);
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(v, i) = AT(u, i) + beta1 * AT(v, i) - delta1 * AT(q, i);
+      rw(3, 1);
+      for (int64_t i = 0; i < n; ++i) AT(s, i) = AT(r, i) - alpha1 * AT(v, i);
+      rw(2, 1);
+    }
+    spmv(A, v, q); /* q_{j+1} = A v_{j+1} */
+    double phi1, pi1, gam, eta, theta, kappa, nu;
+    if (merged) {
+      /* t with the seven dot products in one pass */
+      acc_t a[7] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+      for (int64_t i = 0; i < n; ++i) {
+        double qi = AT(q, i), si = AT(s, i), r0i = AT(r0, i), fi = AT(f0, i);
+        double ti = AT(u, i) - alpha1 * qi;
+        AT(t, i) = ti;
+        acc_add(&a[0], r0i * si);
+        acc_add(&a[1], r0i * qi);
+        acc_add(&a[2], fi * si);
+        acc_add(&a[3], fi * ti);
+        acc_add(&a[4], si * ti);
+        acc_add(&a[5], ti * ti);
+        acc_add(&a[6], si * si);
+      }
+      rw(5, 1);
+      phi1 = acc_val(&a[0]); pi1 = acc_val(&a[1]); gam = acc_val(&a[2]); eta = acc_val(&a[3]);
+      theta = acc_val(&a[4]); kappa = acc_val(&a[5]); nu = acc_val(&a[6]);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(t, i) = AT(u, i) - alpha1 * AT(q, i);
+      rw(2, 1);
+      phi1 = dot(A, r0, s); rw(2, 0);
+      pi1 = dot(A, r0, q); rw(2, 0);
+      gam = dot(A, f0, s); rw(2, 0);
+      eta = dot(A, f0, t); rw(2, 0);
+      theta = dot(A, s, t); rw(2, 0);
+      kappa = dot(A, t, t); rw(1, 0);
+      nu = dot(A, s, s); rw(1, 0);
+    }
+    if (!finite(phi1) || !finite(pi1) || !finite(gam) || !finite(eta) || !finite(theta) || !finite(kappa) ||
+        !finite(nu)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    double omega1 = kappa == 0.0 ? 0.0 : theta / kappa;
+    if (!finite(omega1)) { out->iters = j; out->status = ST_NONFINITE; return; }
+    double sigma1 = gam - omega1 * eta;
+    if (merged) {
+      for (int64_t i = 0; i < n; ++i) {
+        double si = AT(s, i);
+        AT(r, i) = si - omega1 * AT(t, i);
+        AT(x, i) = AT(x, i) + AT(z, i) + omega1 * si;
+      }
+      rw(4, 2);
+    } else {
+      for (int64_t i = 0; i < n; ++i) AT(r, i) = AT(s, i) - omega1 * AT(t, i);
+      rw(2, 1);
+      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + AT(z, i) + omega1 * AT(s, i);
+      rw(3, 1);
+    }
+    out->iters = j + 1;
+    double est = nu - omega1 * theta;
+    hist[(j + 1) * hs] = hist_value(est);
+    if (!finite(est)) { out->status = ST_NONFINITE; return; }
+    if (!(flags & ORACLE_NO_STOP_TEST) && est < eps2) { out->status = ST_CONVERGED; return; }
+    spmv(A, r, u); /* u_{j+1} = A r_{j+1} */
+    sigma_prev = sigma; sigma = sigma1; rho = rho1; alpha = alpha1; omega = omega1; phi = phi1; pi = pi1;
+    tau = tau1;
+  }
+  out->status = ST_MAXIT;
+}
+
 /* ---------------- exported entry points ---------------- */
 
 /* Number of N-vectors of scratch per column a variant needs. */
@@ -526,6 +902,12 @@ static int n_work(int variant) {
     case ORACLE_REORDERED_MERGED: return 9;
     case ORACLE_PIPELINED_BASIC:
     case ORACLE_PIPELINED_MERGED: return 10;
+    case ORACLE_PRECOND_BASIC:
+    case ORACLE_PRECOND_MERGED: return 7;
+    case ORACLE_PPIPE_BASIC:
+    case ORACLE_PPIPE_MERGED: return 15;
+    case ORACLE_IMPROVED_BASIC:
+    case ORACLE_IMPROVED_MERGED: return 8;
     default: return -1;
   }
 }
@@ -560,9 +942,19 @@ int oracle_solve(int variant, int64_t n, const int32_t *rowptr, const int32_t *c
   memset(&g_tr, 0, sizeof(g_tr));
   double *work = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(nw + 2));
   double *hbuf = (double *)malloc(sizeof(double) * (size_t)(maxit + 1));
-  if (!work || !hbuf) { free(work); free(hbuf); return -2; }
+  double *invd = (flags & ORACLE_JACOBI) ? (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1)) : NULL;
+  if (!work || !hbuf || ((flags & ORACLE_JACOBI) && !invd)) { free(work); free(hbuf); free(invd); return -2; }
+  if (invd) { /* M = diag(A); a zero or missing diagonal entry counts as 1 */
+    for (int64_t i = 0; i < n; ++i) {
+      double d = 0.0;
+      for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+        if (colidx[e] == i) d += vals[e];
+      invd[i] = d == 0.0 ? 1.0 : 1.0 / d;
+    }
+  }
+  g_invdiag = invd;
   for (int32_t c = 0; c < k; ++c) {
-    col_t w[10];
+    col_t w[16];
     for (int q = 0; q < nw; ++q) w[q] = (col_t){work + (size_t)q * n, 1};
     col_t rloc = {work + (size_t)nw * n, 1};
     col_t b = {(double *)B + c, k};
@@ -577,6 +969,12 @@ int oracle_solve(int variant, int64_t n, const int32_t *rowptr, const int32_t *c
       case ORACLE_REORDERED_MERGED: reordered(&A, b, x, rloc, w, tol, maxit, flags, 1, hbuf, 1, &res); break;
       case ORACLE_PIPELINED_BASIC: pipelined(&A, b, x, rloc, w, tol, maxit, flags, 0, hbuf, 1, &res); break;
       case ORACLE_PIPELINED_MERGED: pipelined(&A, b, x, rloc, w, tol, maxit, flags, 1, hbuf, 1, &res); break;
+      case ORACLE_PRECOND_BASIC: precond(&A, b, x, rloc, w, tol, maxit, flags, 0, hbuf, 1, &res); break;
+      case ORACLE_PRECOND_MERGED: precond(&A, b, x, rloc, w, tol, maxit, flags, 1, hbuf, 1, &res); break;
+      case ORACLE_PPIPE_BASIC: ppipe(&A, b, x, rloc, w, tol, maxit, flags, 0, hbuf, 1, &res); break;
+      case ORACLE_PPIPE_MERGED: ppipe(&A, b, x, rloc, w, tol, maxit, flags, 1, hbuf, 1, &res); break;
+      case ORACLE_IMPROVED_BASIC: improved(&A, b, x, rloc, w, tol, maxit, flags, 0, hbuf, 1, &res); break;
+      case ORACLE_IMPROVED_MERGED: improved(&A, b, x, rloc, w, tol, maxit, flags, 1, hbuf, 1, &res); break;
     }
     if (iters) iters[c] = res.iters;
     if (status) status[c] = res.status;
@@ -595,8 +993,10 @@ int oracle_solve(int variant, int64_t n, const int32_t *rowptr, const int32_t *c
   if (traffic) {
     traffic[0] = g_tr.reads; traffic[1] = g_tr.writes; traffic[2] = g_tr.copies; traffic[3] = g_tr.spmv;
   }
+  g_invdiag = NULL;
   free(work);
   free(hbuf);
+  free(invd);
   return 0;
 }
 

@@ -39,6 +39,15 @@ MUTANTS = {
     "stop test 10x too loose": ("est < eps2)", "est < 100.0 * eps2)"),
     "refinement subtracts d": ("AT(x, i) = AT(x, i) + (double)AT(d32, i);", "AT(x, i) = AT(x, i) - (double)AT(d32, i);"),
     "fp32 inner r update sign": ("AT(r, i) = si - of * AT(t, i);", "AT(r, i) = si + of * AT(t, i);"),
+    "improved sigma sign": ("double sigma1 = gam - omega1 * eta;", "double sigma1 = gam + omega1 * eta;"),
+    "improved tau drops beta tau": ("double tau1 = sigma + beta1 * tau - delta1 * pi;",
+                                    "double tau1 = sigma - delta1 * pi;"),
+    "improved t uses u_{j+1}": ("double ti = AT(u, i) - alpha1 * qi;", "double ti = AT(s, i) - alpha1 * qi;"),
+    "ppipe r^ drops alpha z^": ("AT(rh, i) = qhi - omega * (AT(wh, i) - alpha * AT(zh, i));",
+                                "AT(rh, i) = qhi - omega * AT(wh, i);"),
+    "ppipe q^ from old s^": ("AT(qh, i) = rhi - alpha * sn;", "AT(qh, i) = rhi - alpha * shi;"),
+    "precond x uses p for p^": ("      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(ph, i) + omega * AT(sh, i);\n      rw(3, 1);\n      out->iters = j + 1;",
+                                "      for (int64_t i = 0; i < n; ++i) AT(x, i) = AT(x, i) + alpha * AT(p, i) + omega * AT(sh, i);\n      rw(3, 1);\n      out->iters = j + 1;"),
 }
 
 
@@ -68,7 +77,9 @@ def _solve(lib, A, B, variant, tol, maxit, flags=0):
 
 
 TABLE2 = {"classical_plain": (18, 4), "classical_merged": (14, 4), "pipelined_plain": (34, 9),
-          "pipelined_merged": (18, 8), "reordered_plain": (22, 6), "reordered_merged": (15, 6)}
+          "pipelined_merged": (18, 8), "reordered_plain": (22, 6), "reordered_merged": (15, 6),
+          "precond_plain": (18, 4), "precond_merged": (15, 4), "ppipe_plain": (43, 13), "ppipe_merged": (23, 11),
+          "improved_plain": (27, 6), "improved_merged": (14, 6)}
 
 
 def _pins_pass(lib) -> bool:
@@ -99,6 +110,14 @@ def _pins_pass(lib) -> bool:
         elif np.max(np.abs(X - ref1)) > 1e-10 * np.abs(ref1).max():
             return False
         if (tr[0], tr[1]) != (3 * 2 * TABLE2[v][0], 3 * 2 * TABLE2[v][1]):
+            return False
+    # Jacobi preconditioner (M = diag(A), not a multiple of I here): Algorithms 5, 6 and 7
+    A2 = I.perturbed27(4, seed=6)
+    Xd2 = np.linalg.solve(A2.to_dense(), B[: A2.n] if A2.n <= B.shape[0] else I.rhs(A2.n, 2, 5))
+    B2 = A2.to_dense() @ Xd2
+    for v in ("precond_plain", "precond_merged", "ppipe_plain", "ppipe_merged", "reordered_plain", "reordered_merged"):
+        X, R, it, st, hist, tr = _solve(lib, A2, B2, v, 1e-12, 300, 2)
+        if not np.all(st == 0) or np.max(np.linalg.norm(X - Xd2, axis=0) / np.linalg.norm(Xd2, axis=0)) > 1e-9:
             return False
     # mixed-precision refinement: FP64 accuracy from FP32 inner solves
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
