@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--mixed-grid", type=int, default=128)
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the differentiable solve (64^3, k = 8: forward + adjoint backward)")
+    p.add_argument("--profile-mixed", action="store_true",
+                   help="only the mixed-precision solve at --mixed-grid, in the host-loop mode (profiler captures)")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batching comparison (64 systems, grids 16^3..64^3, 1..8 RHS)")
     p.add_argument("--eager", action="store_true",
@@ -410,6 +412,18 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    if args.profile_mixed:
+        A = inputs.perturbed27(args.mixed_grid, seed=7)
+        B = torch.from_numpy(inputs.rhs(A.n, 32, 3)).to(dev)
+        with bicgk.Operator(A) as opm:
+            bicgk.set_profiling(opm.handle, True)
+            for _ in range(1 + args.steps):
+                r = opm.solve_mixed(B, tol=1e-10, max_outer=20, inner_tol=1e-5, max_inner=5000, want_hist=False)
+            torch.cuda.synchronize()
+            times = bicgk.kernel_times(opm.handle)
+        print(json.dumps({"profile_mixed": True, "grid": args.mixed_grid, "outer": int(r.outer_iters.max()),
+                          "inner": float(r.inner_iters.mean()), "kernel_ms": times}), flush=True)
+        return
 
     A = inputs.convdiff7(args.grid)
     B_host = inputs.rhs(A.n, args.k, 2 + rank)

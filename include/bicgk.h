@@ -6,6 +6,8 @@
  * Method: B. Krasnopolsky, "Revisiting Performance of BiCGStab Methods for
  * Solving Systems with Multiple Right-Hand Sides", arXiv:1907.12874.
  *   - classical BiCGStab, basic (Algorithm 1) and merged (Algorithm 2) forms;
+ *   - preconditioned (Algorithm 5), preconditioned Pipelined (Algorithm 7) and
+ *     Improved (Algorithm 3) BiCGStab, basic and merged forms;
  *   - Reordered BiCGStab (Algorithm 6) with the identity preconditioner
  *     applied as a vector copy (Sec. 2.3), basic and merged forms;
  *   - Pipelined BiCGStab (Algorithm 4), basic and merged forms;
@@ -47,7 +49,13 @@ enum bicgk_variant {
   BICGK_REORDERED_PLAIN = 2,  /* Algorithm 6 with M^-1 = copy, one kernel per op   */
   BICGK_REORDERED_MERGED = 3, /* Algorithm 6 with M^-1 = copy                       */
   BICGK_PIPELINED_PLAIN = 4,  /* Algorithm 4, one kernel per op                     */
-  BICGK_PIPELINED_MERGED = 5  /* Algorithm 4                                        */
+  BICGK_PIPELINED_MERGED = 5, /* Algorithm 4                                        */
+  BICGK_PRECOND_PLAIN = 6,    /* Algorithm 5 (preconditioned), one kernel per op    */
+  BICGK_PRECOND_MERGED = 7,   /* Algorithm 5                                        */
+  BICGK_PPIPE_PLAIN = 8,      /* Algorithm 7 (preconditioned Pipelined), per op     */
+  BICGK_PPIPE_MERGED = 9,     /* Algorithm 7                                        */
+  BICGK_IMPROVED_PLAIN = 10,  /* Algorithm 3 (Improved, needs A^T r_0), per op      */
+  BICGK_IMPROVED_MERGED = 11  /* Algorithm 3                                        */
 };
 
 /* Per-RHS outcome written to status[c]. */
@@ -60,8 +68,10 @@ enum bicgk_rhs_status {
 
 /* Solve flags (bit mask). */
 enum bicgk_flags {
-  BICGK_FLAG_NO_STOP_TEST = 1 /* run exactly maxit iterations (fixed-count benchmarking,
-                                 Sec. 2.3 uses N_it = 1000); breakdown rules still apply */
+  BICGK_FLAG_NO_STOP_TEST = 1, /* run exactly maxit iterations (fixed-count benchmarking,
+                                  Sec. 2.3 uses N_it = 1000); breakdown rules still apply */
+  BICGK_FLAG_JACOBI = 2        /* M = diag(A) (Jacobi) instead of the identity copy in the forms
+                                  that apply M^-1 (Algorithms 5, 6, 7); a zero diagonal counts as 1 */
 };
 
 /* Error codes. */
@@ -189,10 +199,11 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
  *
  * Scratch: one 16 MiB file-scope device array in this library, which every
  * GPU that loads the library keeps until the process exits.  A problem fits if
- *   8*14*(n_rows*kp + 34) + 8*(maxit+1)*kp + 8*1024*SMs + ~1.3 KB <= 16 MiB
- * (kp = k rounded up to a power of two; about n_rows*kp <= 140,000 at
+ *   8*18*(n_rows*kp + 34) + 8*(maxit+1)*kp + 8*448*(4*SMs + 64) + ~2 KB <= 16 MiB
+ * (kp = k rounded up to a power of two; about n_rows*kp <= 95,000 at
  * maxit = 1000); larger problems return BICGK_E_UNSUPPORTED with the sizes in
- * bicgk_last_cuda_error().  The iteration loop runs from the host (one
+ * bicgk_last_cuda_error().  variant: 0..9 (the Improved form needs a
+ * transposed copy of A and is refused); flags: BICGK_FLAG_NO_STOP_TEST only.  The iteration loop runs from the host (one
  * stream synchronisation per iteration), not from a CUDA graph.
  *
  * Every call, on any stream or thread, uses the same array and leaves its

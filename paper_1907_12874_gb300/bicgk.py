@@ -24,9 +24,16 @@ VARIANTS = {
     "reordered_merged": 3,
     "pipelined_plain": 4,
     "pipelined_merged": 5,
+    "precond_plain": 6,
+    "precond_merged": 7,
+    "ppipe_plain": 8,
+    "ppipe_merged": 9,
+    "improved_plain": 10,
+    "improved_merged": 11,
 }
 STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "nonfinite"}
 FLAG_NO_STOP_TEST = 1
+FLAG_JACOBI = 2
 MAX_K = 64
 
 _lock = threading.Lock()

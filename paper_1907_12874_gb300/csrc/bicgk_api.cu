@@ -41,7 +41,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 // One step of a kernel sequence: a streaming op, or an SpMM between workspace roles.
 struct Step {
-  int spmm;  // 0: streaming op `op`; 1: y = A x; 2: y = b - A x; 3: y = A x in FP32
+  int spmm;  // 0: streaming op `op`; 1: y = A x; 2: y = b - A x; 3: y = A x in FP32; 4: y = A^T x
   int op;
   int x, y, b;
 };
@@ -49,6 +49,7 @@ Step vec(int op) { return Step{0, op, 0, 0, 0}; }
 Step spmm(int x, int y) { return Step{1, -1, x, y, 0}; }
 Step resid(int x, int y, int b) { return Step{2, -1, x, y, b}; }
 Step spmm32(int x, int y) { return Step{3, -1, x, y, 0}; }
+Step spmm_t(int x, int y) { return Step{4, -1, x, y, 0}; }
 
 
 
@@ -66,8 +67,9 @@ Seq make_inner32_seq() {
   return q;
 }
 
-// Kernel sequences of the six forms (one Step = one kernel launch).
-Seq make_seq(int variant) {
+// Kernel sequences of the twelve forms (one Step = one kernel launch).  `jacobi`: M = diag(A)
+// instead of the identity copy for the forms that apply M^-1 (Algorithms 5, 6, 7).
+Seq make_seq(int variant, bool jacobi = false) {
   Seq q;
   q.fin = {resid(V_X, V_TMP, V_B), vec(OP_TRUE_RES)};
   switch (variant) {
@@ -82,16 +84,18 @@ Seq make_seq(int variant) {
                 vec(OP_DOT_PSI), vec(OP_UPD_X_C), vec(OP_UPD_R_C), vec(OP_DOT_RR), vec(OP_DOT_RHO),
                 vec(OP_UPD_P)};
       break;
-    case BICGK_REORDERED_MERGED:  // Algorithm 6, M^-1 = copy; v^ in V_P, t^ in V_TMP
+    case BICGK_REORDERED_MERGED:  // Algorithm 6; v^ in V_P, t^ in V_TMP
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_R)};
-      q.body = {spmm(V_P, V_V), vec(OP_DELTA), vec(OP_COPY_SV), vec(OP_UPD_TH), spmm(V_TMP, V_T),
-                vec(OP_RG4), vec(OP_COPY_QT), vec(OP_UPD_R_R), vec(OP_RFIN)};
+      if (jacobi) q.setup.push_back(vec(OP_PREC_R_Z));
+      q.body = {spmm(V_P, V_V), vec(OP_DELTA), vec(OP_PREC_V_S), vec(OP_UPD_TH), spmm(V_TMP, V_T),
+                vec(OP_RG4), vec(OP_PREC_T_Q), vec(OP_UPD_R_R), vec(OP_RFIN)};
       break;
     case BICGK_REORDERED_PLAIN:
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_R)};
-      q.body = {spmm(V_P, V_V), vec(OP_DELTA), vec(OP_COPY_SV), vec(OP_UPD_TH), spmm(V_TMP, V_T),
+      if (jacobi) q.setup.push_back(vec(OP_PREC_R_Z));
+      q.body = {spmm(V_P, V_V), vec(OP_DELTA), vec(OP_PREC_V_S), vec(OP_UPD_TH), spmm(V_TMP, V_T),
                 vec(OP_UPD_RT), vec(OP_DOT_T_RT), vec(OP_DOT_T_T), vec(OP_DOT_T_R0), vec(OP_DOT_RT_RT),
-                vec(OP_COPY_QT), vec(OP_UPD_R_R), vec(OP_UPD_X_R), vec(OP_UPD_Z_R), vec(OP_UPD_VH)};
+                vec(OP_PREC_T_Q), vec(OP_UPD_R_R), vec(OP_UPD_X_R), vec(OP_UPD_Z_R), vec(OP_UPD_VH)};
       break;
     case BICGK_PIPELINED_MERGED:  // Algorithm 4
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_P), spmm(V_R, V_W), spmm(V_W, V_T), vec(OP_DOT_RW0)};
@@ -103,6 +107,42 @@ Seq make_seq(int variant) {
                 vec(OP_DOT_YY), vec(OP_DOT_QQ), spmm(V_Z, V_V), vec(OP_PU_X), vec(OP_PU_R), vec(OP_PU_TMP),
                 vec(OP_PU_W), vec(OP_DOT_R0R), vec(OP_DOT_R0Z), vec(OP_DOT_R0W), vec(OP_DOT_R0S),
                 spmm(V_W, V_T)};
+      break;
+    case BICGK_PRECOND_MERGED:  // Algorithm 5; p^ in V_Q, s^ in V_Y
+      q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_C)};
+      q.body = {vec(OP_PREC_P_Q), spmm(V_Q, V_V), vec(OP_DELTA), vec(OP_UPD_S), vec(OP_PREC_S_Y), spmm(V_Y, V_T),
+                vec(OP_G1), vec(OP5_RRHO), vec(OP5_UPD_X), vec(OP_UPD_P)};
+      break;
+    case BICGK_PRECOND_PLAIN:
+      q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_C)};
+      q.body = {vec(OP_PREC_P_Q), spmm(V_Q, V_V), vec(OP_DELTA), vec(OP_UPD_S), vec(OP_PREC_S_Y), spmm(V_Y, V_T),
+                vec(OP_DOT_TS), vec(OP_DOT_PSI), vec(OP5_UPD_X), vec(OP_UPD_R_C), vec(OP_DOT_RR),
+                vec(OP_DOT_RHO), vec(OP_UPD_P)};
+      break;
+    case BICGK_PPIPE_MERGED:  // Algorithm 7; p^ in V_P, q^ in V_RT
+      q.setup = {resid(V_X, V_R, V_B), vec(OP7_SETUP), vec(OP_PREC_R_RH), spmm(V_RH, V_W), vec(OP_PREC_W_WH),
+                 spmm(V_WH, V_T), vec(OP_DOT_RW0)};
+      q.body = {vec(OP7_L1), vec(OP7_L2), vec(OP_PREC_Z_ZH), spmm(V_ZH, V_V), vec(OP7_L4), vec(OP7_L5),
+                vec(OP_PREC_W_WH), spmm(V_WH, V_T)};
+      break;
+    case BICGK_PPIPE_PLAIN:
+      q.setup = {resid(V_X, V_R, V_B), vec(OP7_SETUP), vec(OP_PREC_R_RH), spmm(V_RH, V_W), vec(OP_PREC_W_WH),
+                 spmm(V_WH, V_T), vec(OP_DOT_RW0)};
+      q.body = {vec(OP7_PU_PH), vec(OP7_PU_SH), vec(OP7_PU_QH), vec(OP_PU_S), vec(OP_PU_Z), vec(OP_PU_Q),
+                vec(OP_PU_Y), vec(OP_DOT_QY), vec(OP_DOT_YY), vec(OP_DOT_QQ), vec(OP_PREC_Z_ZH), spmm(V_ZH, V_V),
+                vec(OP7_X), vec(OP7_TMPH), vec(OP7_RH), vec(OP_PU_R), vec(OP_PU_TMP), vec(OP_PU_W),
+                vec(OP_DOT_R0R), vec(OP_DOT_R0Z), vec(OP_DOT_R0W), vec(OP_DOT_R0S), vec(OP_PREC_W_WH),
+                spmm(V_WH, V_T)};
+      break;
+    case BICGK_IMPROVED_MERGED:  // Algorithm 3; u in V_W, f_0 = A^T r_0 in V_RT
+      q.setup = {resid(V_X, V_R, V_B), vec(OP3_SETUP), spmm(V_R, V_W), spmm_t(V_R, V_RT), vec(OP3_SIG0)};
+      q.body = {vec(OP3_L1), spmm(V_V, V_Q), vec(OP3_L2), vec(OP3_L3), spmm(V_R, V_W)};
+      break;
+    case BICGK_IMPROVED_PLAIN:
+      q.setup = {resid(V_X, V_R, V_B), vec(OP3_SETUP), spmm(V_R, V_W), spmm_t(V_R, V_RT), vec(OP3_SIG0)};
+      q.body = {vec(OP3_Z), vec(OP3_V), vec(OP3_S), spmm(V_V, V_Q), vec(OP3_T), vec(OP3_D_R0S), vec(OP3_D_R0Q),
+                vec(OP3_D_F0S), vec(OP3_D_F0T), vec(OP3_D_ST), vec(OP3_D_TT), vec(OP3_D_SS), vec(OP_UPD_R_C),
+                vec(OP3_X), spmm(V_R, V_W)};
       break;
   }
   return q;
@@ -163,6 +203,7 @@ struct bicgk_op_s {
   Workspace ws[kMaxGroups];
   Workspace ws32;            // FP32 inner-solve workspace of the mixed-precision refinement
   bicgk_op trans = nullptr;  // operator of A^T (atomic-free transpose products; made on first use)
+  double *d_invdiag = nullptr;  // Jacobi preconditioner 1/a_ii (made on first use)
   double *d_stage[2] = {nullptr, nullptr};  // caller-layout staging for host-memory calls
   int64_t stage_elems = 0;
   cudaStream_t cap_stream = nullptr;
@@ -190,9 +231,10 @@ struct bicgk_op_s {
 namespace {
 
 KArgs make_args(bicgk_op A, const Workspace &W, int use_cond, cudaGraphConditionalHandle h,
-                const int *ext_act = nullptr) {
+                const int *ext_act = nullptr, const double *invdiag = nullptr) {
   KArgs a;
   a.ext_act = ext_act;
+  a.invdiag = invdiag;
   for (int r = 0; r < V_NVEC; ++r) a.v[r] = W.d_vec + (int64_t)r * W.vstride;
   a.sc = W.d_sc;
   a.fl = W.d_fl;
@@ -232,6 +274,14 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
   sa.n = A->n;
   sa.stage_cap = a.kp <= 2 ? A->stage_cap : 0;
   sa.cols_per_lane = a.kp >= 8 ? A->spmm_cpl : 2;
+  if (st.spmm == 4) {  // y = A^T x: the SpMM kernel over the transposed copy
+    bicgk_op T = A->trans;
+    sa.rowptr = T->d_rowptr;
+    sa.colidx = T->d_col;
+    sa.vals = T->d_val;
+    sa.stage_cap = a.kp <= 2 ? T->stage_cap : 0;
+    return launch_spmm(a.kp, 0, sa, spmm_grid(T, a.kp, 0), s);
+  }
   if (st.spmm == 3) {
     sa.vals = A->d_val32;
     return launch_spmm32(a.kp, sa, A->nsm * spmm32_blocks_per_sm(a.kp, sa.stage_cap), s);
@@ -340,13 +390,14 @@ int ensure_stage(bicgk_op A, int64_t elems) {
 }
 
 // Capture q.setup + WHILE(q.body) + q.fin for workspace W into one graph.
-int build_graph_seq(bicgk_op A, Workspace &W, const Seq &q, const int *ext_act, GraphEntry *ge) {
+int build_graph_seq(bicgk_op A, Workspace &W, const Seq &q, const int *ext_act, GraphEntry *ge,
+                    const double *invdiag = nullptr) {
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   ge->graph = g;
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-  const KArgs a = make_args(A, W, 1, h, ext_act);
+  const KArgs a = make_args(A, W, 1, h, ext_act, invdiag);
   cudaStream_t cs = A->cap_stream;
   // set-up
   CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -400,8 +451,21 @@ int build_graph_seq(bicgk_op A, Workspace &W, const Seq &q, const int *ext_act, 
   return BICGK_OK;
 }
 
-int build_graph(bicgk_op A, Workspace &W, int variant, GraphEntry *ge) {
-  return build_graph_seq(A, W, make_seq(variant), nullptr, ge);
+int build_graph(bicgk_op A, Workspace &W, int variant, bool jacobi, GraphEntry *ge) {
+  return build_graph_seq(A, W, make_seq(variant, jacobi), nullptr, ge, jacobi ? A->d_invdiag : nullptr);
+}
+
+// What a form needs beyond the operator: the transposed copy (Algorithm 3), the Jacobi diagonal.
+int ensure_variant_data(bicgk_op A, int variant, bool jacobi, cudaStream_t s) {
+  if ((variant == BICGK_IMPROVED_PLAIN || variant == BICGK_IMPROVED_MERGED) && !A->trans) {
+    int rc = bicgk_op_transpose(A, &A->trans, s);
+    if (rc) return rc;
+  }
+  if (jacobi && !A->d_invdiag) {
+    CK(cudaMalloc(&A->d_invdiag, sizeof(double) * A->n));
+    CK(launch_invdiag(A->d_rowptr, A->d_col, A->d_val, A->d_invdiag, A->n, s));
+  }
+  return BICGK_OK;
 }
 
 int check_device(int *dev, int *nsm) {
@@ -424,8 +488,7 @@ void prof_record(bicgk_op A, const std::string &name, float ms) {
 }
 
 // Profiling mode: the loop runs from the host, one launch at a time, each bracketed by events.
-int run_profiled(bicgk_op A, Workspace &W, int variant, const KArgs &a, cudaStream_t s) {
-  const Seq q = make_seq(variant);
+int run_profiled_seq(bicgk_op A, Workspace &W, const Seq &q, const KArgs &a, cudaStream_t s) {
   const size_t nmax = q.body.size() > q.setup.size() ? q.body.size() : q.setup.size();
   while (A->ev.size() < 2 * (nmax + 2)) {
     cudaEvent_t e;
@@ -456,6 +519,10 @@ int run_profiled(bicgk_op A, Workspace &W, int variant, const KArgs &a, cudaStre
     go = W.h_ctl->any_active && W.h_ctl->iter < W.h_ctl->maxit;
   }
   return run_list(q.fin);
+}
+
+int run_profiled(bicgk_op A, Workspace &W, int variant, bool jacobi, const KArgs &a, cudaStream_t s) {
+  return run_profiled_seq(A, W, make_seq(variant, jacobi), a, s);
 }
 
 }  // namespace
@@ -541,6 +608,7 @@ int bicgk_op_destroy(bicgk_op A) {
   if (!A) return BICGK_OK;
   cudaDeviceSynchronize();
   if (A->trans) bicgk_op_destroy(A->trans);
+  cudaFree(A->d_invdiag);
   for (Workspace &W : A->ws) free_workspace(W);
   free_workspace(A->ws32);
   cudaFree(A->d_val32);
@@ -590,10 +658,14 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
                 int variant, int32_t flags, int mem, double *X, int32_t *iters, int32_t *status,
                 double *resid_hist, double *true_relres, void *stream) {
   if (!A || !B || !X || !iters || !status || k < 1 || !(rel_tol >= 0.0) || maxit < 0 || maxit > 10000000 ||
-      variant < 0 || variant > 5 || (mem != BICGK_MEM_HOST && mem != BICGK_MEM_DEVICE) || (flags & ~1))
+      variant < 0 || variant > 11 || (mem != BICGK_MEM_HOST && mem != BICGK_MEM_DEVICE) || (flags & ~3))
     return BICGK_E_INVALID;
   if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
+  const bool jacobi = (flags & BICGK_FLAG_JACOBI) != 0;
+  const int gkey = variant + 100 * (jacobi ? 1 : 0);
+  int rc0 = ensure_variant_data(A, variant, jacobi, s);
+  if (rc0) return rc0;
   // columns are independent: split k >= kSplitMinK into two groups solved concurrently, so that
   // one group's FP64-bound SpMM overlaps the other group's bandwidth-bound vector kernels
   const int ngroups = (!A->profiling && A->opt_groups != 1 && k >= kSplitMinK) ? 2 : 1;
@@ -606,7 +678,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     if ((rc = ensure_workspace(A, A->ws[g], kpg))) return rc;
     if ((rc = ensure_hist(A->ws[g], (int64_t)(maxit + 1) * kpg))) return rc;
   }
-  const Seq q = make_seq(variant);
+  const Seq q = make_seq(variant, jacobi);
   // inputs
   const double *dB = B, *dX0 = X0;
   double *dX = X;
@@ -637,22 +709,22 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     hc->kp = W.kp;
     hc->flags = flags;
     CK(cudaMemcpyAsync(W.d_ctl, hc, sizeof(Ctl), cudaMemcpyHostToDevice, gs));
-    const KArgs a0 = make_args(A, W, 0, cudaGraphConditionalHandle{});
+    const KArgs a0 = make_args(A, W, 0, cudaGraphConditionalHandle{}, nullptr, jacobi ? A->d_invdiag : nullptr);
     CK(launch_reset(a0, hist_len, gs));
     CK(launch_pack(dB + c0[g], dX0 ? dX0 + c0[g] : nullptr, k, kg, a0, gs));
     launches += 2;  // reset, pack
     if (A->profiling) {
-      if ((rc = run_profiled(A, W, variant, a0, gs))) return rc;
+      if ((rc = run_profiled(A, W, variant, jacobi, a0, gs))) return rc;
     } else {
-      auto it = W.graphs.find(variant);
+      auto it = W.graphs.find(gkey);
       if (it == W.graphs.end()) {
         GraphEntry ge;
-        if ((rc = build_graph(A, W, variant, &ge))) {
+        if ((rc = build_graph(A, W, variant, jacobi, &ge))) {
           if (ge.exec) cudaGraphExecDestroy(ge.exec);
           if (ge.graph) cudaGraphDestroy(ge.graph);
           return rc;
         }
-        it = W.graphs.emplace(variant, ge).first;
+        it = W.graphs.emplace(gkey, ge).first;
       }
       CK(cudaGraphLaunch(it->second.exec, gs));
     }
@@ -792,7 +864,12 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
     hi->kp = kp;
     CK(cudaMemcpyAsync(V.d_ctl, hi, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(launch_reset(ai0, (int64_t)(max_inner + 1) * kp, s));
-    CK(cudaGraphLaunch(it->second.exec, s));                           // FP32 inner solve of A d = r
+    if (A->profiling) {  // the same kernels from a host loop, each timed (profilers see them)
+      const KArgs ai = make_args(A, V, 0, cudaGraphConditionalHandle{}, ext_act);
+      if ((rc = run_profiled_seq(A, V, qi, ai, s))) return rc;
+    } else {
+      CK(cudaGraphLaunch(it->second.exec, s));                         // FP32 inner solve of A d = r
+    }
     CK(launch_vec(OP_IR_UPDATE, air, vec_grid(A, OP_IR_UPDATE), s));   // x += d (FP64)
     CK(cudaMemcpyAsync(V.h_fl, V.d_fl, sizeof(int) * F_NFLAG * kMaxKp, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(V.h_ctl, V.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -991,8 +1068,8 @@ int batch_ensure(bicgk_batch b, int32_t maxit) {
   return BICGK_OK;
 }
 
-int batch_build_graph(bicgk_batch b, int variant, GraphEntry *ge) {
-  const Seq q = make_seq(variant);
+int batch_build_graph(bicgk_batch b, int variant, bool jacobi, GraphEntry *ge) {
+  const Seq q = make_seq(variant, jacobi);
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   ge->graph = g;
@@ -1003,7 +1080,7 @@ int batch_build_graph(bicgk_batch b, int variant, GraphEntry *ge) {
     Workspace &W = b->ws[i];
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-    const KArgs a = make_args(A, W, 1, h);
+    const KArgs a = make_args(A, W, 1, h, nullptr, jacobi ? A->d_invdiag : nullptr);
     CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = launch_reset(a, W.hist_cap, cs);
     if (e == cudaSuccess) e = launch_pack_io(b->d_io + i, b->k[i], a, cs);
@@ -1215,8 +1292,10 @@ int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const
                       double rel_tol, int32_t maxit, int variant, int32_t flags, int mode, int32_t *iters,
                       int32_t *status, double *true_relres, void *stream) {
   if (!b || !B || !X || !iters || !status || !(rel_tol >= 0.0) || maxit < 0 || maxit > 10000000 || variant < 0 ||
-      variant > 5 || (flags & ~1) || (mode != BICGK_BATCH_GRAPH && mode != BICGK_BATCH_LOOP))
+      variant > 11 || (flags & ~3) || (mode != BICGK_BATCH_GRAPH && mode != BICGK_BATCH_LOOP))
     return BICGK_E_INVALID;
+  const bool jacobi = (flags & BICGK_FLAG_JACOBI) != 0;
+  const int gkey = variant + 100 * (jacobi ? 1 : 0);
   for (int i = 0; i < b->nsys; ++i)
     if (!B[i] || !X[i]) return BICGK_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1235,6 +1314,8 @@ int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const
     return BICGK_OK;
   }
   if ((rc = batch_ensure(b, maxit))) return rc;
+  for (int i = 0; i < b->nsys; ++i)
+    if ((rc = ensure_variant_data(b->ops[i], variant, jacobi, s))) return rc;
   for (int i = 0; i < b->nsys; ++i) {
     Ctl *hc = b->h_ctl + i;
     memset(hc, 0, sizeof(Ctl));
@@ -1250,22 +1331,22 @@ int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const
   }
   CK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(Ctl) * b->nsys, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(b->d_io, b->h_io, sizeof(BatchIO) * b->nsys, cudaMemcpyHostToDevice, s));
-  auto it = b->graphs.find(variant);
+  auto it = b->graphs.find(gkey);
   if (it == b->graphs.end()) {
     GraphEntry ge;
-    if ((rc = batch_build_graph(b, variant, &ge))) {
+    if ((rc = batch_build_graph(b, variant, jacobi, &ge))) {
       if (ge.exec) cudaGraphExecDestroy(ge.exec);
       if (ge.graph) cudaGraphDestroy(ge.graph);
       return rc;
     }
-    it = b->graphs.emplace(variant, ge).first;
+    it = b->graphs.emplace(gkey, ge).first;
   }
   CK(cudaGraphLaunch(it->second.exec, s));
   CK(cudaMemcpyAsync(b->h_fl, b->d_fl, sizeof(int) * F_NFLAG * kMaxKp * b->nsys, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(b->h_sc, b->d_sc, sizeof(double) * S_NSLOT * kMaxKp * b->nsys, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(Ctl) * b->nsys, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  const Seq q = make_seq(variant);
+  const Seq q = make_seq(variant, jacobi);
   for (int i = 0; i < b->nsys; ++i) {
     const int *fl = b->h_fl + (size_t)i * F_NFLAG * kMaxKp;
     const double *sc = b->h_sc + (size_t)i * S_NSLOT * kMaxKp;
@@ -1318,7 +1399,7 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
                                    void *stream) {
   if (n_rows < 1 || nnz < 0 || n_rows > INT32_MAX - 1 || nnz > INT32_MAX || !rowptr || (nnz > 0 && (!colidx || !vals)) ||
       !B || !X || !iters || !status || k < 1 || !(rel_tol >= 0.0) || maxit < 0 || maxit > 10000000 ||
-      variant < 0 || variant > 5 || (flags & ~1))
+      variant < 0 || variant > 9 || (flags & ~1))
     return BICGK_E_INVALID;
   if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;

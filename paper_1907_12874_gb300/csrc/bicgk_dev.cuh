@@ -16,7 +16,7 @@ namespace bicgk {
 
 constexpr int kVecThreads = 512;  // threads per block of the streaming kernels
 constexpr int kMaxKp = 64;        // largest padded RHS count
-constexpr int kMaxDots = 4;       // largest number of dot products fused in one pass
+constexpr int kMaxDots = 7;       // largest number of dot products fused in one pass (Algorithm 3)
 constexpr int kSpmmThreads = 256; // threads per block of the SpMM kernels
 constexpr int kSpmmTileRows = 256;      // rows per staged tile (kp <= 2 path)
 constexpr int kSpmmStageMax = 4096;     // largest staged tile (CSR entries)
@@ -25,7 +25,10 @@ constexpr int kMaxRedGroups = 64;       // group tickets (grids up to 1024 block
 
 // Per-column FP64 scalar slots.
 enum Slot : int {
-  S_RHO = 0, S_ALPHA, S_OMEGA, S_BETA, S_EPS2, S_BN2, S_D0, S_D1, S_D2, S_TRUE, S_NSLOT
+  S_RHO = 0, S_ALPHA, S_OMEGA, S_BETA, S_EPS2, S_BN2, S_D0, S_D1, S_D2, S_TRUE,
+  // Algorithm 3 (Improved BiCGStab): stored dots of the basic form and the recurrence state
+  S_D3, S_D4, S_D5, S_SIGMA, S_SIGP, S_PI, S_TAU, S_PHI, S_AOLD, S_CZ, S_CV, S_DLT,
+  S_NSLOT
 };
 // Per-column int flags.
 enum Flag : int { F_ACT = 0, F_XUPD, F_XZERO, F_ITERS, F_STATUS, F_NFLAG };
@@ -50,8 +53,10 @@ struct Ctl {
 };
 
 // Vector roles in the workspace.
+// Algorithm 5 keeps p^ in V_Q and s^ in V_Y; Algorithm 7 keeps p^ in V_P and q^ in V_RT plus the
+// four hatted roles below; Algorithm 3 keeps u in V_W and f_0 = A^T r_0 in V_RT.
 enum Vec : int {
-  V_X = 0, V_R, V_R0, V_P, V_V, V_S, V_T, V_W, V_Z, V_Q, V_Y, V_TMP, V_RT, V_B, V_NVEC
+  V_X = 0, V_R, V_R0, V_P, V_V, V_S, V_T, V_W, V_Z, V_Q, V_Y, V_TMP, V_RT, V_B, V_SH, V_ZH, V_RH, V_WH, V_NVEC
 };
 
 struct KArgs {
@@ -65,6 +70,7 @@ struct KArgs {
   int use_cond;  // 1 inside the captured graph (the loop is a conditional WHILE node)
   cudaGraphConditionalHandle cond;
   const int *ext_act;  // inner solves of the refinement: columns the outer loop still iterates
+  const double *invdiag;  // Jacobi preconditioner 1/a_ii per row (nullptr: M = identity, a copy)
 };
 
 // Streaming kernel identifiers (one per fused vector operation of the listings).
@@ -87,6 +93,15 @@ enum Op : int {
   OP32_SETUP, OP32_DELTA, OP32_UPD_S, OP32_G1, OP32_G3, OP32_UPD_P,
   // mixed-precision refinement: FP64 outer steps (V_Q / V_Y point to the FP32 b and d blocks)
   OP_IR_SETUP, OP_IR_RESID, OP_IR_UPDATE,
+  // preconditioner applications y = M^-1 x (identity copy or Jacobi)
+  OP_PREC_P_Q, OP_PREC_S_Y, OP_PREC_R_RH, OP_PREC_W_WH, OP_PREC_Z_ZH, OP_PREC_R_Z, OP_PREC_V_S, OP_PREC_T_Q,
+  // Algorithm 5 (preconditioned BiCGStab)
+  OP5_RRHO, OP5_UPD_X,
+  // Algorithm 7 (preconditioned Pipelined BiCGStab)
+  OP7_SETUP, OP7_L1, OP7_L2, OP7_L4, OP7_L5, OP7_PU_PH, OP7_PU_SH, OP7_PU_QH, OP7_X, OP7_TMPH, OP7_RH,
+  // Algorithm 3 (Improved BiCGStab)
+  OP3_SETUP, OP3_SIG0, OP3_L1, OP3_L2, OP3_L3, OP3_Z, OP3_V, OP3_S, OP3_T, OP3_D_R0S, OP3_D_R0Q, OP3_D_F0S,
+  OP3_D_F0T, OP3_D_ST, OP3_D_TT, OP3_D_SS, OP3_X,
   OP_COUNT
 };
 
@@ -144,6 +159,9 @@ cudaError_t launch_pack_io(const BatchIO *io, int k, const KArgs &a, cudaStream_
 cudaError_t launch_unpack_io(const BatchIO *io, int k, const KArgs &a, cudaStream_t s);
 // dst = (float)src elementwise.
 cudaError_t launch_to_float(const double *src, float *dst, int64_t n, cudaStream_t s);
+// Jacobi preconditioner: invdiag[i] = 1 / (sum of the row's diagonal entries), 1 where that is 0.
+cudaError_t launch_invdiag(const int32_t *rowptr, const int32_t *colidx, const double *vals, double *invdiag,
+                           int64_t n, cudaStream_t s);
 // Fill the history with NaN and clear the per-column state.
 cudaError_t launch_reset(const KArgs &a, int64_t hist_len, cudaStream_t s);
 

@@ -61,7 +61,34 @@ __global__ void __launch_bounds__(kSpmmThreads) spmm_group_kernel(const SpmmArgs
     T2 acc[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) acc[h] = Vec2<T>::make(0, 0);
+    // FP32: four nonzeros per step.  Their column indices, values and x rows are all loaded
+    // before the first FMA (memory-level parallelism for the gathers); the FMAs then run in entry
+    // order, so the sum is the one of a loop over single entries.  The FP64 kernel is bound by its
+    // FMA pipe instead, and the extra registers spill there.
     int e = e0;
+    if constexpr (sizeof(T) == 4) {
+      for (; e + 3 < e1; e += 4) {
+        int j[4];
+        T av[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          j[q] = __ldg(ci + e + q);
+          av[q] = __ldg(va + e + q);
+        }
+        T2 u[4][H];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int h = 0; h < H; ++h) u[q][h] = __ldg(x2 + (int64_t)j[q] * (KP / 2) + cl * H + h);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int h = 0; h < H; ++h) {
+            acc[h].x = fma(av[q], u[q][h].x, acc[h].x);
+            acc[h].y = fma(av[q], u[q][h].y, acc[h].y);
+          }
+      }
+    }
     for (; e + 1 < e1; e += 2) {
       const int j0 = __ldg(ci + e), j1 = __ldg(ci + e + 1);
       const T a0 = __ldg(va + e), a1 = __ldg(va + e + 1);

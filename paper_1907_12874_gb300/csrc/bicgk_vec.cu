@@ -52,6 +52,7 @@ __device__ __forceinline__ double2 sel2(bool u0, bool u1, double2 nv, double2 ov
 // Per-thread scalars of its two columns.
 struct Sc2 {
   double2 al, om, be;
+  double2 cz, cv, dl;    // Algorithm 3: beta (alpha_{j+1}/alpha_j), alpha_{j+1} delta_{j+1}, delta_{j+1}
   float2 alf, omf, bef;  // the same scalars rounded to FP32 (FP32 inner solves)
   bool u0, u1;
 };
@@ -124,9 +125,37 @@ __device__ __forceinline__ double sub_rn(double x, double y) { return __dadd_rn(
 enum Fin : int {
   FIN_NONE = 0, FIN_SETUP, FIN_RW0, FIN_DELTA, FIN_G1, FIN_RHO, FIN_STORE_D0, FIN_STORE_D1, FIN_STORE_D2,
   FIN_PSI, FIN_RR, FIN_R4_MERGED, FIN_R4_PLAIN, FIN_PG1_MERGED, FIN_PG1_PLAIN, FIN_PG3_MERGED,
-  FIN_PG3_PLAIN, FIN_TRUE, FIN_IR_SETUP, FIN_IR_RESID
+  FIN_PG3_PLAIN, FIN_TRUE, FIN_IR_SETUP, FIN_IR_RESID, FIN_STORE_D3, FIN_STORE_D4, FIN_STORE_D5, FIN_I_START,
+  FIN_I7_MERGED, FIN_I7_PLAIN
 };
 enum Ctl_ : int { CTL_NONE = 0, CTL_START = 1, CTL_END_ITER = 2, CTL_OUTER = 3 };
+
+// Algorithm 3, scalar lines of iteration j (state: phi_j, pi_j, sigma_j, sigma_{j-1}, tau_j, rho_j,
+// alpha_j, omega_j): rho_{j+1}, delta_{j+1}, beta_{j+1}, tau_{j+1}, alpha_{j+1} and the vector
+// coefficients, evaluated as written (no contraction).  Returns false if the column stopped.
+__device__ bool i3_next(const KArgs &a, int c) {
+  const double phi = SC(S_PHI, c), om = SC(S_OMEGA, c), sgp = SC(S_SIGP, c), al = SC(S_AOLD, c);
+  const double pi = SC(S_PI, c), sg = SC(S_SIGMA, c), rho = SC(S_RHO, c), tau = SC(S_TAU, c);
+  const double rho1 = __dadd_rn(sub_rn(phi, __dmul_rn(om, sgp)), __dmul_rn(__dmul_rn(om, al), pi));
+  if (!fin1(rho1) || !fin1(sg)) { col_stop(a, c, ST_NONFINITE); return false; }
+  if (rho == 0.0 || om == 0.0) { col_stop(a, c, ST_BREAKDOWN); return false; }
+  const double de1 = __dmul_rn(__ddiv_rn(rho1, rho), al);
+  const double be1 = __ddiv_rn(de1, om);
+  const double tau1 = sub_rn(__dadd_rn(sg, __dmul_rn(be1, tau)), __dmul_rn(de1, pi));
+  if (!fin1(de1) || !fin1(be1) || !fin1(tau1)) { col_stop(a, c, ST_NONFINITE); return false; }
+  if (tau1 == 0.0) { col_stop(a, c, ST_BREAKDOWN); return false; }
+  const double al1 = __ddiv_rn(rho1, tau1);
+  if (!fin1(al1)) { col_stop(a, c, ST_NONFINITE); return false; }
+  SC(S_ALPHA, c) = al1;
+  SC(S_BETA, c) = be1;
+  SC(S_DLT, c) = de1;
+  SC(S_CZ, c) = __dmul_rn(be1, __ddiv_rn(al1, al));
+  SC(S_CV, c) = __dmul_rn(al1, de1);
+  SC(S_RHO, c) = rho1;
+  SC(S_TAU, c) = tau1;
+  SC(S_AOLD, c) = al1;
+  return true;
+}
 
 // Column c, executed by thread c of the last block.  s[d*kp + c] = dot d of column c.
 template <int FIN>
@@ -349,6 +378,58 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
     else if (rr < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
     else if (j >= ctl->maxit) col_stop(a, c, ST_MAXIT);
     else FL(F_ITERS, c) = j + 1;
+  } else if constexpr (FIN == FIN_STORE_D3) {
+    SC(S_D3, c) = s[c];
+  } else if constexpr (FIN == FIN_STORE_D4) {
+    SC(S_D4, c) = s[c];
+  } else if constexpr (FIN == FIN_STORE_D5) {
+    SC(S_D5, c) = s[c];
+  } else if constexpr (FIN == FIN_I_START) {
+    // Algorithm 3 set-up: sigma_0 = (r_0, u_0), phi_0 = (r_0, r_0), sigma_{-1} = pi_0 = tau_0 = 0,
+    // rho_0 = alpha_0 = omega_0 = 1; then the scalar lines of iteration 0
+    if (!FL(F_ACT, c)) return;
+    SC(S_PHI, c) = SC(S_RHO, c);
+    SC(S_SIGMA, c) = s[c];
+    SC(S_SIGP, c) = 0.0;
+    SC(S_PI, c) = 0.0;
+    SC(S_TAU, c) = 0.0;
+    SC(S_RHO, c) = 1.0;
+    SC(S_AOLD, c) = 1.0;
+    SC(S_OMEGA, c) = 1.0;
+    if (ctl->maxit > 0) i3_next(a, c);
+  } else if constexpr (FIN == FIN_I7_MERGED || FIN == FIN_I7_PLAIN) {
+    // Algorithm 3: phi = (r_0,s), pi = (r_0,q), gamma = (f_0,s), eta = (f_0,t), theta = (s,t),
+    // kappa = (t,t), nu = (s,s); omega = theta/kappa; sigma = gamma - omega eta; stop on nu - omega theta
+    FL(F_XUPD, c) = 0;
+    if (!FL(F_ACT, c)) return;
+    double ph, pi, ga, et, th, ka, nu;
+    if constexpr (FIN == FIN_I7_MERGED) {
+      ph = s[0 * kp + c]; pi = s[1 * kp + c]; ga = s[2 * kp + c]; et = s[3 * kp + c];
+      th = s[4 * kp + c]; ka = s[5 * kp + c]; nu = s[6 * kp + c];
+    } else {
+      ph = SC(S_D0, c); pi = SC(S_D1, c); ga = SC(S_D2, c); et = SC(S_D3, c); th = SC(S_D4, c); ka = SC(S_D5, c);
+      nu = s[c];
+    }
+    if (!fin1(ph) || !fin1(pi) || !fin1(ga) || !fin1(et) || !fin1(th) || !fin1(ka) || !fin1(nu)) {
+      col_stop(a, c, ST_NONFINITE);
+      return;
+    }
+    const double om = ka == 0.0 ? 0.0 : __ddiv_rn(th, ka);
+    if (!fin1(om)) { col_stop(a, c, ST_NONFINITE); return; }
+    const int j = ctl->iter;
+    const double sg1 = sub_rn(ga, __dmul_rn(om, et));
+    SC(S_OMEGA, c) = om;  // the r and x updates of this iteration use omega_{j+1}
+    FL(F_XUPD, c) = 1;
+    FL(F_ITERS, c) = j + 1;
+    const double est = sub_rn(nu, __dmul_rn(om, th));
+    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(est);
+    if (!fin1(est)) { col_stop(a, c, ST_NONFINITE); return; }
+    if (!nostop && est < SC(S_EPS2, c)) { col_stop(a, c, ST_CONVERGED); return; }
+    SC(S_SIGP, c) = SC(S_SIGMA, c);
+    SC(S_SIGMA, c) = sg1;
+    SC(S_PHI, c) = ph;
+    SC(S_PI, c) = pi;
+    if (j + 1 < ctl->maxit) i3_next(a, c);  // the next iteration's scalar lines
   }
 }
 
@@ -720,6 +801,256 @@ template <> struct OpDef<OP_DOT_R0S> : DotOp<V_R0, V_S, FIN_PG3_PLAIN, CTL_END_I
 // ---- final residual norm (V_TMP holds b - A x)
 template <> struct OpDef<OP_TRUE_RES> : DotOp<V_TMP, V_TMP, FIN_TRUE, CTL_NONE> {};
 
+
+// ---- preconditioner application y = M^-1 x: a copy (M = I) or the Jacobi scaling x_i / a_ii
+template <int SRC, int DST, int DST2 = -1>
+struct PrecOp {
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 1;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(SRC), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &, double2 (&)[1]) {
+    double2 y = v[0];
+    if (a.invdiag) {
+      const int sh = __ffs(a.kp) - 1;
+      y.x *= __ldg(a.invdiag + ((2 * i) >> sh));
+      y.y *= __ldg(a.invdiag + ((2 * i + 1) >> sh));
+    }
+    st2(V(DST), i, y);
+    if constexpr (DST2 >= 0) st2(V(DST2), i, y);
+  }
+};
+template <> struct OpDef<OP_PREC_P_Q> : PrecOp<V_P, V_Q> {};
+template <> struct OpDef<OP_PREC_S_Y> : PrecOp<V_S, V_Y> {};
+template <> struct OpDef<OP_PREC_R_RH> : PrecOp<V_R, V_RH> {};
+template <> struct OpDef<OP_PREC_W_WH> : PrecOp<V_W, V_WH> {};
+template <> struct OpDef<OP_PREC_Z_ZH> : PrecOp<V_Z, V_ZH> {};
+template <> struct OpDef<OP_PREC_R_Z> : PrecOp<V_R, V_Z, V_P> {};  // Alg. 6: z_0 = M^-1 r_0, v^_0 = z_0
+template <> struct OpDef<OP_PREC_V_S> : PrecOp<V_V, V_S> {};
+template <> struct OpDef<OP_PREC_T_Q> : PrecOp<V_T, V_Q> {};
+
+// X += alpha VP + omega VQ for the columns forming x_{j+1}
+template <int VP, int VQ>
+struct XUpd {
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_X), i); v[1] = ld2(V(VP), i); v[2] = ld2(V(VQ), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 xn = fma2(s.om, v[2], fma2(s.al, v[1], v[0]));
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+  }
+};
+// DST = VR - omega VM
+template <int DST, int VR, int VM>
+struct OUpd {
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(VR), i); v[1] = ld2(V(VM), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(DST), i, fma2(neg2(s.om), v[1], v[0]));
+  }
+};
+
+// ---- Algorithm 5 (p^ in V_Q, s^ in V_Y)
+template <>
+struct OpDef<OP5_RRHO> {  // r_{j+1} = s - omega t with rho_{j+1} = (r_{j+1}, r_0)
+  static constexpr int ND = 1, FIN = FIN_RHO, CTL = CTL_END_ITER, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_S), i); v[1] = ld2(V(V_T), i); v[2] = ld2(V(V_R0), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&acc)[ND]) {
+    const double2 r = fma2(neg2(s.om), v[1], v[0]);
+    st2(V(V_R), i, r);
+    dot_acc(acc[0], r, v[2]);
+  }
+};
+template <> struct OpDef<OP5_UPD_X> : XUpd<V_Q, V_Y> {};  // x += alpha p^ + omega s^
+
+// ---- Algorithm 7 (p^ in V_P, q^ in V_RT, s^ z^ r^ w^ in V_SH V_ZH V_RH V_WH)
+template <>
+struct OpDef<OP7_SETUP> {  // r^_0 := r_0 kept as r_0; step -1 vectors p^, s^, z^, s, z, v = 0
+  static constexpr int ND = 2, FIN = FIN_SETUP, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_B), i); v[1] = ld2(V(V_R), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &, double2 (&acc)[ND]) {
+    const double2 z = make_double2(0.0, 0.0);
+    st2(V(V_R0), i, v[1]);
+    st2(V(V_P), i, z);
+    st2(V(V_SH), i, z);
+    st2(V(V_ZH), i, z);
+    st2(V(V_S), i, z);
+    st2(V(V_Z), i, z);
+    st2(V(V_V), i, z);
+    dot_acc(acc[0], v[0], v[0]);
+    dot_acc(acc[1], v[1], v[1]);
+  }
+};
+template <>
+struct OpDef<OP7_L1> {  // p^ = r^ + beta (p^ - omega s^); s^ = w^ + beta (s^ - omega z^); q^ = r^ - alpha s^
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 5;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_RH), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_SH), i); v[3] = ld2(V(V_WH), i); v[4] = ld2(V(V_ZH), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 nom = neg2(s.om);
+    st2(V(V_P), i, fma2(s.be, fma2(nom, v[2], v[1]), v[0]));
+    const double2 sh = fma2(s.be, fma2(nom, v[4], v[2]), v[3]);
+    st2(V(V_SH), i, sh);
+    st2(V(V_RT), i, fma2(neg2(s.al), sh, v[0]));
+  }
+};
+template <>
+struct OpDef<OP7_L2> {  // s, z, q, y with theta = (q,y), phi = (y,y), pi = (q,q)
+  static constexpr int ND = 3, FIN = FIN_PG1_MERGED, CTL = CTL_NONE, NL = 6;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_W), i); v[1] = ld2(V(V_S), i); v[2] = ld2(V(V_Z), i); v[3] = ld2(V(V_T), i);
+    v[4] = ld2(V(V_V), i); v[5] = ld2(V(V_R), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&acc)[ND]) {
+    const double2 nom = neg2(s.om), nal = neg2(s.al);
+    const double2 sn = fma2(s.be, fma2(nom, v[2], v[1]), v[0]);
+    const double2 zn = fma2(s.be, fma2(nom, v[4], v[2]), v[3]);
+    const double2 q = fma2(nal, sn, v[5]);
+    const double2 y = fma2(nal, zn, v[0]);
+    st2(V(V_S), i, sn);
+    st2(V(V_Z), i, zn);
+    st2(V(V_Q), i, q);
+    st2(V(V_Y), i, y);
+    dot_acc(acc[0], q, y);
+    dot_acc(acc[1], y, y);
+    dot_acc(acc[2], q, q);
+  }
+};
+template <>
+struct OpDef<OP7_L4> {  // x += alpha p^ + omega q^; r^ = q^ - omega (w^ - alpha z^)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 5;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_X), i); v[1] = ld2(V(V_P), i); v[2] = ld2(V(V_RT), i); v[3] = ld2(V(V_WH), i); v[4] = ld2(V(V_ZH), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 xn = fma2(s.om, v[2], fma2(s.al, v[1], v[0]));
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+    st2(V(V_RH), i, fma2(neg2(s.om), fma2(neg2(s.al), v[4], v[3]), v[2]));
+  }
+};
+template <>
+struct OpDef<OP7_L5> {  // r = q - omega y; w = y - omega (t - alpha v); (r0,r), (r0,z), (r0,w), (r0,s)
+  static constexpr int ND = 4, FIN = FIN_PG3_MERGED, CTL = CTL_END_ITER, NL = 7;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_Q), i); v[1] = ld2(V(V_Y), i); v[2] = ld2(V(V_T), i); v[3] = ld2(V(V_V), i);
+    v[4] = ld2(V(V_R0), i); v[5] = ld2(V(V_Z), i); v[6] = ld2(V(V_S), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&acc)[ND]) {
+    const double2 nom = neg2(s.om);
+    const double2 r = fma2(nom, v[1], v[0]);
+    const double2 w = fma2(nom, fma2(neg2(s.al), v[3], v[2]), v[1]);
+    st2(V(V_R), i, r);
+    st2(V(V_W), i, w);
+    dot_acc(acc[0], v[4], r);
+    dot_acc(acc[1], v[4], v[5]);
+    dot_acc(acc[2], v[4], w);
+    dot_acc(acc[3], v[4], v[6]);
+  }
+};
+template <> struct OpDef<OP7_PU_PH> : PUpd<V_P, V_RH, V_P, V_SH, true> {};
+template <> struct OpDef<OP7_PU_SH> : PUpd<V_SH, V_WH, V_SH, V_ZH, true> {};
+template <> struct OpDef<OP7_PU_QH> : PUpd<V_RT, V_RH, V_RH, V_SH, false> {};
+template <> struct OpDef<OP7_X> : XUpd<V_P, V_RT> {};
+template <> struct OpDef<OP7_TMPH> : PUpd<V_TMP, V_WH, V_WH, V_ZH, false> {};  // 4-vector op, first call
+template <> struct OpDef<OP7_RH> : OUpd<V_RH, V_RT, V_TMP> {};                 // second call
+
+// ---- Algorithm 3 (u in V_W, f_0 = A^T r_0 in V_RT); kernels use alpha_{j+1}, beta_{j+1},
+// delta_{j+1} and the coefficients cz = beta (alpha_{j+1}/alpha_j), cv = alpha_{j+1} delta_{j+1}
+template <>
+struct OpDef<OP3_SETUP> {  // r^_0 = r_0; q_0 = v_0 = z_0 = 0; (b,b), (r_0,r_0)
+  static constexpr int ND = 2, FIN = FIN_SETUP, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_B), i); v[1] = ld2(V(V_R), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &, double2 (&acc)[ND]) {
+    const double2 z = make_double2(0.0, 0.0);
+    st2(V(V_R0), i, v[1]);
+    st2(V(V_Q), i, z);
+    st2(V(V_V), i, z);
+    st2(V(V_Z), i, z);
+    dot_acc(acc[0], v[0], v[0]);
+    dot_acc(acc[1], v[1], v[1]);
+  }
+};
+template <> struct OpDef<OP3_SIG0> : DotOp<V_R0, V_W, FIN_I_START, CTL_START> {};  // sigma_0 = (r_0, u_0)
+template <>
+struct OpDef<OP3_L1> {  // z = alpha r + cz z - cv v; v = u + beta v - delta q; s = r - alpha v
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 5;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_R), i); v[1] = ld2(V(V_Z), i); v[2] = ld2(V(V_V), i); v[3] = ld2(V(V_W), i); v[4] = ld2(V(V_Q), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 ar = make_double2(s.al.x * v[0].x, s.al.y * v[0].y);
+    st2(V(V_Z), i, fma2(neg2(s.cv), v[2], fma2(s.cz, v[1], ar)));
+    const double2 vn = fma2(neg2(s.dl), v[4], fma2(s.be, v[2], v[3]));
+    st2(V(V_V), i, vn);
+    st2(V(V_S), i, fma2(neg2(s.al), vn, v[0]));
+  }
+};
+template <>
+struct OpDef<OP3_L2> {  // t = u - alpha q with the seven dot products
+  static constexpr int ND = 7, FIN = FIN_I7_MERGED, CTL = CTL_END_ITER, NL = 5;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_W), i); v[1] = ld2(V(V_Q), i); v[2] = ld2(V(V_R0), i); v[3] = ld2(V(V_S), i); v[4] = ld2(V(V_RT), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&acc)[ND]) {
+    const double2 t = fma2(neg2(s.al), v[1], v[0]);
+    st2(V(V_T), i, t);
+    dot_acc(acc[0], v[2], v[3]);
+    dot_acc(acc[1], v[2], v[1]);
+    dot_acc(acc[2], v[4], v[3]);
+    dot_acc(acc[3], v[4], t);
+    dot_acc(acc[4], v[3], t);
+    dot_acc(acc[5], t, t);
+    dot_acc(acc[6], v[3], v[3]);
+  }
+};
+template <>
+struct OpDef<OP3_L3> {  // r = s - omega t; x += z + omega s
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 4;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) {
+    v[0] = ld2(V(V_S), i); v[1] = ld2(V(V_T), i); v[2] = ld2(V(V_X), i); v[3] = ld2(V(V_Z), i);
+  }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_R), i, fma2(neg2(s.om), v[1], v[0]));
+    const double2 xz = make_double2(v[2].x + v[3].x, v[2].y + v[3].y);
+    const double2 xn = fma2(s.om, v[0], xz);
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[2]));
+  }
+};
+template <>
+struct OpDef<OP3_Z> {  // z = alpha r + cz z - cv v   (one extended-BLAS call)
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_R), i); v[1] = ld2(V(V_Z), i); v[2] = ld2(V(V_V), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 ar = make_double2(s.al.x * v[0].x, s.al.y * v[0].y);
+    st2(V(V_Z), i, fma2(neg2(s.cv), v[2], fma2(s.cz, v[1], ar)));
+  }
+};
+template <>
+struct OpDef<OP3_V> {  // v = u + beta v - delta q
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_W), i); v[1] = ld2(V(V_V), i); v[2] = ld2(V(V_Q), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    st2(V(V_V), i, fma2(neg2(s.dl), v[2], fma2(s.be, v[1], v[0])));
+  }
+};
+template <> struct OpDef<OP3_S> : PUpd<V_S, V_R, V_R, V_V, false> {};  // s = r - alpha v
+template <> struct OpDef<OP3_T> : PUpd<V_T, V_W, V_W, V_Q, false> {};  // t = u - alpha q
+template <> struct OpDef<OP3_D_R0S> : DotOp<V_R0, V_S, FIN_STORE_D0, CTL_NONE> {};
+template <> struct OpDef<OP3_D_R0Q> : DotOp<V_R0, V_Q, FIN_STORE_D1, CTL_NONE> {};
+template <> struct OpDef<OP3_D_F0S> : DotOp<V_RT, V_S, FIN_STORE_D2, CTL_NONE> {};
+template <> struct OpDef<OP3_D_F0T> : DotOp<V_RT, V_T, FIN_STORE_D3, CTL_NONE> {};
+template <> struct OpDef<OP3_D_ST> : DotOp<V_S, V_T, FIN_STORE_D4, CTL_NONE> {};
+template <> struct OpDef<OP3_D_TT> : DotOp<V_T, V_T, FIN_STORE_D5, CTL_NONE> {};
+template <> struct OpDef<OP3_D_SS> : DotOp<V_S, V_S, FIN_I7_PLAIN, CTL_END_ITER> {};
+template <>
+struct OpDef<OP3_X> {  // x += z + omega s
+  static constexpr int ND = 0, FIN = FIN_NONE, CTL = CTL_NONE, NL = 3;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_X), i); v[1] = ld2(V(V_Z), i); v[2] = ld2(V(V_S), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&)[1]) {
+    const double2 xz = make_double2(v[0].x + v[1].x, v[0].y + v[1].y);
+    const double2 xn = fma2(s.om, v[2], xz);
+    if (s.u0 | s.u1) st2(V(V_X), i, sel2(s.u0, s.u1, xn, v[0]));
+  }
+};
+
 // ---- mixed-precision refinement, FP32 inner solve (roles hold float arrays)
 struct Op32 {
   using V2 = float2;
@@ -816,13 +1147,14 @@ struct OpDef<OP_IR_UPDATE> {  // x += d for the columns this pass refines
 
 template <int ND>
 struct RedSmem {
-  double red[kVecThreads / 32][ND][kMaxKp];
+  double red[kVecThreads / 32][ND < 4 ? ND : 4][kMaxKp];  // warp partials, up to 4 dots at a time
   double sums[ND * kMaxKp];
   unsigned int ticket;
 };
 
 template <class D, int ND = D::ND>
 __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND : 1]) {
+  constexpr int NC = ND < 4 ? ND : 4;  // dots per shared-memory chunk
   __shared__ RedSmem<ND> sm;
   const int kp = a.kp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -846,25 +1178,32 @@ __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND :
       if (kp > 1) v1[d] += __shfl_xor_sync(0xffffffffu, v1[d], m);
     }
   }
-  if (kp == 1) {
-    if (lane == 0)
-#pragma unroll
-      for (int d = 0; d < ND; ++d) sm.red[warp][d][0] = v0[d];
-  } else if (lane < (kp >> 1)) {
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      sm.red[warp][d][2 * lane] = v0[d];
-      sm.red[warp][d][2 * lane + 1] = v1[d];
-    }
-  }
-  __syncthreads();
   const int nout = ND * kp;
   double *mypart = a.part + (size_t)blockIdx.x * (kMaxDots * kMaxKp);
-  for (int t = threadIdx.x; t < nout; t += blockDim.x) {
-    const int d = t / kp, c = t - d * kp;
-    double s = 0.0;
-    for (int w = 0; w < kVecThreads / 32; ++w) s += sm.red[w][d][c];
-    mypart[d * kMaxKp + c] = s;
+#pragma unroll
+  for (int d0 = 0; d0 < ND; d0 += NC) {
+    if (kp == 1) {
+      if (lane == 0)
+#pragma unroll
+        for (int d = 0; d < NC; ++d)
+          if (d0 + d < ND) sm.red[warp][d][0] = v0[d0 + d];
+    } else if (lane < (kp >> 1)) {
+#pragma unroll
+      for (int d = 0; d < NC; ++d)
+        if (d0 + d < ND) {
+          sm.red[warp][d][2 * lane] = v0[d0 + d];
+          sm.red[warp][d][2 * lane + 1] = v1[d0 + d];
+        }
+    }
+    __syncthreads();
+    const int nchunk = (ND - d0 < NC ? ND - d0 : NC) * kp;
+    for (int t = threadIdx.x; t < nchunk; t += blockDim.x) {
+      const int d = t / kp, c = t - d * kp;
+      double s = 0.0;
+      for (int w = 0; w < kVecThreads / 32; ++w) s += sm.red[w][d][c];
+      mypart[(d0 + d) * kMaxKp + c] = s;
+    }
+    __syncthreads();
   }
   // Fixed-order sum of the block partials; no block ever waits for another.  With few partial
   // sums (grid x outputs <= kOneLevelMax) the last block to arrive adds them all in block order.
@@ -942,6 +1281,9 @@ __global__ void __launch_bounds__(kVecThreads, 2) vec_kernel(const KArgs a) {
   s.al = make_double2(SC(S_ALPHA, c0), SC(S_ALPHA, c1));
   s.om = make_double2(SC(S_OMEGA, c0), SC(S_OMEGA, c1));
   s.be = make_double2(SC(S_BETA, c0), SC(S_BETA, c1));
+  s.cz = make_double2(SC(S_CZ, c0), SC(S_CZ, c1));
+  s.cv = make_double2(SC(S_CV, c0), SC(S_CV, c1));
+  s.dl = make_double2(SC(S_DLT, c0), SC(S_DLT, c1));
   s.alf = make_float2((float)s.al.x, (float)s.al.y);
   s.omf = make_float2((float)s.om.x, (float)s.om.y);
   s.bef = make_float2((float)s.be.x, (float)s.be.y);
@@ -1100,6 +1442,44 @@ const OpInfo kOps[OP_COUNT] = {
     OPI(OP_IR_SETUP, "ir_dot_b", 1, 0),
     OPI(OP_IR_RESID, "ir_resid_to_fp32", 1, 1),
     OPI(OP_IR_UPDATE, "ir_update_x", 2, 1),
+    OPI(OP_PREC_P_Q, "precond_p", 1, 1),
+    OPI(OP_PREC_S_Y, "precond_s", 1, 1),
+    OPI(OP_PREC_R_RH, "precond_r", 1, 1),
+    OPI(OP_PREC_W_WH, "precond_w", 1, 1),
+    OPI(OP_PREC_Z_ZH, "precond_z", 1, 1),
+    OPI(OP_PREC_R_Z, "precond_r_z", 1, 2),
+    OPI(OP_PREC_V_S, "precond_copy_s", 1, 1),
+    OPI(OP_PREC_T_Q, "precond_copy_q", 1, 1),
+    OPI(OP5_RRHO, "merged_r_rho", 3, 1),
+    OPI(OP5_UPD_X, "upd_x", 3, 1),
+    OPI(OP7_SETUP, "setup_ppipe", 2, 7),
+    OPI(OP7_L1, "merged_phat_shat_qhat", 5, 3),
+    OPI(OP7_L2, "merged_szqy_3dots", 6, 4),
+    OPI(OP7_L4, "merged_x_rhat", 5, 2),
+    OPI(OP7_L5, "merged_r_w_4dots", 7, 2),
+    OPI(OP7_PU_PH, "upd_phat", 3, 1),
+    OPI(OP7_PU_SH, "upd_shat", 3, 1),
+    OPI(OP7_PU_QH, "upd_qhat", 2, 1),
+    OPI(OP7_X, "upd_x", 3, 1),
+    OPI(OP7_TMPH, "upd_rhat_part1", 2, 1),
+    OPI(OP7_RH, "upd_rhat_part2", 2, 1),
+    OPI(OP3_SETUP, "setup_improved", 2, 4),
+    OPI(OP3_SIG0, "dot_sigma0", 2, 0),
+    OPI(OP3_L1, "merged_z_v_s", 5, 3),
+    OPI(OP3_L2, "merged_t_7dots", 5, 1),
+    OPI(OP3_L3, "merged_r_x", 4, 2),
+    OPI(OP3_Z, "upd_z", 3, 1),
+    OPI(OP3_V, "upd_v", 3, 1),
+    OPI(OP3_S, "upd_s", 2, 1),
+    OPI(OP3_T, "upd_t", 2, 1),
+    OPI(OP3_D_R0S, "dot_phi", 2, 0),
+    OPI(OP3_D_R0Q, "dot_pi", 2, 0),
+    OPI(OP3_D_F0S, "dot_gamma", 2, 0),
+    OPI(OP3_D_F0T, "dot_eta", 2, 0),
+    OPI(OP3_D_ST, "dot_theta", 2, 0),
+    OPI(OP3_D_TT, "dot_kappa", 1, 0),
+    OPI(OP3_D_SS, "dot_nu", 1, 0),
+    OPI(OP3_X, "upd_x", 3, 1),
 };
 #undef OPI
 
@@ -1172,6 +1552,25 @@ cudaError_t launch_pack_io(const BatchIO *io, int k, const KArgs &a, cudaStream_
 }
 cudaError_t launch_unpack_io(const BatchIO *io, int k, const KArgs &a, cudaStream_t s) {
   unpack_io_kernel<<<small_grid(a.n * k), 256, 0, s>>>(io, k, a);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void invdiag_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               const double *__restrict__ va, double *__restrict__ inv, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double d = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e)
+      if (ci[e] == i) d += va[e];
+    inv[i] = d == 0.0 ? 1.0 : 1.0 / d;
+  }
+}
+}  // namespace
+
+cudaError_t launch_invdiag(const int32_t *rowptr, const int32_t *colidx, const double *vals, double *invdiag,
+                           int64_t n, cudaStream_t s) {
+  invdiag_kernel<<<small_grid(n), 256, 0, s>>>(rowptr, colidx, vals, invdiag, n);
   return cudaGetLastError();
 }
 
