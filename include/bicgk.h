@@ -100,16 +100,33 @@ int bicgk_csr_create(bicgk_op *out, int64_t n_rows, int64_t nnz, const int32_t *
                      const int32_t *colidx, const double *vals, int mem, void *stream);
 
 /*
- * Y = A X for a block of k vectors (the SpMV of Algorithms 1-6 applied to k
+ * Y = A X for a block of k vectors (the SpMV of Algorithms 1-7 applied to k
  * row-interleaved vectors; the operation behind Sigma_mul, Sec. 3.1).
  *   X, Y: device arrays of n_rows*k FP64, RHS-interleaved (i*k + c); they must
- *   not overlap.  1 <= k <= BICGK_MAX_K.  Runs on `stream`, returns without
- *   synchronising.
+ *   not overlap.  1 <= k <= BICGK_MAX_K.  Any 8-byte alignment is accepted
+ *   (unaligned or non-power-of-two blocks go through the operator's workspace).
+ *   Runs on `stream`, returns without synchronising.
  */
 int bicgk_spmm(bicgk_op A, int32_t k, const double *X, double *Y, void *stream);
 
 /*
- * Solve A X = B for k right-hand sides (Algorithms 1, 2, 4 or 6, per `variant`).
+ * Y = A X in FP32: the product of the FP32 inner solves of bicgk_solve_mixed
+ * (the SpMV of Sec. 3.1 with the values rounded once to FP32), for callers that
+ * keep FP32 blocks.
+ *   X, Y: device arrays of n_rows*k FP32, RHS-interleaved (i*k + c); they must
+ *   not overlap; 4-byte alignment suffices.  1 <= k <= BICGK_MAX_K.
+ *   y_ic = sum over the entries of row i, in CSR order, of fl32(a_ij) x_jc,
+ *   accumulated in FP32 with fused multiply-adds.
+ * The FP32 copy of the values is made on the first FP32 use and kept with the
+ * operator.  Errors: BICGK_E_INVALID (null or equal pointers, k < 1),
+ * BICGK_E_UNSUPPORTED (k > BICGK_MAX_K), BICGK_E_NOMEM, BICGK_E_CUDA.  Runs on
+ * `stream`, returns without synchronising.
+ */
+int bicgk_spmm_f32(bicgk_op A, int32_t k, const float *X, float *Y, void *stream);
+
+/*
+ * Solve A X = B for k right-hand sides with one of the twelve forms of
+ * bicgk_variant (Algorithms 1-7, basic and merged).
  *   B      : n_rows*k FP64, RHS-interleaved, in space `mem`.
  *   X0     : initial guess in the same layout and space, or NULL for zero.
  *   X      : n_rows*k FP64 output in the same layout and space (may alias X0).

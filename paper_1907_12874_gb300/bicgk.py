@@ -58,6 +58,7 @@ def _load():
             vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
             lib.bicgk_csr_create.argtypes = [ctypes.POINTER(vp), i64, i64, vp, vp, vp, ctypes.c_int, vp]
             lib.bicgk_spmm.argtypes = [vp, i32, vp, vp, vp]
+            lib.bicgk_spmm_f32.argtypes = [vp, i32, vp, vp, vp]
             lib.bicgk_solve.argtypes = [vp, i32, vp, vp, dbl, i32, ctypes.c_int, i32, ctypes.c_int, vp, vp, vp, vp,
                                         vp, vp]
             lib.bicgk_op_destroy.argtypes = [vp]
@@ -87,7 +88,7 @@ def _load():
             lib.bicgk_kernel_times.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_char_p),
                                                ctypes.POINTER(i64), ctypes.POINTER(dbl)]
             lib.bicgk_last_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]
-            for f in ("bicgk_csr_create", "bicgk_spmm", "bicgk_solve", "bicgk_solve_mixed", "bicgk_op_destroy",
+            for f in ("bicgk_csr_create", "bicgk_spmm", "bicgk_spmm_f32", "bicgk_solve", "bicgk_solve_mixed", "bicgk_op_destroy",
                       "bicgk_set_profiling",
                       "bicgk_set_option",
                       "bicgk_kernel_times", "bicgk_last_stats"):
@@ -161,6 +162,15 @@ def spmm(handle: int, X, Y, stream=None) -> None:
     """Y = A X for torch CUDA tensors of shape (N, k), float64, contiguous."""
     k = 1 if X.dim() == 1 else X.shape[1]
     _check(_load().bicgk_spmm(ctypes.c_void_p(handle), k, _ptr(X), _ptr(Y), _stream(stream)), "bicgk_spmm")
+
+
+def spmm_f32(handle: int, X, Y, stream=None) -> None:
+    """Y = A X in FP32 (values rounded once to FP32) for torch CUDA tensors of shape (N, k), float32."""
+    if X.dtype != Y.dtype or str(X.dtype) != "torch.float32":
+        raise TypeError("spmm_f32 takes float32 tensors")
+    k = 1 if X.dim() == 1 else X.shape[1]
+    _check(_load().bicgk_spmm_f32(ctypes.c_void_p(handle), k, _ptr(X), _ptr(Y), _stream(stream)),
+           "bicgk_spmm_f32")
 
 
 @dataclass
@@ -335,6 +345,13 @@ class Operator:
             import torch
             Y = torch.empty_like(X)
         spmm(self.handle, X, Y, stream)
+        return Y
+
+    def spmm_f32(self, X, Y=None, stream=None):
+        if Y is None:
+            import torch
+            Y = torch.empty_like(X)
+        spmm_f32(self.handle, X, Y, stream)
         return Y
 
     def close(self):

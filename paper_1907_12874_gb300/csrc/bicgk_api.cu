@@ -11,6 +11,7 @@
 //      returns to the host;
 //   3. unpack X and copy the per-column results to the host.
 // The graph of each (variant, kp) is captured once per operator and reused.
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -246,6 +247,8 @@ KArgs make_args(bicgk_op A, const Workspace &W, int use_cond, cudaGraphCondition
   a.cond = h;
   return a;
 }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int vec_grid(bicgk_op A, int op) {
   if (A->grid_vec_abs > 0) return A->grid_vec_abs;
@@ -636,7 +639,9 @@ int bicgk_spmm(bicgk_op A, int32_t k, const double *X, double *Y, void *stream) 
   sa.b = nullptr;
   sa.n = A->n;
   sa.stage_cap = kp <= 2 ? A->stage_cap : 0;
-  if (kp == k) {  // caller layout is the kernel layout
+  // the caller's layout is the kernel layout when k is a power of two; the kernels read and
+  // write kp >= 2 blocks as 16-byte vectors, so the caller's arrays must then be 16-byte aligned
+  if (kp == k && (kp == 1 || (aligned16(X) && aligned16(Y)))) {
     sa.x = X;
     sa.y = Y;
     CK(launch_spmm(kp, 0, sa, spmm_grid(A, kp, 0), s));
@@ -651,6 +656,47 @@ int bicgk_spmm(bicgk_op A, int32_t k, const double *X, double *Y, void *stream) 
   sa.y = a.v[V_TMP];
   CK(launch_spmm(kp, 0, sa, spmm_grid(A, kp, 0), s));
   CK(launch_unpack_role(Y, k, k, a, V_TMP, 0, s));
+  return BICGK_OK;
+}
+
+int bicgk_spmm_f32(bicgk_op A, int32_t k, const float *X, float *Y, void *stream) {
+  if (!A || !X || !Y || k < 1 || (const void *)X == (const void *)Y) return BICGK_E_INVALID;
+  if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int kp = pow2_at_least(k);
+  if (!A->d_val32) {
+    CK(cudaMalloc(&A->d_val32, sizeof(float) * A->nnz + 16));
+    CK(launch_to_float(A->d_val, A->d_val32, A->nnz, s));
+  }
+  SpmmArgs sa;
+  sa.rowptr = A->d_rowptr;
+  sa.colidx = A->d_col;
+  sa.vals = A->d_val32;
+  sa.b = nullptr;
+  sa.n = A->n;
+  sa.stage_cap = kp <= 2 ? A->stage_cap : 0;
+  sa.cols_per_lane = 2;
+  const int grid = A->nsm * spmm32_blocks_per_sm(kp, sa.stage_cap);
+  if (kp == k && (kp == 1 || (aligned16(X) && aligned16(Y)))) {
+    sa.x = X;
+    sa.y = Y;
+    CK(launch_spmm32(kp, sa, grid, s));
+    return BICGK_OK;
+  }
+  // pad to kp columns (zeros) in the FP32 workspace with pitched copies, multiply, copy back
+  Workspace &V = A->ws32;
+  V.ebytes = 4;
+  int rc = ensure_workspace(A, V, kp);
+  if (rc) return rc;
+  float *xb = reinterpret_cast<float *>(V.d_vec + (int64_t)V_B * V.vstride);
+  float *yb = reinterpret_cast<float *>(V.d_vec + (int64_t)V_TMP * V.vstride);
+  const size_t w = sizeof(float) * (size_t)k, wp = sizeof(float) * (size_t)kp;
+  if (kp != k) CK(cudaMemsetAsync(xb, 0, wp * (size_t)A->n, s));
+  CK(cudaMemcpy2DAsync(xb, wp, X, w, w, (size_t)A->n, cudaMemcpyDeviceToDevice, s));
+  sa.x = xb;
+  sa.y = yb;
+  CK(launch_spmm32(kp, sa, grid, s));
+  CK(cudaMemcpy2DAsync(Y, w, yb, wp, w, (size_t)A->n, cudaMemcpyDeviceToDevice, s));
   return BICGK_OK;
 }
 
@@ -1412,7 +1458,7 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
     g_cuda_err = "bicgk_solve_noalloc: needs an sm_103 device with index < 64";
     return BICGK_E_UNSUPPORTED;
   }
-  // scratch layout: 14 vectors | scalars | flags | block partials | control block | history
+  // scratch layout: V_NVEC (18) vectors | scalars | flags | block partials | control block | history
   const int kp = pow2_at_least(k);
   const int64_t vstride = (n_rows * kp + 2 + 31) / 32 * 32;
   const int64_t hist_len = (int64_t)(maxit + 1) * kp;

@@ -21,6 +21,8 @@
 //            memory with coalesced loads, so the lanes' strided reads of their
 //            own rows hit shared memory instead of scattering over L1.  A tile
 //            with more entries than the stage buffer reads them from global.
+#include <type_traits>
+
 #include "bicgk_dev.cuh"
 
 namespace bicgk {
@@ -194,9 +196,82 @@ __global__ void __launch_bounds__(kSpmmThreads) spmm_row_kernel(const SpmmArgs a
   }
 }
 
+// FP32, kp >= 8 (the inner solves of the mixed-precision refinement).  The FP32 product is
+// bound by the L1 data path, not by FMAs: in the group kernel every lane of a row re-reads the
+// row's column index and value for each nonzero as a broadcast load, which costs the L1 about
+// as much as the x row itself.  Here a row is owned by L = kp/4 lanes with 4 columns each (one
+// 16-byte load of the x row per nonzero); the row's CSR entries are read C at a time with one
+// coalesced load per lane and passed to the row's lanes by shuffles, so the L1 carries the x
+// rows and one load per lane per chunk.  The gathers of a chunk (up to 8 in flight) are issued
+// before its FMAs; the FMAs run in entry order, so every sum is the one of the entry-by-entry
+// loop.
+template <int KP>
+__global__ void __launch_bounds__(kSpmmThreads) spmm32_seg_kernel(const SpmmArgs a) {
+  static_assert(KP >= 8 && KP <= 64, "segment kernel: 8 <= kp <= 64");
+  constexpr int L = KP / 4;           // lanes per row
+  constexpr int C = L > 8 ? L : 8;    // CSR entries per chunk
+  constexpr int M = C / L;            // entries each lane loads per chunk
+  constexpr int G = 8;                // gathers in flight
+  constexpr int RPP = kSpmmThreads / L;
+  const int lane = threadIdx.x & 31;
+  const int g = threadIdx.x / L, cl = threadIdx.x % L;
+  const unsigned segmask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (lane & ~(L - 1)));
+  const int32_t *__restrict__ rp = a.rowptr;
+  const int32_t *__restrict__ ci = a.colidx;
+  const float *__restrict__ va = static_cast<const float *>(a.vals);
+  const float4 *__restrict__ x4 = static_cast<const float4 *>(a.x);
+  float4 *__restrict__ y4 = static_cast<float4 *>(a.y);
+  const int64_t stride = (int64_t)gridDim.x * RPP;
+  for (int64_t r = (int64_t)blockIdx.x * RPP + g; r < a.n; r += stride) {
+    const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int base = e0; base < e1; base += C) {
+      const int cnt = (e1 - base < C) ? e1 - base : C;
+      // entry q of the chunk is held by lane q % L in slot q / L
+      int jj[M];
+      float aa[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int q = m * L + cl;
+        jj[m] = 0;
+        aa[m] = 0.f;
+        if (q < cnt) {
+          jj[m] = __ldg(ci + base + q);
+          aa[m] = __ldg(va + base + q);
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < C; h += G) {
+        float4 u[G];
+        float av[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+          const int q = h + t;
+          const int j = __shfl_sync(segmask, jj[q / L], q % L, L);
+          av[t] = __shfl_sync(segmask, aa[q / L], q % L, L);
+          u[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (q < cnt) u[t] = __ldg(x4 + (int64_t)j * (KP / 4) + cl);
+        }
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+          if (h + t < cnt) {
+            acc.x = fmaf(av[t], u[t].x, acc.x);
+            acc.y = fmaf(av[t], u[t].y, acc.y);
+            acc.z = fmaf(av[t], u[t].z, acc.z);
+            acc.w = fmaf(av[t], u[t].w, acc.w);
+          }
+        }
+      }
+    }
+    y4[r * (KP / 4) + cl] = acc;
+  }
+}
+
 template <typename T, int KP, int MODE>
 cudaError_t launch_kp(const SpmmArgs &a, int grid, cudaStream_t s) {
-  if constexpr (KP <= 2) {
+  if constexpr (std::is_same<T, float>::value && MODE == 0 && KP >= 8) {
+    spmm32_seg_kernel<KP><<<grid, kSpmmThreads, 0, s>>>(a);
+  } else if constexpr (KP <= 2) {
     const size_t smem = (size_t)a.stage_cap * (sizeof(T) + sizeof(int32_t));
     spmm_row_kernel<T, KP, MODE><<<grid, kSpmmThreads, smem, s>>>(a);
   } else if constexpr (KP >= 8) {
@@ -214,7 +289,9 @@ template <typename T, int KP, int MODE>
 int occ_kp(int stage_cap) {
   int nb = 0;
   cudaError_t e;
-  if constexpr (KP <= 2)
+  if constexpr (std::is_same<T, float>::value && MODE == 0 && KP >= 8)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm32_seg_kernel<KP>, kSpmmThreads, 0);
+  else if constexpr (KP <= 2)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_row_kernel<T, KP, MODE>, kSpmmThreads,
                                                       (size_t)stage_cap * (sizeof(T) + sizeof(int32_t)));
   else

@@ -97,6 +97,57 @@ def test_spmm_matches_oracle(bk, cuda, k, kind):
     assert np.all(np.abs(Y - Yo) <= bound + 1e-300)
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("kind", ["convdiff7", "random", "perturbed27"])
+def test_spmm_f32_matches_oracle(bk, cuda, k, kind):
+    """FP32 product of the mixed-precision inner solves: y = fl32(A) x summed in FP32 with FMAs in
+    CSR order.  Reference: the FP64 oracle on the FP32-rounded values and inputs (exact to far
+    below FP32 rounding); bound: recursive FP32 summation, len * 2^-24 * (|A||x|) per entry.  The
+    random matrix has empty rows and a 3000-entry row (many chunks, a ragged last chunk)."""
+    torch = cuda
+    A = {"convdiff7": lambda: I.convdiff7(13), "random": lambda: _random_csr(3001, 7),
+         "perturbed27": lambda: I.perturbed27(9, seed=2)}[kind]()
+    A32 = I.CSR(A.rowptr, A.colidx, A.vals.astype(np.float32).astype(np.float64))
+    X32 = I.rhs(A.n, k, 11).astype(np.float32)
+    Yo = oracle.spmm(A32, X32.astype(np.float64))
+    with bk.Operator(A) as op:
+        Y = op.spmm_f32(torch.from_numpy(X32).cuda()).cpu().numpy().astype(np.float64)
+    absA = I.CSR(A.rowptr, A.colidx, np.abs(A32.vals))
+    lens = np.maximum(1, np.diff(A.rowptr))[:, None]
+    bound = oracle.spmm(absA, np.abs(X32).astype(np.float64)) * (1.01 * 2.0 ** -24) * lens
+    assert np.all(np.abs(Y - Yo) <= bound + 1e-300)
+
+
+@pytest.mark.parametrize("k", [2, 4, 8, 32])
+def test_spmm_unaligned_caller_arrays(bk, cuda, k):
+    """Caller blocks that start 8 bytes (FP64) or 4 bytes (FP32) past a 16-byte boundary go
+    through the operator's workspace; the result is bitwise the aligned call's."""
+    torch = cuda
+    A = I.convdiff7(11)
+    X = I.rhs(A.n, k, 3)
+    with bk.Operator(A) as op:
+        Xa = torch.from_numpy(X).cuda()
+        Ya = op.spmm(Xa)
+        buf_x = torch.zeros(A.n * k + 1, dtype=torch.float64, device="cuda")
+        buf_y = torch.zeros(A.n * k + 1, dtype=torch.float64, device="cuda")
+        Xu = buf_x[1:].view(A.n, k)
+        Xu.copy_(Xa)
+        Yu = buf_y[1:].view(A.n, k)
+        assert Xu.data_ptr() % 16 == 8 and Yu.data_ptr() % 16 == 8
+        op.spmm(Xu, Yu)
+        assert torch.equal(Ya, Yu)
+        X32 = Xa.float()
+        Ya32 = op.spmm_f32(X32)
+        b32x = torch.zeros(A.n * k + 1, dtype=torch.float32, device="cuda")
+        b32y = torch.zeros(A.n * k + 1, dtype=torch.float32, device="cuda")
+        Xu32 = b32x[1:].view(A.n, k)
+        Xu32.copy_(X32)
+        Yu32 = b32y[1:].view(A.n, k)
+        assert Xu32.data_ptr() % 16 == 4
+        op.spmm_f32(Xu32, Yu32)
+        assert torch.equal(Ya32, Yu32)
+
+
 def _compare_chaotic(r, X, ro, A, B, tol):
     """Nearly symmetric operators: compare with the unique exact solution (see module doc)."""
     import scipy.sparse.linalg as sla
