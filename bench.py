@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--sweep", action="store_true", help="also time every variant at k = 1..32")
+    p.add_argument("--replica", action="store_true",
+                   help="also run the paper's iteration benchmark: Poisson 200^3, m = 1, 4, 16, every form")
+    p.add_argument("--replica-iters", type=int, default=100)
     p.add_argument("--no-mixed", action="store_true",
                    help="skip the mixed-precision comparison (27-point 128^3, k = 32, rel tol 1e-10)")
     p.add_argument("--mixed-grid", type=int, default=128)
@@ -355,6 +358,96 @@ def batch_section(args, bicgk, inputs, torch, dev, nsys=64):
     return res
 
 
+# Table 4 of the paper (Lomonosov-2, one node of 14 Xeon cores, FP64): seconds per iteration of the
+# 7-point Poisson problem on a 200^3 grid, basic and merged forms, m = 1, 4, 16 right-hand sides.
+PAPER_TABLE4 = {
+    "classical": {1: (0.062, 0.058), 4: (0.181, 0.164), 16: (0.65, 0.59)},
+    "improved": {1: (0.074, 0.061), 4: (0.236, 0.182), 16: (0.87, 0.66)},
+    "pipelined": {1: (0.087, 0.069), 4: (0.282, 0.212), 16: (1.06, 0.78)},
+    "precond": {1: (0.066, 0.064), 4: (0.201, 0.189), 16: (0.72, 0.68)},
+    "reordered": {1: (0.072, 0.065), 4: (0.224, 0.196), 16: (0.81, 0.70)},
+    "ppipe": {1: (0.107, 0.085), 4: (0.368, 0.279), 16: (1.39, 1.03)},
+}
+# vector reads + writes per iteration (Table 2) and M^-1 copies (one read + one write each)
+TABLE2_VECTORS = {"classical": (22, 18), "improved": (33, 20), "pipelined": (43, 26), "precond": (22, 19),
+                  "reordered": (28, 21), "ppipe": (56, 34)}
+TABLE2_COPIES = {"classical": 0, "improved": 0, "pipelined": 0, "precond": 2, "reordered": 2, "ppipe": 2}
+
+
+def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
+    """Every form at k = 1, 2, 4, 8, 16, 32 on the benchmark operator: fixed-iteration timing (graph
+    mode, CUDA events), RHS-iterations/s = k / time per iteration, and the achieved fraction of the
+    HBM copy bandwidth for the algorithmic bytes of one iteration: two products of
+    12 nnz + 4 (N + 1) + 16 N k bytes (x read once) and 8 N k bytes per vector pass of Table 2
+    (M^-1 copies as one read and one write each)."""
+    N, nnz = A.n, A.nnz
+    res = {"workload": f"{args.grid}^3 benchmark operator, {nit} fixed iterations per form and k",
+           "hbm_gbs": hbm_gbs, "rows": {}}
+    with bicgk.Operator(A) as opw:
+        for k in (1, 2, 4, 8, 16, 32):
+            Bk = torch.from_numpy(inputs.rhs(N, k, 2)).to(dev)
+            Xk = torch.empty_like(Bk)
+            for v in bicgk.VARIANTS:
+                base, form = v.rsplit("_", 1)
+                opw.solve(Bk, X=Xk, tol=0.0, maxit=3, variant=v, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                opw.solve(Bk, X=Xk, tol=0.0, maxit=nit, variant=v, flags=bicgk.FLAG_NO_STOP_TEST,
+                          want_hist=False, want_true=False)
+                e1.record()
+                torch.cuda.synchronize()
+                s_it = e0.elapsed_time(e1) / 1e3 / nit
+                vecs = TABLE2_VECTORS[base][0 if form == "plain" else 1] + 2 * TABLE2_COPIES[base]
+                byts = 2 * (12 * nnz + 4 * (N + 1) + 16 * N * k) + vecs * 8 * N * k
+                res["rows"][f"{v}/k{k}"] = {"rhs_iterations_per_s": k / s_it, "ms_per_iter": s_it * 1e3,
+                                            "algorithmic_gb_per_iter": byts / 1e9,
+                                            "hbm_frac": byts / s_it / (hbm_gbs * 1e9)}
+    return res
+
+
+def replica_section(args, bicgk, inputs, torch, dev, hbm_gbs):
+    """The paper's iteration benchmark on the GPU (Sec. 2.3, Tables 3-4): 7-point Poisson on a
+    200^3 grid (8,000,000 rows), m = 1, 4, 16 right-hand sides U[-1,1], fixed iteration count, every
+    form basic and merged.  Per iteration: measured time (graph mode, CUDA events), the paper's
+    data-transfer model T = Sigma / B (Eq. SpMV_mem for the two products, 8 N m bytes per vector
+    pass, B = the measured HBM copy bandwidth), and the paper's own Lomonosov-2 times."""
+    n = 200
+    A = inputs.convdiff7(n, beta=(0.0, 0.0, 0.0))
+    N, C = A.n, A.nnz / A.n
+    nit = args.replica_iters
+    res = {"workload": f"7-point Poisson {n}^3 ({N} rows, {A.nnz} nnz), x0 = 0, B U[-1,1] seed 5, "
+                       f"{nit} fixed iterations per timing (the paper uses 1000; the time per iteration "
+                       f"is steady)", "hbm_gbs": hbm_gbs, "rows": {}}
+    with bicgk.Operator(A) as op:
+        for m in (1, 4, 16):
+            B = torch.from_numpy(inputs.rhs(N, m, 5)).to(dev)
+            X = torch.empty_like(B)
+            sig_mul = N * (8 * m * (C + 1) + 4 * (3 * C + 1))
+            for base in PAPER_TABLE4:
+                row = {}
+                for form in ("plain", "merged"):
+                    v = f"{base}_{form}"
+                    op.solve(B, X=X, tol=0.0, maxit=3, variant=v, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    r = op.solve(B, X=X, tol=0.0, maxit=nit, variant=v, flags=bicgk.FLAG_NO_STOP_TEST,
+                                 want_hist=False, want_true=False)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / nit
+                    vecs = TABLE2_VECTORS[base][0 if form == "plain" else 1] + 2 * TABLE2_COPIES[base]
+                    model_ms = (2 * sig_mul + vecs * 8 * N * m) / (hbm_gbs * 1e9) * 1e3
+                    row[form] = {"ms_per_iter": ms, "model_ms": model_ms,
+                                 "all_columns_ran": bool((r.status == 1).all() and (r.iters == nit).all())}
+                p_basic, p_merged = PAPER_TABLE4[base][m]
+                row["merged_gain"] = row["plain"]["ms_per_iter"] / row["merged"]["ms_per_iter"] - 1
+                row["paper_lomonosov2_s"] = {"basic": p_basic, "merged": p_merged, "gain": p_basic / p_merged - 1}
+                res["rows"][f"{base}/m{m}"] = row
+    return res
+
+
 def adjoint_section(args, bicgk, inputs, torch, dev):
     """64^3 convection-diffusion, 8 RHS, loss = sum(w * X): forward + backward wall time (CUDA events).
 
@@ -539,14 +632,11 @@ def main():
                             sorted(times.items(), key=lambda kv: -kv[1][1])}
 
     if args.sweep and rank == 0:
-        sweep = {}
-        for k in (1, 2, 4, 8, 16, 32):
-            Bk = torch.from_numpy(inputs.rhs(A.n, k, 2)).to(dev)
-            Xk = torch.empty_like(Bk)
-            for v in bicgk.VARIANTS:
-                msk, itsk, _, _, _ = timed(v, 2, 1, B=Bk, X=Xk)
-                sweep[f"{v}/k{k}"] = itsk / (msk / 1e3)
-        out["sweep_rhs_iterations_per_s"] = sweep
+        out["sweep"] = sweep_section(args, bicgk, inputs, torch, dev, A, hbm_peak()[0])
+
+    # the paper's own iteration benchmark (Poisson 200^3, every form, m = 1, 4, 16)
+    if args.replica and rank == 0:
+        out["paper_replica"] = replica_section(args, bicgk, inputs, torch, dev, hbm_peak()[0])
 
     # mixed precision (FP32 inner solves in FP64 refinement) vs FP64 on the same GPU
     if not args.no_mixed and rank == 0:
@@ -569,6 +659,13 @@ def main():
                                "kind": "oracle",
                                "sample": f"{cols} of the {args.k} columns x {iters} fixed iterations "
                                          f"({secs:.1f} s of CPU time)"}
+        # the same oracle on one core (the paper's runs use one MPI rank per core)
+        all_threads = oracle.threads()
+        oracle.set_threads(1)
+        rate1, secs1 = cpu_oracle_rate(A, B_host, args.variant, 1, 4)
+        oracle.set_threads(all_threads)
+        out["cpu_baseline"]["one_core"] = {"value": rate1, "cores": 1,
+                                           "sample": f"1 column x 4 fixed iterations ({secs1:.1f} s)"}
     op.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

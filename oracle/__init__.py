@@ -71,6 +71,8 @@ def _load():
             lib.oracle_spmm.argtypes = [i64, vp, vp, vp, i32, vp, vp]
             lib.oracle_spmm.restype = ctypes.c_int
             lib.oracle_threads.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = None
             lib.oracle_solve_mixed.argtypes = [i64, vp, vp, vp, i32, vp, vp, dbl, i32, dbl, i32, vp, vp, vp, vp, vp,
                                                vp]
             lib.oracle_solve_mixed.restype = ctypes.c_int
@@ -84,6 +86,11 @@ def _ptr(a):
 
 def threads() -> int:
     return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Run the following oracle calls on n OpenMP threads (timing on one core and on all)."""
+    _load().oracle_set_threads(int(n))
 
 
 def spmm(A, X: np.ndarray) -> np.ndarray:

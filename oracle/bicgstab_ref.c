@@ -1146,9 +1146,14 @@ int oracle_solve_mixed(int64_t n, const int32_t *rowptr, const int32_t *colidx, 
 }
 
 /* Threads the OpenMP runtime will use for the parallel loops (1 without OpenMP). */
+/* Thread count for the following calls (timing the oracle on one core and on all of them). */
 #ifdef _OPENMP
 #include <omp.h>
 int oracle_threads(void) { return omp_get_max_threads(); }
+void oracle_set_threads(int n) {
+  if (n > 0) omp_set_num_threads(n);
+}
 #else
 int oracle_threads(void) { return 1; }
+void oracle_set_threads(int n) { (void)n; }
 #endif

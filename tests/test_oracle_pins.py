@@ -198,6 +198,25 @@ def test_columns_are_independent_bitwise():
             assert np.array_equal(rk.hist[:, c], r1.hist[:, 0], equal_nan=True)
 
 
+def test_thread_count_does_not_change_results():
+    """Only row-parallel loops are threaded (every row's result is computed by one thread in a
+    fixed order) and the dot products are serial, so one thread and all threads agree bitwise."""
+    A = I.perturbed27(9, seed=4)
+    B = I.rhs(A.n, 3, 6)
+    n_all = oracle.threads()
+    try:
+        oracle.set_threads(1)
+        assert oracle.threads() == 1
+        r1 = {v: oracle.solve(A, B, tol=1e-10, maxit=300, variant=v) for v in ("classical_merged", "ppipe_plain")}
+        y1 = oracle.spmm(A, B)
+    finally:
+        oracle.set_threads(n_all)
+    for v, r in r1.items():
+        rn = oracle.solve(A, B, tol=1e-10, maxit=300, variant=v)
+        assert np.array_equal(r.X, rn.X) and np.array_equal(r.iters, rn.iters)
+    assert np.array_equal(y1, oracle.spmm(A, B))
+
+
 def test_stop_is_first_crossing():
     """iters is the first j with (estimate of ||r_j||) < tol * ||b||."""
     A = I.convdiff7(10)
