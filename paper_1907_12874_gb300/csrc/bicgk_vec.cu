@@ -443,7 +443,7 @@ __device__ void fin_ctl(const KArgs &a) {
     int any = 0;
     for (int c = 0; c < a.kp; ++c) any |= FL(F_ACT, c);
     ctl->any_active = any;
-    int go;
+    int go = 0;
     if constexpr (CTL == CTL_OUTER) {
       ctl->iter += 1;  // refinement passes: the host drives this loop
       return;
@@ -1216,7 +1216,8 @@ __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND :
   const bool two_level = nblk * nout > kOneLevelMax;
   const int ngrp = two_level ? (nblk + kRedGroup - 1) / kRedGroup : 1;
   const double *top = a.part;  // partials the final block adds: block partials or group partials
-  __threadfence();
+  // the threads that wrote partials make them visible before thread 0 takes the ticket
+  if ((int)threadIdx.x < NC * kp) __threadfence();
   __syncthreads();
   if (two_level) {
     const int g = blockIdx.x / kRedGroup;
@@ -1236,7 +1237,7 @@ __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND :
       gpart[d * kMaxKp + c] = s;
     }
     if (threadIdx.x == 0) a.ctl->gticket[g] = 0;
-    __threadfence();
+    if ((int)threadIdx.x < nout) __threadfence();
     __syncthreads();
     top = a.part + (size_t)nblk * kStride;
   }
