@@ -1269,8 +1269,33 @@ __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND :
   }
 }
 
+// Blocks of 512 threads per SM a streaming kernel is compiled for.  Two (at most 64 registers)
+// suit most ops.  The fused groups of the Pipelined forms and of Algorithm 3 hold many vectors
+// per chunk and spilled at 64 registers; compiled for one block of up to 128 registers they run
+// 3-8 % faster at k <= 8 and the same at k = 32 (measured).  Group 3 of Algorithm 2 and the last
+// group of Algorithm 6 spill too but are as fast or faster at two blocks when the two column
+// groups of a solve run concurrently, so they keep two.
 template <int OP>
-__global__ void __launch_bounds__(kVecThreads, 2) vec_kernel(const KArgs a) {
+struct VecMinBlocks {
+  static constexpr int value = 2;
+};
+#define BICGK_ONE_BLOCK(op) \
+  template <>               \
+  struct VecMinBlocks<op> { \
+    static constexpr int value = 1; \
+  };
+BICGK_ONE_BLOCK(OP_PG1)
+BICGK_ONE_BLOCK(OP_PG3)
+BICGK_ONE_BLOCK(OP7_L1)
+BICGK_ONE_BLOCK(OP7_L2)
+BICGK_ONE_BLOCK(OP7_L4)
+BICGK_ONE_BLOCK(OP7_L5)
+BICGK_ONE_BLOCK(OP3_L1)
+BICGK_ONE_BLOCK(OP3_L2)
+#undef BICGK_ONE_BLOCK
+
+template <int OP>
+__global__ void __launch_bounds__(kVecThreads, VecMinBlocks<OP>::value) vec_kernel(const KArgs a) {
   using D = OpDef<OP>;
   constexpr int ND = D::ND;
   const int kp = a.kp;
