@@ -379,7 +379,8 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
     mode, CUDA events), RHS-iterations/s = k / time per iteration, and the achieved fraction of the
     HBM copy bandwidth for the algorithmic bytes of one iteration: two products of
     12 nnz + 4 (N + 1) + 16 N k bytes (x read once) and 8 N k bytes per vector pass of Table 2
-    (M^-1 copies as one read and one write each)."""
+    (M^-1 copies as one read and one write each).  paper_model_ms is the paper's data-transfer
+    model T = Sigma / B (Eq. SpMV_mem, x read C + 1 times) with B the measured HBM bandwidth."""
     N, nnz = A.n, A.nnz
     res = {"workload": f"{args.grid}^3 benchmark operator, {nit} fixed iterations per form and k",
            "hbm_gbs": hbm_gbs, "rows": {}}
@@ -400,9 +401,12 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
                 s_it = e0.elapsed_time(e1) / 1e3 / nit
                 vecs = TABLE2_VECTORS[base][0 if form == "plain" else 1] + 2 * TABLE2_COPIES[base]
                 byts = 2 * (12 * nnz + 4 * (N + 1) + 16 * N * k) + vecs * 8 * N * k
+                C = nnz / N
+                model = (2 * N * (8 * k * (C + 1) + 4 * (3 * C + 1)) + vecs * 8 * N * k) / (hbm_gbs * 1e9)
                 res["rows"][f"{v}/k{k}"] = {"rhs_iterations_per_s": k / s_it, "ms_per_iter": s_it * 1e3,
                                             "algorithmic_gb_per_iter": byts / 1e9,
-                                            "hbm_frac": byts / s_it / (hbm_gbs * 1e9)}
+                                            "hbm_frac": byts / s_it / (hbm_gbs * 1e9),
+                                            "paper_model_ms": model * 1e3}
     return res
 
 
@@ -659,6 +663,12 @@ def main():
                                "kind": "oracle",
                                "sample": f"{cols} of the {args.k} columns x {iters} fixed iterations "
                                          f"({secs:.1f} s of CPU time)"}
+        # the oracle's basic form of the same method (one loop per vector operation), all cores
+        plain_v = args.variant.replace("_merged", "_plain")
+        if plain_v != args.variant:
+            ratep, secsp = cpu_oracle_rate(A, B_host, plain_v, cols, iters)
+            out["cpu_baseline"]["basic_form"] = {"variant": plain_v, "value": ratep, "cores": oracle.threads(),
+                                                 "sample": f"{cols} columns x {iters} fixed iterations ({secsp:.1f} s)"}
         # the same oracle on one core (the paper's runs use one MPI rank per core)
         all_threads = oracle.threads()
         oracle.set_threads(1)

@@ -84,3 +84,22 @@ def test_full_size_solve(bk, cuda, system):
     assert np.all(ro.status == 0)
     spread = np.maximum(2, 0.15 * ro.iters)
     assert np.all(np.abs(r.iters[SAMPLE] - ro.iters) <= spread), (r.iters[SAMPLE], ro.iters)
+
+
+@pytest.mark.parametrize("k", [1, 4])
+def test_full_size_solve_small_k(bk, cuda, system, k):
+    """k = 1 and k = 4 at full size (the one-lane-per-row SpMM and the group SpMM at kp = 4): every
+    column converged, true residuals recomputed by the oracle below the tolerance, iteration counts
+    within the oracle's spread on this nearly symmetric operator."""
+    torch = cuda
+    A, Bfull = system
+    B = np.ascontiguousarray(Bfull[:, :k])
+    with bk.Operator(A) as op:
+        r = op.solve(torch.from_numpy(B).cuda(), tol=TOL, maxit=5000, want_hist=False)
+        X = r.X.cpu().numpy()
+    assert np.all(r.status == 0), r.status
+    relres = np.linalg.norm(B - oracle.spmm(A, X), axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(relres < 2 * TOL), relres
+    ro = oracle.solve(A, B, tol=TOL, maxit=5000, variant="classical_merged")
+    assert np.all(ro.status == 0)
+    assert np.all(np.abs(r.iters - ro.iters) <= np.maximum(2, 0.15 * ro.iters)), (r.iters, ro.iters)
