@@ -1,0 +1,120 @@
+"""Randomized parity: seeded random sparse systems of varied shape through every form.
+
+The structured stencils of the other parity tests have rows of equal length, sorted columns and
+power-of-two-friendly sizes.  Here every case draws its own shape: n from 1 to 2999 (odd and
+even, tiles with a ragged tail), row lengths from 0 to 40 with an occasional row of hundreds to
+thousands of entries (staged tiles that overflow the stage buffer), unsorted distinct column
+indices, k from 1 to 64 (every padding of kp), and for the forms that apply M^-1 the identity or
+Jacobi.  The matrices are strictly diagonally dominant (diagonal = sum |off| + U[0.5, 2]), so
+nonsingular with ||A^-1||_inf <= 2.  Checks through the C-ABI:
+  * x_m after m = 1..3 fixed iterations per column within 1e-11 relative of the oracle's, the
+    residual histories within 1e-10, the same status;
+  * a full solve to 1e-10.  A row of hundreds of entries makes BiCGStab amplify rounding
+    differences on these matrices: one rounding unit in b moves the oracle's own iteration counts
+    by up to 20 % and its solution by up to 1e-9, while on matrices of short rows it moves them by
+    none and by 1e-16..1e-12.  So each case measures that sensitivity (four oracle solves with b
+    perturbed by one unit, the maximum over the columns) and requires the GPU iteration counts within
+    max(1, 2 x spread) of the oracle's and the solutions within max(1e-10, 10 x change) of the
+    oracle's; stable systems thus keep +-1 and 1e-10.  Every case also satisfies the bound that
+    does not depend on the trajectory: for a strictly row diagonally dominant A,
+    ||A^-1||_inf <= 1 / min_i (|a_ii| - sum_j!=i |a_ij|) (Varah's bound), so
+    ||x - x_oracle||_inf <= (||b - A x||_inf + ||b - A x_oracle||_inf) / that margin, with both
+    residuals from the oracle's product.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_12874_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+CASES = 36
+
+
+def _random_system(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(1, 3000))
+    maxlen = int(rng.choice([1, 4, 12, 40]))
+    lens = rng.integers(0, maxlen + 1, size=n)
+    if n > 10 and rng.random() < 0.35:
+        lens[int(rng.integers(n))] = int(rng.integers(100, min(n, 2000) + 1)) if n > 100 else n - 1
+    cols, vals, rowptr = [], [], [0]
+    for i in range(n):
+        m = min(int(lens[i]), n - 1)
+        off = rng.choice(np.delete(np.arange(n), i), size=m, replace=False) if m > 0 else np.zeros(0, int)
+        v = rng.uniform(-1.0, 1.0, size=m)
+        c = np.concatenate([off, [i]])
+        w = np.concatenate([v, [np.abs(v).sum() + rng.uniform(0.5, 2.0)]])
+        perm = rng.permutation(c.size)          # unsorted column indices, diagonal anywhere
+        cols.append(c[perm])
+        vals.append(w[perm])
+        rowptr.append(rowptr[-1] + c.size)
+    A = I.CSR(np.array(rowptr), np.concatenate(cols), np.concatenate(vals), f"random{seed}")
+    k = int(rng.integers(1, 65))
+    B = rng.uniform(-1.0, 1.0, size=(n, k))
+    return A, B, rng
+
+
+def _colerr(X, Xo):
+    den = np.linalg.norm(Xo, axis=0)
+    return np.linalg.norm(X - Xo, axis=0) / np.where(den == 0, 1.0, den)
+
+
+@pytest.fixture(scope="module")
+def bk(cuda):
+    from paper_1907_12874_gb300 import bicgk
+    return bicgk
+
+
+@pytest.mark.parametrize("case", range(CASES))
+def test_random_system(bk, cuda, case):
+    torch = cuda
+    variant = list(oracle.VARIANTS)[case % len(oracle.VARIANTS)]
+    A, B, rng = _random_system(case)
+    base = variant.rsplit("_", 1)[0]
+    jacobi = base in ("precond", "reordered", "ppipe") and rng.random() < 0.5
+    flags = oracle.JACOBI if jacobi else 0
+    m = int(rng.integers(1, 4))
+    with bk.Operator(A) as op:
+        Bd = torch.from_numpy(B).cuda()
+        r = op.solve(Bd, tol=0.0, maxit=m, variant=variant, flags=bk.FLAG_NO_STOP_TEST | (bk.FLAG_JACOBI if jacobi else 0))
+        ro = oracle.solve(A, B, tol=0.0, maxit=m, variant=variant, flags=oracle.NO_STOP_TEST | flags)
+        X = r.X.cpu().numpy()
+        assert np.array_equal(r.status, ro.status), (r.status, ro.status)
+        assert np.all(_colerr(X, ro.X) <= 1e-11), (A.n, B.shape[1], m, _colerr(X, ro.X).max())
+        np.testing.assert_allclose(r.hist[: m + 1], ro.hist[: m + 1], rtol=1e-10, atol=1e-300)
+        r = op.solve(Bd, tol=1e-10, maxit=2000, variant=variant, flags=bk.FLAG_JACOBI if jacobi else 0)
+        ro = oracle.solve(A, B, tol=1e-10, maxit=2000, variant=variant, flags=flags)
+        X = r.X.cpu().numpy()
+    assert np.all(r.status == 0) and np.all(ro.status == 0), (r.status, ro.status)
+    # the oracle's own sensitivity to one rounding unit in b (four draws), per column: the change
+    # of its iteration count and of its solution
+    spread = np.zeros(B.shape[1], dtype=np.int64)
+    sens = np.zeros(B.shape[1])
+    g = np.random.default_rng(77 + case)
+    for _ in range(4):
+        rp = oracle.solve(A, B * (1.0 + 2.0 ** -52 * g.standard_normal(B.shape)), tol=1e-10, maxit=2000,
+                          variant=variant, flags=flags)
+        spread = np.maximum(spread, np.abs(rp.iters - ro.iters))
+        sens = np.maximum(sens, _colerr(rp.X, ro.X))
+    # the GPU differs from the oracle in rounding at every iteration, not once: twice the one-unit
+    # spread in iterations, ten times the one-unit change of the solution (stable systems: +-1
+    # and 1e-10, the bar of the structured tests).  The sensitivity is the system's: the maximum
+    # over its columns (four draws per column are a noisy estimate of one column's).
+    assert np.all(np.abs(r.iters - ro.iters) <= max(1, 2 * int(spread.max()))), (r.iters, ro.iters, spread)
+    err = _colerr(X, ro.X)
+    assert np.all(err <= max(1e-10, 10.0 * float(sens.max()))), (err, sens)
+    # Varah's bound on ||A^-1||_inf for a strictly row diagonally dominant A
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    diag = np.zeros(A.n)
+    off = np.zeros(A.n)
+    isdiag = A.colidx == rows
+    np.add.at(diag, rows[isdiag], np.abs(A.vals[isdiag]))
+    np.add.at(off, rows[~isdiag], np.abs(A.vals[~isdiag]))
+    margin = float(np.min(diag - off))
+    assert margin > 0
+    res_g = np.abs(B - oracle.spmm(A, X)).max(axis=0)
+    res_o = np.abs(B - oracle.spmm(A, ro.X)).max(axis=0)
+    bound = (res_g + res_o) / margin
+    assert np.all(np.abs(X - ro.X).max(axis=0) <= 1.01 * bound + 1e-300), (np.abs(X - ro.X).max(axis=0), bound)
