@@ -137,7 +137,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_algorithmic(name: str, n: int, nnz: int, k: int):
+def kernel_algorithmic(name: str, n: int, nnz: int, k: int, variant: str = "classical_merged"):
     """Algorithmic bytes and FP64 flops of one launch of a kernel class (ideal x reuse)."""
     from paper_1907_12874_gb300 import bicgk as bk  # noqa: F401
     vec = 8.0 * n * k
@@ -145,6 +145,11 @@ def kernel_algorithmic(name: str, n: int, nnz: int, k: int):
         resid = name.startswith("spmm_resid")
         b = 12.0 * nnz + 4.0 * (n + 1) + 2 * vec + (vec if resid else 0.0)
         f = 2.0 * nnz * k + (n * k if resid else 0.0)
+        if name.startswith("spmm_delta"):   # epilogue dot (v, r^0): reads r^0
+            b, f = b + vec, f + 2.0 * n * k
+        if name.startswith("spmm_g1"):      # epilogue dots (t,s), (t,t), (s,s)
+            # s is the product's own x in Algorithm 2 (read once); Algorithm 5 multiplies s^ = M^-1 s
+            b, f = b + (vec if variant.startswith("precond") else 0.0), f + 6.0 * n * k
         return b, f
     table = {  # reads, writes, FP64 flops per element (FMA = 2)
         "dot_delta": (2, 0, 2), "upd_s": (2, 1, 2), "merged_phi_psi_theta": (2, 0, 6),
@@ -164,6 +169,13 @@ def kernel_algorithmic(name: str, n: int, nnz: int, k: int):
 
 
 KERNEL_SOURCES = {"spmm": ("bicgk_dev.cuh", "bicgk_spmm.cu"), "vec": ("bicgk_dev.cuh", "bicgk_vec.cu")}
+
+
+def kernel_source_kind(name: str) -> str:
+    """Which sources a kernel class is compiled from: the SpMM kernels, or the streaming kernels
+    (which also hold the SpMM with a dot epilogue)."""
+    plain_spmm = name.startswith("spmm") and not name.startswith(("spmm_delta", "spmm_g1"))
+    return "spmm" if plain_spmm else "vec"
 
 
 def source_hash(kind: str) -> str:
@@ -187,7 +199,7 @@ def recorded_traffic():
         m = re.match(r"\|\s*([a-z0-9_]+)\s*\|\s*(\d+)\s*\|\s*([0-9.e+]+)\s*\|\s*([0-9a-f]{12})\s*\|", line)
         if not m:
             continue
-        kind = "spmm" if m.group(1).startswith("spmm") else "vec"
+        kind = kernel_source_kind(m.group(1))
         if m.group(4) == source_hash(kind):
             out[(m.group(1), int(m.group(2)))] = float(m.group(3))
     return out
@@ -249,7 +261,7 @@ def run_reference(args):
     from paper_1907_12874_gb300 import inputs
     A = inputs.convdiff7(args.grid)
     B = inputs.rhs(A.n, args.k, 2)
-    cols, iters = 1, 10
+    cols, iters = 2, 40        # about 1.6 s of CPU time per step on 16 cores
     for _ in range(args.warmup):
         cpu_oracle_rate(A, B, args.variant, cols, iters)
     rates, secs = [], 0.0
@@ -385,6 +397,16 @@ TABLE2_VECTORS = {"classical": (22, 18), "improved": (33, 20), "pipelined": (43,
 TABLE2_COPIES = {"classical": 0, "improved": 0, "pipelined": 0, "precond": 2, "reordered": 2, "ppipe": 2}
 
 
+def fused_passes_saved(variant: str, k: int) -> int:
+    """Vector passes per iteration that the dot epilogues of the SpMM save (the library fuses when
+    a solve runs as two column groups, k >= 16): the dot kernel after v = A p re-reads v; the one
+    after t = A s re-reads t and s, and s is the product's own x in Algorithm 2 (in Algorithm 5 the
+    product reads s^ = M^-1 s, so the epilogue still reads s)."""
+    if k < 16:
+        return 0
+    return {"classical_merged": 3, "precond_merged": 2, "reordered_merged": 1}.get(variant, 0)
+
+
 def solve_gbs(A, k: int, variant: str, column_iterations: int, ms: float, groups: int) -> float:
     """Algorithmic HBM GB/s of the useful work of a solve: every column-iteration reads x and
     writes y in the form's two products, pays its share of the CSR reads of its group's products
@@ -395,6 +417,7 @@ def solve_gbs(A, k: int, variant: str, column_iterations: int, ms: float, groups
     N, nnz = A.n, A.nnz
     kg = k / groups
     vecs = TABLE2_VECTORS[base][0 if form == "plain" else 1] + 2 * TABLE2_COPIES[base]
+    vecs -= fused_passes_saved(variant, k)
     per_col_iter = 2 * (16 * N + (12 * nnz + 4 * (N + 1)) / kg) + vecs * 8 * N
     return column_iterations * per_col_iter / (ms / 1e3) / 1e9
 
@@ -425,7 +448,8 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
                 torch.cuda.synchronize()
                 s_it = e0.elapsed_time(e1) / 1e3 / nit
                 vecs = TABLE2_VECTORS[base][0 if form == "plain" else 1] + 2 * TABLE2_COPIES[base]
-                byts = 2 * (12 * nnz + 4 * (N + 1) + 16 * N * k) + vecs * 8 * N * k
+                # the passes this implementation makes (the SpMM dot epilogues save some at k >= 16)
+                byts = 2 * (12 * nnz + 4 * (N + 1) + 16 * N * k) + (vecs - fused_passes_saved(v, k)) * 8 * N * k
                 C = nnz / N
                 model = (2 * N * (8 * k * (C + 1) + 4 * (3 * C + 1)) + vecs * 8 * N * k) / (hbm_gbs * 1e9)
                 res["rows"][f"{v}/k{k}"] = {"rhs_iterations_per_s": k / s_it, "ms_per_iter": s_it * 1e3,
@@ -646,7 +670,7 @@ def main():
     bicgk.set_profiling(op.handle, args.eager)
     total = sum(t for _, t in times.values())
     dom, (dl, dt) = max(times.items(), key=lambda kv: kv[1][1])
-    byts, flops = kernel_algorithmic(dom, A.n, A.nnz, args.k)
+    byts, flops = kernel_algorithmic(dom, A.n, A.nnz, args.k, args.variant)
     avg_s = dt / dl / 1e3
     hbm, hbm_kind = hbm_peak()
     t_mem, t_alu = byts / (hbm * 1e9), flops / (FP64_PEAK_TFLOPS * 1e12)
@@ -690,7 +714,7 @@ def main():
     # CPU oracle on the host cores (rank 0, N = 1 only)
     if not args.no_cpu and rank == 0 and world == 1:
         import oracle
-        cols, iters = 2, 10
+        cols, iters = 8, 60    # about 10 s of CPU time on 16 cores
         rate, secs = cpu_oracle_rate(A, B_host, args.variant, cols, iters)
         out["cpu_baseline"] = {"value": rate, "unit": "RHS-iterations/s", "cores": oracle.threads(),
                                "kind": "oracle",
@@ -699,16 +723,17 @@ def main():
         # the oracle's basic form of the same method (one loop per vector operation), all cores
         plain_v = args.variant.replace("_merged", "_plain")
         if plain_v != args.variant:
-            ratep, secsp = cpu_oracle_rate(A, B_host, plain_v, cols, iters)
+            colsp, itersp = 2, 30
+            ratep, secsp = cpu_oracle_rate(A, B_host, plain_v, colsp, itersp)
             out["cpu_baseline"]["basic_form"] = {"variant": plain_v, "value": ratep, "cores": oracle.threads(),
-                                                 "sample": f"{cols} columns x {iters} fixed iterations ({secsp:.1f} s)"}
+                                                 "sample": f"{colsp} columns x {itersp} fixed iterations ({secsp:.1f} s)"}
         # the same oracle on one core (the paper's runs use one MPI rank per core)
         all_threads = oracle.threads()
         oracle.set_threads(1)
-        rate1, secs1 = cpu_oracle_rate(A, B_host, args.variant, 1, 4)
+        rate1, secs1 = cpu_oracle_rate(A, B_host, args.variant, 1, 12)
         oracle.set_threads(all_threads)
         out["cpu_baseline"]["one_core"] = {"value": rate1, "cores": 1,
-                                           "sample": f"1 column x 4 fixed iterations ({secs1:.1f} s)"}
+                                           "sample": f"1 column x 12 fixed iterations ({secs1:.1f} s)"}
     op.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -216,8 +216,8 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
  *
  * Scratch: one 16 MiB file-scope device array in this library, which every
  * GPU that loads the library keeps until the process exits.  A problem fits if
- *   8*18*(n_rows*kp + 34) + 8*(maxit+1)*kp + 8*448*(4*SMs + 64) + ~2 KB <= 16 MiB
- * (kp = k rounded up to a power of two; about n_rows*kp <= 95,000 at
+ *   8*18*(n_rows*kp + 34) + 8*(maxit+1)*kp + 8*448*(8*SMs + 128) + ~2 KB <= 16 MiB
+ * (kp = k rounded up to a power of two; about n_rows*kp <= 80,000 at
  * maxit = 1000); larger problems return BICGK_E_UNSUPPORTED with the sizes in
  * bicgk_last_cuda_error().  variant: 0..9 (the Improved form needs a
  * transposed copy of A and is refused); flags: BICGK_FLAG_NO_STOP_TEST only.  The iteration loop runs from the host (one
@@ -242,9 +242,15 @@ enum bicgk_option {
                                       default: the occupancy maximum, 2)                      */
   BICGK_OPT_SPMM_BLOCKS_PER_SM = 2, /* blocks of 256 threads per SM for the SpMM (0..32; default:
                                       the occupancy maximum)                                   */
-  BICGK_OPT_RHS_GROUPS = 3          /* 0: k >= 16 is solved as two column groups running
+  BICGK_OPT_RHS_GROUPS = 3,         /* 0: k >= 16 is solved as two column groups running
                                       concurrently on two internal streams (default); 1: one
                                       group.  Profiling mode always uses one group.            */
+  BICGK_OPT_FUSED_DOTS = 4          /* merged forms of Algorithms 2, 5 and 6: take the dot
+                                      kernel that follows an SpMM in the listing (delta after
+                                      v = A p; group 1 after t = A s, Algorithms 2 and 5) into
+                                      the SpMM's epilogue.  0: when the solve runs as two column
+                                      groups (default); 1: never; 2: always.  The iterates are
+                                      the same up to the summation order of those dots.        */
 };
 
 /*

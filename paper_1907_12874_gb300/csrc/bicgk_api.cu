@@ -42,7 +42,8 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 // One step of a kernel sequence: a streaming op, or an SpMM between workspace roles.
 struct Step {
-  int spmm;  // 0: streaming op `op`; 1: y = A x; 2: y = b - A x; 3: y = A x in FP32; 4: y = A^T x
+  int spmm;  // 0: streaming op `op`; 1: y = A x; 2: y = b - A x; 3: y = A x in FP32; 4: y = A^T x;
+             // 5: y = A x with the dots of epilogue `op` (SpmmEpi)
   int op;
   int x, y, b;
 };
@@ -51,6 +52,7 @@ Step spmm(int x, int y) { return Step{1, -1, x, y, 0}; }
 Step resid(int x, int y, int b) { return Step{2, -1, x, y, b}; }
 Step spmm32(int x, int y) { return Step{3, -1, x, y, 0}; }
 Step spmm_t(int x, int y) { return Step{4, -1, x, y, 0}; }
+Step spmm_dot(int x, int y, int epi) { return Step{5, epi, x, y, 0}; }
 
 
 
@@ -70,14 +72,29 @@ Seq make_inner32_seq() {
 
 // Kernel sequences of the twelve forms (one Step = one kernel launch).  `jacobi`: M = diag(A)
 // instead of the identity copy for the forms that apply M^-1 (Algorithms 5, 6, 7).
-Seq make_seq(int variant, bool jacobi = false) {
+// `fuse`: the merged forms take the dot kernel that follows an SpMM into the SpMM's epilogue
+// (delta after v = A p, group 1 after t = A s).
+Seq make_seq(int variant, bool jacobi = false, bool fuse = false) {
   Seq q;
+  // y = A x followed by the dot kernel `op` of the listing, fused when `fuse`
+  auto spmm_then = [](int x, int y, int op, int epi, bool fuse, std::vector<Step> &body) {
+    if (fuse) {
+      body.push_back(spmm_dot(x, y, epi));
+    } else {
+      body.push_back(spmm(x, y));
+      body.push_back(vec(op));
+    }
+  };
+  const bool fuse_delta = fuse, fuse_g1 = fuse;
   q.fin = {resid(V_X, V_TMP, V_B), vec(OP_TRUE_RES)};
   switch (variant) {
     case BICGK_CLASSICAL_MERGED:  // Algorithm 2
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_C)};
-      q.body = {spmm(V_P, V_V), vec(OP_DELTA), vec(OP_UPD_S), spmm(V_S, V_T), vec(OP_G1), vec(OP_G3),
-                vec(OP_UPD_P)};
+      spmm_then(V_P, V_V, OP_DELTA, EPI_DELTA, fuse_delta, q.body);
+      q.body.push_back(vec(OP_UPD_S));
+      spmm_then(V_S, V_T, OP_G1, EPI_G1, fuse_g1, q.body);
+      q.body.push_back(vec(OP_G3));
+      q.body.push_back(vec(OP_UPD_P));
       break;
     case BICGK_CLASSICAL_PLAIN:  // Algorithm 1, one kernel per line
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_C)};
@@ -88,8 +105,10 @@ Seq make_seq(int variant, bool jacobi = false) {
     case BICGK_REORDERED_MERGED:  // Algorithm 6; v^ in V_P, t^ in V_TMP
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_R)};
       if (jacobi) q.setup.push_back(vec(OP_PREC_R_Z));
-      q.body = {spmm(V_P, V_V), vec(OP_DELTA), vec(OP_PREC_V_S), vec(OP_UPD_TH), spmm(V_TMP, V_T),
-                vec(OP_RG4), vec(OP_PREC_T_Q), vec(OP_UPD_R_R), vec(OP_RFIN)};
+      spmm_then(V_P, V_V, OP_DELTA, EPI_DELTA, fuse_delta, q.body);
+      for (int op : {OP_PREC_V_S, OP_UPD_TH}) q.body.push_back(vec(op));
+      q.body.push_back(spmm(V_TMP, V_T));
+      for (int op : {OP_RG4, OP_PREC_T_Q, OP_UPD_R_R, OP_RFIN}) q.body.push_back(vec(op));
       break;
     case BICGK_REORDERED_PLAIN:
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_R)};
@@ -111,8 +130,12 @@ Seq make_seq(int variant, bool jacobi = false) {
       break;
     case BICGK_PRECOND_MERGED:  // Algorithm 5; p^ in V_Q, s^ in V_Y
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_C)};
-      q.body = {vec(OP_PREC_P_Q), spmm(V_Q, V_V), vec(OP_DELTA), vec(OP_UPD_S), vec(OP_PREC_S_Y), spmm(V_Y, V_T),
-                vec(OP_G1), vec(OP5_RRHO), vec(OP5_UPD_X), vec(OP_UPD_P)};
+      q.body.push_back(vec(OP_PREC_P_Q));
+      spmm_then(V_Q, V_V, OP_DELTA, EPI_DELTA, fuse_delta, q.body);
+      q.body.push_back(vec(OP_UPD_S));
+      q.body.push_back(vec(OP_PREC_S_Y));
+      spmm_then(V_Y, V_T, OP_G1, EPI_G1, fuse_g1, q.body);
+      for (int op : {OP5_RRHO, OP5_UPD_X, OP_UPD_P}) q.body.push_back(vec(op));
       break;
     case BICGK_PRECOND_PLAIN:
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_C)};
@@ -218,6 +241,7 @@ struct bicgk_op_s {
   int opt_vec_blocks = 0;
   int opt_spmm_blocks = 0;
   int opt_groups = 0;
+  int opt_fused = 0;  // BICGK_OPT_FUSED_DOTS
   // launch shapes chosen by the batch autotuner (0 = the per-SM rule above)
   int grid_vec_abs = 0;
   int grid_spmm_abs = 0;
@@ -289,12 +313,19 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
     sa.vals = A->d_val32;
     return launch_spmm32(a.kp, sa, A->nsm * spmm32_blocks_per_sm(a.kp, sa.stage_cap), s);
   }
+  if (st.spmm == 5) {  // the fused kernel's grid: its occupancy, at most the reduction buffers' capacity
+    int nb = spmm_dot_blocks_per_sm(a.kp, st.op, sa.stage_cap);
+    if (nb > kPartBlocksPerSm) nb = kPartBlocksPerSm;
+    if (A->opt_spmm_blocks > 0 && A->opt_spmm_blocks < nb) nb = A->opt_spmm_blocks;
+    return launch_spmm_dot(a.kp, st.op, sa, a, A->nsm * nb, s);
+  }
   const int mode = st.spmm == 2 ? 1 : 0;
   return launch_spmm(a.kp, mode, sa, spmm_grid(A, a.kp, mode), s);
 }
 
 std::string step_name(const Step &st, int kp) {
   if (st.spmm == 0) return op_name(st.op);
+  if (st.spmm == 5) return std::string(spmm_dot_name(st.op)) + "_k" + std::to_string(kp);
   return std::string(st.spmm == 2 ? "spmm_resid_k" : "spmm_k") + std::to_string(kp);
 }
 
@@ -360,7 +391,7 @@ int ensure_workspace(bicgk_op A, Workspace &W, int kp) {
   CK(cudaMemset(W.d_vec, 0, bytes));
   CK(cudaMalloc(&W.d_sc, sizeof(double) * S_NSLOT * kMaxKp));
   CK(cudaMalloc(&W.d_fl, sizeof(int) * F_NFLAG * kMaxKp));
-  CK(cudaMalloc(&W.d_part, sizeof(double) * ((size_t)A->nsm * 4 + kMaxRedGroups) * kMaxDots * kMaxKp));
+  CK(cudaMalloc(&W.d_part, sizeof(double) * ((size_t)A->nsm * kPartBlocksPerSm + kMaxRedGroups) * kMaxDots * kMaxKp));
   CK(cudaMemset(W.d_sc, 0, sizeof(double) * S_NSLOT * kMaxKp));
   CK(cudaMemset(W.d_fl, 0, sizeof(int) * F_NFLAG * kMaxKp));
   W.kp = kp;
@@ -454,8 +485,19 @@ int build_graph_seq(bicgk_op A, Workspace &W, const Seq &q, const int *ext_act, 
   return BICGK_OK;
 }
 
-int build_graph(bicgk_op A, Workspace &W, int variant, bool jacobi, GraphEntry *ge) {
-  return build_graph_seq(A, W, make_seq(variant, jacobi), nullptr, ge, jacobi ? A->d_invdiag : nullptr);
+// Whether a solve of k columns takes the merged forms' dot kernels into the SpMM epilogues
+// (BICGK_OPT_FUSED_DOTS).  Automatic: when the columns are split into two concurrent groups.  There
+// it was measured faster (fewer kernels per iteration for the two groups to share the GPU: 3-4 %
+// at k = 16 and 32); with one group the fused SpMM's grid-wide reduction costs more than the
+// separate dot kernel (2-8 % slower at k = 1..8).  Profiling mode decides the same way.
+bool fuse_dots(bicgk_op A, int k) {
+  if (A->opt_fused == 1) return false;
+  if (A->opt_fused == 2) return true;
+  return A->opt_groups != 1 && k >= kSplitMinK;
+}
+
+int build_graph(bicgk_op A, Workspace &W, int variant, bool jacobi, bool fuse, GraphEntry *ge) {
+  return build_graph_seq(A, W, make_seq(variant, jacobi, fuse), nullptr, ge, jacobi ? A->d_invdiag : nullptr);
 }
 
 // What a form needs beyond the operator: the transposed copy (Algorithm 3), the Jacobi diagonal.
@@ -524,8 +566,8 @@ int run_profiled_seq(bicgk_op A, Workspace &W, const Seq &q, const KArgs &a, cud
   return run_list(q.fin);
 }
 
-int run_profiled(bicgk_op A, Workspace &W, int variant, bool jacobi, const KArgs &a, cudaStream_t s) {
-  return run_profiled_seq(A, W, make_seq(variant, jacobi), a, s);
+int run_profiled(bicgk_op A, Workspace &W, int variant, bool jacobi, bool fuse, const KArgs &a, cudaStream_t s) {
+  return run_profiled_seq(A, W, make_seq(variant, jacobi, fuse), a, s);
 }
 
 }  // namespace
@@ -709,7 +751,8 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
   if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   const bool jacobi = (flags & BICGK_FLAG_JACOBI) != 0;
-  const int gkey = variant + 100 * (jacobi ? 1 : 0);
+  const bool fuse = fuse_dots(A, k);
+  const int gkey = variant + 100 * (jacobi ? 1 : 0) + 1000 * (fuse ? 1 : 0);
   int rc0 = ensure_variant_data(A, variant, jacobi, s);
   if (rc0) return rc0;
   // columns are independent: split k >= kSplitMinK into two groups solved concurrently, so that
@@ -724,7 +767,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     if ((rc = ensure_workspace(A, A->ws[g], kpg))) return rc;
     if ((rc = ensure_hist(A->ws[g], (int64_t)(maxit + 1) * kpg))) return rc;
   }
-  const Seq q = make_seq(variant, jacobi);
+  const Seq q = make_seq(variant, jacobi, fuse);
   // inputs
   const double *dB = B, *dX0 = X0;
   double *dX = X;
@@ -760,12 +803,12 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     CK(launch_pack(dB + c0[g], dX0 ? dX0 + c0[g] : nullptr, k, kg, a0, gs));
     launches += 2;  // reset, pack
     if (A->profiling) {
-      if ((rc = run_profiled(A, W, variant, jacobi, a0, gs))) return rc;
+      if ((rc = run_profiled(A, W, variant, jacobi, fuse, a0, gs))) return rc;
     } else {
       auto it = W.graphs.find(gkey);
       if (it == W.graphs.end()) {
         GraphEntry ge;
-        if ((rc = build_graph(A, W, variant, jacobi, &ge))) {
+        if ((rc = build_graph(A, W, variant, jacobi, fuse, &ge))) {
           if (ge.exec) cudaGraphExecDestroy(ge.exec);
           if (ge.graph) cudaGraphDestroy(ge.graph);
           return rc;
@@ -1008,6 +1051,10 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value) {
       if (value < 0 || value > 2) return BICGK_E_INVALID;
       A->opt_groups = (int)value;
       break;
+    case BICGK_OPT_FUSED_DOTS:
+      if (value < 0 || value > 2) return BICGK_E_INVALID;
+      A->opt_fused = (int)value;
+      break;
     default:
       return BICGK_E_INVALID;
   }
@@ -1096,7 +1143,7 @@ int batch_ensure(bicgk_batch b, int32_t maxit) {
       const size_t bytes = (size_t)W.vstride * V_NVEC * sizeof(double);
       CK(cudaMalloc(&W.d_vec, bytes));
       CK(cudaMemset(W.d_vec, 0, bytes));
-      CK(cudaMalloc(&W.d_part, sizeof(double) * ((size_t)A->nsm * 4 + kMaxRedGroups) * kMaxDots * kMaxKp));
+      CK(cudaMalloc(&W.d_part, sizeof(double) * ((size_t)A->nsm * kPartBlocksPerSm + kMaxRedGroups) * kMaxDots * kMaxKp));
       W.kp = kp;
     }
   }
@@ -1465,7 +1512,7 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
   const size_t b_vec = round256(sizeof(double) * (size_t)vstride * V_NVEC);
   const size_t b_sc = round256(sizeof(double) * S_NSLOT * kMaxKp);
   const size_t b_fl = round256(sizeof(int) * F_NFLAG * kMaxKp);
-  const size_t b_part = round256(sizeof(double) * ((size_t)nsm * 4 + kMaxRedGroups) * kMaxDots * kMaxKp);
+  const size_t b_part = round256(sizeof(double) * ((size_t)nsm * kPartBlocksPerSm + kMaxRedGroups) * kMaxDots * kMaxKp);
   const size_t b_ctl = round256(sizeof(Ctl));
   const size_t b_hist = round256(sizeof(double) * (size_t)hist_len);
   const size_t need = b_vec + b_sc + b_fl + b_part + b_ctl + b_hist;

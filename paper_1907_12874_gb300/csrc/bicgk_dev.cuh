@@ -21,7 +21,8 @@ constexpr int kSpmmThreads = 256; // threads per block of the SpMM kernels
 constexpr int kSpmmTileRows = 256;      // rows per staged tile (kp <= 2 path)
 constexpr int kSpmmStageMax = 4096;     // largest staged tile (CSR entries)
 constexpr int kRedGroup = 16;           // blocks per first-level group of the grid reduction
-constexpr int kMaxRedGroups = 64;       // group tickets (grids up to 1024 blocks)
+constexpr int kMaxRedGroups = 128;      // group tickets (grids up to 2048 blocks)
+constexpr int kPartBlocksPerSm = 8;     // block partials per SM the reduction buffers hold (SpMM grids)
 
 // Per-column FP64 scalar slots.
 enum Slot : int {
@@ -130,6 +131,15 @@ struct SpmmArgs {
 };
 cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s);
 int spmm_blocks_per_sm(int kp, int mode, int stage_cap);
+// y = A x with the dots of the next listing step taken in the product's epilogue (FP64), then
+// the grid reduction and that step's scalar rule, as the separate dot kernel would do them.
+enum SpmmEpi : int {
+  EPI_DELTA = 0,  // delta = (v, r^0) after v = A p: the dot kernel OP_DELTA
+  EPI_G1 = 1,     // (t, s), (t, t), (s, s) after t = A s: group 1 of Algorithm 2 (OP_G1)
+};
+cudaError_t launch_spmm_dot(int kp, int epi, const SpmmArgs &s, const KArgs &a, int grid, cudaStream_t st);
+int spmm_dot_blocks_per_sm(int kp, int epi, int stage_cap);  // occupancy of the fused kernel
+const char *spmm_dot_name(int epi);
 // y = A^T x (ld = k) by an atomic scatter over the rows of A.
 cudaError_t launch_spmm_t_atomic(const int32_t *rowptr, const int32_t *colidx, const double *vals, const double *x,
                                  double *y, int64_t n, int k, cudaStream_t s);

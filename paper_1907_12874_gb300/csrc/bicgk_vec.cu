@@ -1145,17 +1145,19 @@ struct OpDef<OP_IR_UPDATE> {  // x += d for the columns this pass refines
 
 // ------------------------------------------------------------------ the kernel
 
-template <int ND>
+template <int ND, int NT>
 struct RedSmem {
-  double red[kVecThreads / 32][ND < 4 ? ND : 4][kMaxKp];  // warp partials, up to 4 dots at a time
+  double red[NT / 32][ND < 4 ? ND : 4][kMaxKp];  // warp partials, up to 4 dots at a time
   double sums[ND * kMaxKp];
   unsigned int ticket;
 };
 
-template <class D, int ND = D::ND>
+// NT: threads per block of the calling kernel (512 for the streaming kernels, 256 for the SpMM
+// with a dot epilogue); every thread holds the partial sums of its two columns.
+template <class D, int NT = kVecThreads, int ND = D::ND>
 __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND : 1]) {
   constexpr int NC = ND < 4 ? ND : 4;  // dots per shared-memory chunk
-  __shared__ RedSmem<ND> sm;
+  __shared__ RedSmem<ND, NT> sm;
   const int kp = a.kp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double v0[ND], v1[ND];
@@ -1200,7 +1202,7 @@ __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND :
     for (int t = threadIdx.x; t < nchunk; t += blockDim.x) {
       const int d = t / kp, c = t - d * kp;
       double s = 0.0;
-      for (int w = 0; w < kVecThreads / 32; ++w) s += sm.red[w][d][c];
+      for (int w = 0; w < NT / 32; ++w) s += sm.red[w][d][c];
       mypart[(d0 + d) * kMaxKp + c] = s;
     }
     __syncthreads();
@@ -1211,9 +1213,10 @@ __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND :
   // levels: the last block of each group of kRedGroup blocks adds its group (ascending block
   // order) into a group partial, and the last group to finish adds the group partials.
   constexpr int kStride = kMaxDots * kMaxKp;
-  constexpr int kOneLevelMax = 8192;
+  constexpr int kOneLevelMax = 8192;   // partial sums one final block adds at most
+  constexpr int kOneLevelBlocks = 640; // ... and blocks (the streaming grids have at most 608)
   const int nblk = gridDim.x;
-  const bool two_level = nblk * nout > kOneLevelMax;
+  const bool two_level = nblk * nout > kOneLevelMax || nblk > kOneLevelBlocks;
   const int ngrp = two_level ? (nblk + kRedGroup - 1) / kRedGroup : 1;
   const double *top = a.part;  // partials the final block adds: block partials or group partials
   // the threads that wrote partials make them visible before thread 0 takes the ticket
@@ -1343,6 +1346,142 @@ __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<OP>::value) vec_kern
     for (int d = 0; d < ND; ++d) accd[d] = to_d2(acc[d]);
     reduce_and_finalize<D>(a, accd);
   }
+}
+
+// ------------------------------------------------------------------ SpMM with a dot epilogue
+//
+// y = A x (FP64) followed by the dots of the next step of the listing, taken while y is still in
+// registers, then the grid reduction and that step's scalar rule (FIN) exactly as the separate
+// dot kernel would run them.  Saves that kernel's launch, ramp and tail and its re-read of y.
+// The row sums are those of the SpMM kernels (spmm_group_kernel with two columns per lane for
+// kp >= 4, spmm_row_kernel with staged tiles for kp <= 2): one FMA per nonzero and column, in
+// CSR order.  Thread -> column mapping: lane l of a row holds columns 2l, 2l+1 (kp >= 4), the
+// one or two columns of its row (kp <= 2), which is the mapping reduce_and_finalize assumes.
+
+// Epilogue policies: ND dots, the FIN rule and loop control of the dot kernel they replace, and
+// the accumulation for one row's two columns (acc2, element o of the double2 view) or, at
+// kp = 1, one column (acc1, element o).
+struct EpiDelta {  // delta = (v, r^0): OP_DELTA
+  static constexpr int ND = 1, FIN = FIN_DELTA, CTL = CTL_NONE;
+  __device__ static void acc2(const KArgs &a, int64_t o, double2 y, double2 (&acc)[ND]) {
+    dot_acc(acc[0], y, ld2(a.v[V_R0], o));
+  }
+  __device__ static void acc1(const KArgs &a, int64_t o, double y, double2 (&acc)[ND]) {
+    acc[0].x = fma(y, a.v[V_R0][o], acc[0].x);
+  }
+};
+struct EpiG1 {  // phi = (t,s), psi = (t,t), theta = (s,s): OP_G1
+  static constexpr int ND = 3, FIN = FIN_G1, CTL = CTL_NONE;
+  __device__ static void acc2(const KArgs &a, int64_t o, double2 t, double2 (&acc)[ND]) {
+    const double2 s = ld2(a.v[V_S], o);
+    dot_acc(acc[0], t, s);
+    dot_acc(acc[1], t, t);
+    dot_acc(acc[2], s, s);
+  }
+  __device__ static void acc1(const KArgs &a, int64_t o, double t, double2 (&acc)[ND]) {
+    const double s = a.v[V_S][o];
+    acc[0].x = fma(t, s, acc[0].x);
+    acc[1].x = fma(t, t, acc[1].x);
+    acc[2].x = fma(s, s, acc[2].x);
+  }
+};
+
+template <int KP, class E>
+__global__ void __launch_bounds__(kSpmmThreads) spmm_dot_kernel(const SpmmArgs sp, const KArgs a) {
+  double2 acc[E::ND];
+#pragma unroll
+  for (int d = 0; d < E::ND; ++d) acc[d] = make_double2(0.0, 0.0);
+  const int32_t *__restrict__ rp = sp.rowptr;
+  const int32_t *__restrict__ ci = sp.colidx;
+  const double *__restrict__ va = static_cast<const double *>(sp.vals);
+  if constexpr (KP >= 4) {
+    constexpr int L = KP / 2;  // lanes per row, two columns each
+    constexpr int RPP = kSpmmThreads / L;
+    const int g = threadIdx.x / L, cl = threadIdx.x % L;
+    const double2 *__restrict__ x2 = static_cast<const double2 *>(sp.x);
+    double2 *__restrict__ y2 = static_cast<double2 *>(sp.y);
+    const int64_t stride = (int64_t)gridDim.x * RPP;
+    for (int64_t r = (int64_t)blockIdx.x * RPP + g; r < sp.n; r += stride) {
+      const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
+      double2 y = make_double2(0.0, 0.0);
+      int e = e0;
+      for (; e + 1 < e1; e += 2) {
+        const int j0 = __ldg(ci + e), j1 = __ldg(ci + e + 1);
+        const double a0 = __ldg(va + e), a1 = __ldg(va + e + 1);
+        const double2 u0 = __ldg(x2 + (int64_t)j0 * L + cl), u1 = __ldg(x2 + (int64_t)j1 * L + cl);
+        y.x = fma(a0, u0.x, y.x);
+        y.y = fma(a0, u0.y, y.y);
+        y.x = fma(a1, u1.x, y.x);
+        y.y = fma(a1, u1.y, y.y);
+      }
+      if (e < e1) {
+        const int j0 = __ldg(ci + e);
+        const double a0 = __ldg(va + e);
+        const double2 u0 = __ldg(x2 + (int64_t)j0 * L + cl);
+        y.x = fma(a0, u0.x, y.x);
+        y.y = fma(a0, u0.y, y.y);
+      }
+      const int64_t o = r * L + cl;
+      y2[o] = y;
+      E::acc2(a, o, y, acc);
+    }
+  } else {
+    // one lane per row, each 256-row tile's CSR entries staged in shared memory
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int cap = sp.stage_cap;
+    double *s_val = reinterpret_cast<double *>(smem_raw);
+    int32_t *s_col = reinterpret_cast<int32_t *>(s_val + cap);
+    const int64_t ntiles = (sp.n + kSpmmTileRows - 1) / kSpmmTileRows;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int64_t r0 = t * kSpmmTileRows;
+      const int64_t r1 = (r0 + kSpmmTileRows < sp.n) ? r0 + kSpmmTileRows : sp.n;
+      const int te0 = __ldg(rp + r0), te1 = __ldg(rp + r1);
+      const bool staged = (te1 - te0) <= cap;
+      if (staged) {
+        for (int e = te0 + threadIdx.x; e < te1; e += blockDim.x) {
+          s_val[e - te0] = __ldg(va + e);
+          s_col[e - te0] = __ldg(ci + e);
+        }
+      }
+      __syncthreads();
+      const int64_t r = r0 + threadIdx.x;
+      if (r < r1) {
+        const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
+        if constexpr (KP == 1) {
+          const double *__restrict__ xs = static_cast<const double *>(sp.x);
+          double y = 0.0;
+          if (staged)
+            for (int e = e0; e < e1; ++e) y = fma(s_val[e - te0], __ldg(xs + s_col[e - te0]), y);
+          else
+            for (int e = e0; e < e1; ++e) y = fma(__ldg(va + e), __ldg(xs + __ldg(ci + e)), y);
+          static_cast<double *>(sp.y)[r] = y;
+          E::acc1(a, r, y, acc);
+        } else {
+          const double2 *__restrict__ x2 = static_cast<const double2 *>(sp.x);
+          double2 y = make_double2(0.0, 0.0);
+          if (staged) {
+            for (int e = e0; e < e1; ++e) {
+              const double av = s_val[e - te0];
+              const double2 u = __ldg(x2 + s_col[e - te0]);
+              y.x = fma(av, u.x, y.x);
+              y.y = fma(av, u.y, y.y);
+            }
+          } else {
+            for (int e = e0; e < e1; ++e) {
+              const double av = __ldg(va + e);
+              const double2 u = __ldg(x2 + __ldg(ci + e));
+              y.x = fma(av, u.x, y.x);
+              y.y = fma(av, u.y, y.y);
+            }
+          }
+          static_cast<double2 *>(sp.y)[r] = y;
+          E::acc2(a, r, y, acc);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  reduce_and_finalize<E, kSpmmThreads>(a, acc);
 }
 
 // ------------------------------------------------------------------ pack / unpack / reset
@@ -1523,6 +1662,78 @@ cudaError_t launch_vec(int op, const KArgs &a, int grid, cudaStream_t s) {
   return kOps[op].launch(a, grid, s);
 }
 int vec_blocks_per_sm(int op) { return (op >= 0 && op < OP_COUNT) ? kOps[op].occ() : 1; }
+
+namespace {
+// Dynamic shared memory of the fused SpMM: the staged CSR entries of a tile (kp <= 2).  The
+// reduction's static buffers come on top, so above 32 KB the kernel's limit is raised first.
+template <int KP, class E>
+cudaError_t dot_smem(int stage_cap, size_t *smem) {
+  *smem = KP <= 2 ? (size_t)stage_cap * (sizeof(double) + sizeof(int32_t)) : 0;
+  static size_t opened = 0;
+  if (*smem > 32 * 1024 && *smem > opened) {
+    cudaError_t e = cudaFuncSetAttribute(spmm_dot_kernel<KP, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)*smem);
+    if (e != cudaSuccess) return e;
+    opened = *smem;
+  }
+  return cudaSuccess;
+}
+template <int KP, class E>
+cudaError_t launch_dot_kp(const SpmmArgs &s, const KArgs &a, int grid, cudaStream_t st) {
+  size_t smem = 0;
+  cudaError_t e = dot_smem<KP, E>(s.stage_cap, &smem);
+  if (e != cudaSuccess) return e;
+  spmm_dot_kernel<KP, E><<<grid, kSpmmThreads, smem, st>>>(s, a);
+  return cudaGetLastError();
+}
+template <int KP, class E>
+int occ_dot_kp(int stage_cap) {
+  size_t smem = 0;
+  int nb = 0;
+  if (dot_smem<KP, E>(stage_cap, &smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_dot_kernel<KP, E>, kSpmmThreads, smem) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+template <class E>
+cudaError_t launch_dot_e(int kp, const SpmmArgs &s, const KArgs &a, int grid, cudaStream_t st) {
+  switch (kp) {
+    case 1: return launch_dot_kp<1, E>(s, a, grid, st);
+    case 2: return launch_dot_kp<2, E>(s, a, grid, st);
+    case 4: return launch_dot_kp<4, E>(s, a, grid, st);
+    case 8: return launch_dot_kp<8, E>(s, a, grid, st);
+    case 16: return launch_dot_kp<16, E>(s, a, grid, st);
+    case 32: return launch_dot_kp<32, E>(s, a, grid, st);
+    case 64: return launch_dot_kp<64, E>(s, a, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <class E>
+int occ_dot_e(int kp, int stage_cap) {
+  switch (kp) {
+    case 1: return occ_dot_kp<1, E>(stage_cap);
+    case 2: return occ_dot_kp<2, E>(stage_cap);
+    case 4: return occ_dot_kp<4, E>(stage_cap);
+    case 8: return occ_dot_kp<8, E>(stage_cap);
+    case 16: return occ_dot_kp<16, E>(stage_cap);
+    case 32: return occ_dot_kp<32, E>(stage_cap);
+    case 64: return occ_dot_kp<64, E>(stage_cap);
+    default: return 1;
+  }
+}
+}  // namespace
+
+cudaError_t launch_spmm_dot(int kp, int epi, const SpmmArgs &s, const KArgs &a, int grid, cudaStream_t st) {
+  if (epi == EPI_DELTA) return launch_dot_e<EpiDelta>(kp, s, a, grid, st);
+  if (epi == EPI_G1) return launch_dot_e<EpiG1>(kp, s, a, grid, st);
+  return cudaErrorInvalidValue;
+}
+int spmm_dot_blocks_per_sm(int kp, int epi, int stage_cap) {
+  if (epi == EPI_DELTA) return occ_dot_e<EpiDelta>(kp, stage_cap);
+  if (epi == EPI_G1) return occ_dot_e<EpiG1>(kp, stage_cap);
+  return 1;
+}
+const char *spmm_dot_name(int epi) { return epi == EPI_DELTA ? "spmm_delta" : epi == EPI_G1 ? "spmm_g1" : "?"; }
 
 cudaError_t launch_pack(const double *B, const double *X0, int ld, int ncols, const KArgs &a, cudaStream_t s) {
   pack_kernel<<<1024, 256, 0, s>>>(B, X0, ld, ncols, a);

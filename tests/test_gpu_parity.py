@@ -393,3 +393,32 @@ def test_jacobi_diagonal_matrix_one_iterate(bk, cuda):
         r, X = _gpu_solve(bk, cuda, A, B, tol=1e-12, maxit=10, variant=v, flags=2)
         assert np.all(r.iters == 1) and np.all(r.status == 0)
         np.testing.assert_allclose(X, B / d[:, None], rtol=1e-15)
+
+
+@pytest.mark.parametrize("variant", ["classical_merged", "precond_merged", "reordered_merged"])
+@pytest.mark.parametrize("k", [1, 2, 3, 8, 20])
+@pytest.mark.parametrize("kind", ["convdiff7_peclet", "perturbed27"])
+def test_fused_dots_match_separate_kernels(bk, cuda, variant, k, kind):
+    """The dot kernel that follows an SpMM taken into the SpMM's epilogue (BICGK_OPT_FUSED_DOTS)
+    gives the iterates of the separate kernels up to the summation order of those dots, and the
+    oracle's.  Forced on and off at every kp, so the fused one-lane-per-row kernel (kp <= 2) runs
+    with staged tiles (7-point stencil) and with tiles larger than the stage buffer (27-point
+    stencil, 256-row tiles of 6,912 entries)."""
+    torch = cuda
+    A = I.convdiff7(12, peclet=True) if kind == "convdiff7_peclet" else I.perturbed27(11, seed=5)
+    B = I.rhs(A.n, k, 4)
+    Bd = torch.from_numpy(B).cuda()
+    ro = oracle.solve(A, B, tol=0.0, maxit=6, variant=variant, flags=oracle.NO_STOP_TEST)
+    X = {}
+    with bk.Operator(A) as op:
+        for fz in (1, 2):
+            bk.set_option(op.handle, bk.OPT_FUSED_DOTS, fz)
+            r = op.solve(Bd, tol=0.0, maxit=6, variant=variant, flags=bk.FLAG_NO_STOP_TEST)
+            X[fz] = r.X.cpu().numpy()
+            assert np.all(_colerr(X[fz], ro.X) <= 1e-12)
+            np.testing.assert_allclose(r.hist[:7], ro.hist[:7], rtol=1e-10)
+        assert np.all(_colerr(X[2], X[1]) <= 1e-13)
+        r = op.solve(Bd, tol=1e-8, maxit=1000, variant=variant)  # option 2: fused
+        Xf = r.X.cpu().numpy()
+    rof = oracle.solve(A, B, tol=1e-8, maxit=1000, variant=variant)
+    _compare(r, Xf, rof)
