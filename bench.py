@@ -134,7 +134,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+                "sm_min_mhz": min(r[0] for r in rows), "reasons": reasons, "samples": len(rows)}
 
 
 def kernel_algorithmic(name: str, n: int, nnz: int, k: int, variant: str = "classical_merged"):
@@ -147,12 +147,14 @@ def kernel_algorithmic(name: str, n: int, nnz: int, k: int, variant: str = "clas
         f = 2.0 * nnz * k + (n * k if resid else 0.0)
         if name.startswith("spmm_delta"):   # epilogue dot (v, r^0): reads r^0
             b, f = b + vec, f + 2.0 * n * k
-        if name.startswith("spmm_g1"):      # epilogue dots (t,s), (t,t), (s,s)
+        if name.startswith(("spmm_g1", "spmm_phi_psi")):  # epilogue dots (t,s), (t,t)[, (s,s)]
             # s is the product's own x in Algorithm 2 (read once); Algorithm 5 multiplies s^ = M^-1 s
-            b, f = b + (vec if variant.startswith("precond") else 0.0), f + 6.0 * n * k
+            nd = 3 if name.startswith("spmm_g1") else 2
+            b, f = b + (vec if variant.startswith("precond") else 0.0), f + 2.0 * nd * n * k
         return b, f
     table = {  # reads, writes, FP64 flops per element (FMA = 2)
         "dot_delta": (2, 0, 2), "upd_s": (2, 1, 2), "merged_phi_psi_theta": (2, 0, 6),
+        "upd_s_theta": (2, 1, 4), "merged_phi_psi": (2, 0, 4),
         "merged_x_r_rho": (5, 2, 8), "upd_p": (3, 1, 4), "dot_phi": (2, 0, 2), "dot_psi": (1, 0, 2),
         "upd_x": (3, 1, 4), "upd_r": (2, 1, 2), "dot_rr": (1, 0, 2), "dot_rho": (2, 0, 2),
         "precond_copy_s": (1, 1, 0), "precond_copy_q": (1, 1, 0), "upd_that": (2, 1, 2),
@@ -174,7 +176,7 @@ KERNEL_SOURCES = {"spmm": ("bicgk_dev.cuh", "bicgk_spmm.cu"), "vec": ("bicgk_dev
 def kernel_source_kind(name: str) -> str:
     """Which sources a kernel class is compiled from: the SpMM kernels, or the streaming kernels
     (which also hold the SpMM with a dot epilogue)."""
-    plain_spmm = name.startswith("spmm") and not name.startswith(("spmm_delta", "spmm_g1"))
+    plain_spmm = name.startswith("spmm") and not name.startswith(("spmm_delta", "spmm_g1", "spmm_phi_psi"))
     return "spmm" if plain_spmm else "vec"
 
 
@@ -627,7 +629,7 @@ def main():
     # end to end through the C-ABI with pinned host buffers
     Bh = torch.from_numpy(B_host).pin_memory()
     Xh = torch.empty_like(Bh).pin_memory()
-    ms_e2e, its_e2e, _, _, _ = timed(args.variant, args.steps, 1, B=Bh, X=Xh)
+    ms_e2e, its_e2e, _, _, clocks_e2e = timed(args.variant, args.steps, 1, B=Bh, X=Xh, clocks=True)
     e2e_value = aggregate_rate(float(its_e2e), ms_e2e, pg, dev)
     nbytes = 8 * A.n * args.k
 
@@ -640,7 +642,9 @@ def main():
         "converged": conv_ok, "max_true_relres": relres,
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": "RHS-iterations/s", "h2d_bytes_per_step": nbytes,
+        "e2e": {"value": e2e_value, "unit": "RHS-iterations/s", "ms_per_step": ms_e2e / args.steps,
+                "iters_per_rhs": float(its_e2e) / (args.steps * args.k), "clocks": clocks_e2e,
+                "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes + 8 * args.k + 8 * args.k},
     }
 

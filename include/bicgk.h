@@ -245,12 +245,19 @@ enum bicgk_option {
   BICGK_OPT_RHS_GROUPS = 3,         /* 0: k >= 16 is solved as two column groups running
                                       concurrently on two internal streams (default); 1: one
                                       group.  Profiling mode always uses one group.            */
-  BICGK_OPT_FUSED_DOTS = 4          /* merged forms of Algorithms 2, 5 and 6: take the dot
+  BICGK_OPT_FUSED_DOTS = 4,         /* merged forms of Algorithms 2, 5 and 6: take the dot
                                       kernel that follows an SpMM in the listing (delta after
                                       v = A p; group 1 after t = A s, Algorithms 2 and 5) into
                                       the SpMM's epilogue.  0: when the solve runs as two column
                                       groups (default); 1: never; 2: always.  The iterates are
                                       the same up to the summation order of those dots.        */
+  BICGK_OPT_THETA_IN_S = 5          /* merged forms of Algorithms 2 and 5: take theta = (s, s)
+                                      of group 1 in the kernel that forms s = r - alpha v
+                                      (Algorithm 5: before s^ = M^-1 s), leaving phi = (t, s)
+                                      and psi = (t, t) to group 1.  0: for k >= 4, except the
+                                      merged classical form when its dots are folded into the
+                                      SpMM (default); 1: never; 2: always.  Same iterates up to
+                                      the summation order of theta.                            */
 };
 
 /*
@@ -281,7 +288,10 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value);
  *   status, true_relres (nullable) are host arrays of sum(k) entries, systems in order.
  *   mode BICGK_BATCH_GRAPH: one CUDA-graph launch with an independent branch (set-up,
  *   conditional WHILE loop, true residual) per system; BICGK_BATCH_LOOP: bicgk_solve on each
- *   system in turn (the per-system launch loop).  Residual histories are not returned.
+ *   system in turn (the per-system launch loop).  Both modes run every system as one column
+ *   group without dot epilogues (BICGK_OPT_RHS_GROUPS = 1, BICGK_OPT_FUSED_DOTS = 1) and the
+ *   same kernel sequence, so their results are bitwise equal.  Residual histories are not
+ *   returned.
  * bicgk_batch_last_launches: kernels the last bicgk_batch_solve launched.
  */
 typedef struct bicgk_batch_s *bicgk_batch;

@@ -223,7 +223,7 @@ def solve(handle: int, B, X0=None, tol: float = 1e-8, maxit: int = 1000, variant
     return SolveResult(X, iters, status, hist, trr)
 
 
-OPT_VEC_BLOCKS_PER_SM, OPT_SPMM_BLOCKS_PER_SM, OPT_RHS_GROUPS, OPT_FUSED_DOTS = 1, 2, 3, 4
+OPT_VEC_BLOCKS_PER_SM, OPT_SPMM_BLOCKS_PER_SM, OPT_RHS_GROUPS, OPT_FUSED_DOTS, OPT_THETA_IN_S = 1, 2, 3, 4, 5
 
 
 def set_option(handle: int, option: int, value: int) -> None:

@@ -72,9 +72,14 @@ Seq make_inner32_seq() {
 
 // Kernel sequences of the twelve forms (one Step = one kernel launch).  `jacobi`: M = diag(A)
 // instead of the identity copy for the forms that apply M^-1 (Algorithms 5, 6, 7).
-// `fuse`: the merged forms take the dot kernel that follows an SpMM into the SpMM's epilogue
-// (delta after v = A p, group 1 after t = A s).
-Seq make_seq(int variant, bool jacobi = false, bool fuse = false) {
+// `opts` (SEQ_* bits): SEQ_FUSE, the merged forms take the dot kernel that follows an SpMM into
+// the SpMM's epilogue (delta after v = A p, group 1 after t = A s); SEQ_THETA_S, the merged
+// forms of Algorithms 2 and 5 take theta = (s, s) in the s update instead of in group 1.
+enum SeqOpt : int { SEQ_FUSE = 1, SEQ_THETA_S = 2 };
+Seq make_seq(int variant, bool jacobi = false, int opts = 0) {
+  const bool fuse = opts & SEQ_FUSE, theta_s = opts & SEQ_THETA_S;
+  const int op_s = theta_s ? OP_UPD_S_TH : OP_UPD_S, op_g1 = theta_s ? OP_G1_PP : OP_G1;
+  const int epi_g1 = theta_s ? EPI_G1_PP : EPI_G1;
   Seq q;
   // y = A x followed by the dot kernel `op` of the listing, fused when `fuse`
   auto spmm_then = [](int x, int y, int op, int epi, bool fuse, std::vector<Step> &body) {
@@ -91,8 +96,8 @@ Seq make_seq(int variant, bool jacobi = false, bool fuse = false) {
     case BICGK_CLASSICAL_MERGED:  // Algorithm 2
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_C)};
       spmm_then(V_P, V_V, OP_DELTA, EPI_DELTA, fuse_delta, q.body);
-      q.body.push_back(vec(OP_UPD_S));
-      spmm_then(V_S, V_T, OP_G1, EPI_G1, fuse_g1, q.body);
+      q.body.push_back(vec(op_s));
+      spmm_then(V_S, V_T, op_g1, epi_g1, fuse_g1, q.body);
       q.body.push_back(vec(OP_G3));
       q.body.push_back(vec(OP_UPD_P));
       break;
@@ -132,9 +137,9 @@ Seq make_seq(int variant, bool jacobi = false, bool fuse = false) {
       q.setup = {resid(V_X, V_R, V_B), vec(OP_SETUP_C)};
       q.body.push_back(vec(OP_PREC_P_Q));
       spmm_then(V_Q, V_V, OP_DELTA, EPI_DELTA, fuse_delta, q.body);
-      q.body.push_back(vec(OP_UPD_S));
+      q.body.push_back(vec(op_s));
       q.body.push_back(vec(OP_PREC_S_Y));
-      spmm_then(V_Y, V_T, OP_G1, EPI_G1, fuse_g1, q.body);
+      spmm_then(V_Y, V_T, op_g1, epi_g1, fuse_g1, q.body);
       for (int op : {OP5_RRHO, OP5_UPD_X, OP_UPD_P}) q.body.push_back(vec(op));
       break;
     case BICGK_PRECOND_PLAIN:
@@ -242,6 +247,7 @@ struct bicgk_op_s {
   int opt_spmm_blocks = 0;
   int opt_groups = 0;
   int opt_fused = 0;  // BICGK_OPT_FUSED_DOTS
+  int opt_theta = 0;  // BICGK_OPT_THETA_IN_S
   // launch shapes chosen by the batch autotuner (0 = the per-SM rule above)
   int grid_vec_abs = 0;
   int grid_spmm_abs = 0;
@@ -496,8 +502,24 @@ bool fuse_dots(bicgk_op A, int k) {
   return A->opt_groups != 1 && k >= kSplitMinK;
 }
 
-int build_graph(bicgk_op A, Workspace &W, int variant, bool jacobi, bool fuse, GraphEntry *ge) {
-  return build_graph_seq(A, W, make_seq(variant, jacobi, fuse), nullptr, ge, jacobi ? A->d_invdiag : nullptr);
+// Whether theta = (s, s) of Algorithms 2 and 5 is taken in the s update (BICGK_OPT_THETA_IN_S).
+// Automatic, from fixed-iteration timings at 128^3 (7-point stencil): from k = 4 on, where the
+// s update stays bandwidth-bound with the extra FMA and group 1 sheds a third of its FP64 work
+// (0.5-2 % per iteration at k = 4..16, 3 % at k = 32 without the dot epilogues), except for the
+// classical form with the epilogues, where it gained nothing at k = 32 and cost 1 % at k = 16.
+// At k = 1 the reduction added to the s update costs more than it saves.
+bool theta_in_s(bicgk_op A, int k, int variant) {
+  if (A->opt_theta == 1) return false;
+  if (A->opt_theta == 2) return true;
+  return k >= 4 && !(variant == BICGK_CLASSICAL_MERGED && fuse_dots(A, k));
+}
+
+int seq_opts(bicgk_op A, int k, int variant) {
+  return (fuse_dots(A, k) ? SEQ_FUSE : 0) | (theta_in_s(A, k, variant) ? SEQ_THETA_S : 0);
+}
+
+int build_graph(bicgk_op A, Workspace &W, int variant, bool jacobi, int opts, GraphEntry *ge) {
+  return build_graph_seq(A, W, make_seq(variant, jacobi, opts), nullptr, ge, jacobi ? A->d_invdiag : nullptr);
 }
 
 // What a form needs beyond the operator: the transposed copy (Algorithm 3), the Jacobi diagonal.
@@ -566,8 +588,8 @@ int run_profiled_seq(bicgk_op A, Workspace &W, const Seq &q, const KArgs &a, cud
   return run_list(q.fin);
 }
 
-int run_profiled(bicgk_op A, Workspace &W, int variant, bool jacobi, bool fuse, const KArgs &a, cudaStream_t s) {
-  return run_profiled_seq(A, W, make_seq(variant, jacobi, fuse), a, s);
+int run_profiled(bicgk_op A, Workspace &W, int variant, bool jacobi, int opts, const KArgs &a, cudaStream_t s) {
+  return run_profiled_seq(A, W, make_seq(variant, jacobi, opts), a, s);
 }
 
 }  // namespace
@@ -751,8 +773,8 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
   if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   const bool jacobi = (flags & BICGK_FLAG_JACOBI) != 0;
-  const bool fuse = fuse_dots(A, k);
-  const int gkey = variant + 100 * (jacobi ? 1 : 0) + 1000 * (fuse ? 1 : 0);
+  const int opts = seq_opts(A, k, variant);
+  const int gkey = variant + 100 * (jacobi ? 1 : 0) + 1000 * opts;
   int rc0 = ensure_variant_data(A, variant, jacobi, s);
   if (rc0) return rc0;
   // columns are independent: split k >= kSplitMinK into two groups solved concurrently, so that
@@ -767,7 +789,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     if ((rc = ensure_workspace(A, A->ws[g], kpg))) return rc;
     if ((rc = ensure_hist(A->ws[g], (int64_t)(maxit + 1) * kpg))) return rc;
   }
-  const Seq q = make_seq(variant, jacobi, fuse);
+  const Seq q = make_seq(variant, jacobi, opts);
   // inputs
   const double *dB = B, *dX0 = X0;
   double *dX = X;
@@ -803,12 +825,12 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     CK(launch_pack(dB + c0[g], dX0 ? dX0 + c0[g] : nullptr, k, kg, a0, gs));
     launches += 2;  // reset, pack
     if (A->profiling) {
-      if ((rc = run_profiled(A, W, variant, jacobi, fuse, a0, gs))) return rc;
+      if ((rc = run_profiled(A, W, variant, jacobi, opts, a0, gs))) return rc;
     } else {
       auto it = W.graphs.find(gkey);
       if (it == W.graphs.end()) {
         GraphEntry ge;
-        if ((rc = build_graph(A, W, variant, jacobi, fuse, &ge))) {
+        if ((rc = build_graph(A, W, variant, jacobi, opts, &ge))) {
           if (ge.exec) cudaGraphExecDestroy(ge.exec);
           if (ge.graph) cudaGraphDestroy(ge.graph);
           return rc;
@@ -1055,6 +1077,10 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value) {
       if (value < 0 || value > 2) return BICGK_E_INVALID;
       A->opt_fused = (int)value;
       break;
+    case BICGK_OPT_THETA_IN_S:
+      if (value < 0 || value > 2) return BICGK_E_INVALID;
+      A->opt_theta = (int)value;
+      break;
     default:
       return BICGK_E_INVALID;
   }
@@ -1162,7 +1188,6 @@ int batch_ensure(bicgk_batch b, int32_t maxit) {
 }
 
 int batch_build_graph(bicgk_batch b, int variant, bool jacobi, GraphEntry *ge) {
-  const Seq q = make_seq(variant, jacobi);
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   ge->graph = g;
@@ -1171,6 +1196,7 @@ int batch_build_graph(bicgk_batch b, int variant, bool jacobi, GraphEntry *ge) {
   for (int i = 0; i < b->nsys; ++i) {
     bicgk_op A = b->ops[i];
     Workspace &W = b->ws[i];
+    const Seq q = make_seq(variant, jacobi, seq_opts(A, b->k[i], variant));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
     const KArgs a = make_args(A, W, 1, h, nullptr, jacobi ? A->d_invdiag : nullptr);
@@ -1249,6 +1275,12 @@ int bicgk_batch_create(bicgk_batch *out, int32_t nsys, const int64_t *n_rows, co
   int rc = BICGK_OK;
   for (int i = 0; i < nsys && rc == BICGK_OK; ++i)
     rc = bicgk_csr_create(&b->ops[i], n_rows[i], nnz[i], rowptr[i], colidx[i], vals[i], mem, stream);
+  // each system runs as one column group without dot epilogues, in the graph and in the launch
+  // loop alike (the loop calls bicgk_solve with these operators)
+  for (int i = 0; i < nsys && rc == BICGK_OK; ++i) {
+    b->ops[i]->opt_groups = 1;
+    b->ops[i]->opt_fused = 1;
+  }
   cudaError_t e = cudaSuccess;
   if (rc == BICGK_OK) {
     if ((e = cudaMalloc(&b->d_ctl, sizeof(Ctl) * nsys)) != cudaSuccess ||
@@ -1439,8 +1471,8 @@ int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const
   CK(cudaMemcpyAsync(b->h_sc, b->d_sc, sizeof(double) * S_NSLOT * kMaxKp * b->nsys, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(Ctl) * b->nsys, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  const Seq q = make_seq(variant, jacobi);
   for (int i = 0; i < b->nsys; ++i) {
+    const Seq q = make_seq(variant, jacobi, seq_opts(b->ops[i], b->k[i], variant));
     const int *fl = b->h_fl + (size_t)i * F_NFLAG * kMaxKp;
     const double *sc = b->h_sc + (size_t)i * S_NSLOT * kMaxKp;
     for (int c = 0; c < b->k[i]; ++c) {
@@ -1538,6 +1570,8 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
   A.d_col = const_cast<int32_t *>(colidx);
   A.d_val = const_cast<double *>(vals);
   A.stage_cap = 0;  // the k <= 2 SpMM reads CSR entries from global memory (same arithmetic)
+  A.opt_groups = 1;  // one column group, no dot epilogues: bicgk_solve's sequence for k < 16
+  A.opt_fused = 1;
   Workspace W;
   W.kp = kp;
   W.vstride = vstride;
@@ -1560,7 +1594,7 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
   const KArgs a = make_args(&A, W, 0, cudaGraphConditionalHandle{});
   CK(launch_reset(a, hist_len, s));        // history = NaN, per-column scalars and flags = 0
   CK(launch_pack(B, X0, k, k, a, s));      // B and X0 in, padding columns and pad elements = 0
-  const Seq q = make_seq(variant);
+  const Seq q = make_seq(variant, false, seq_opts(&A, k, variant));
   Ctl poll;
   auto run = [&](const std::vector<Step> &steps) -> int {
     for (const Step &st : steps) CK(launch_step(&A, st, a, s));

@@ -103,6 +103,9 @@ enum Op : int {
   // Algorithm 3 (Improved BiCGStab)
   OP3_SETUP, OP3_SIG0, OP3_L1, OP3_L2, OP3_L3, OP3_Z, OP3_V, OP3_S, OP3_T, OP3_D_R0S, OP3_D_R0Q, OP3_D_F0S,
   OP3_D_F0T, OP3_D_ST, OP3_D_TT, OP3_D_SS, OP3_X,
+  // Algorithms 2 and 5 with theta = (s, s) taken where s is formed: the s update with that dot,
+  // and group 1 reduced to phi = (t, s), psi = (t, t)
+  OP_UPD_S_TH, OP_G1_PP,
   OP_COUNT
 };
 
@@ -136,6 +139,7 @@ int spmm_blocks_per_sm(int kp, int mode, int stage_cap);
 enum SpmmEpi : int {
   EPI_DELTA = 0,  // delta = (v, r^0) after v = A p: the dot kernel OP_DELTA
   EPI_G1 = 1,     // (t, s), (t, t), (s, s) after t = A s: group 1 of Algorithm 2 (OP_G1)
+  EPI_G1_PP = 2,  // (t, s), (t, t) after t = A s, theta from OP_UPD_S_TH (OP_G1_PP)
 };
 cudaError_t launch_spmm_dot(int kp, int epi, const SpmmArgs &s, const KArgs &a, int grid, cudaStream_t st);
 int spmm_dot_blocks_per_sm(int kp, int epi, int stage_cap);  // occupancy of the fused kernel

@@ -126,7 +126,7 @@ enum Fin : int {
   FIN_NONE = 0, FIN_SETUP, FIN_RW0, FIN_DELTA, FIN_G1, FIN_RHO, FIN_STORE_D0, FIN_STORE_D1, FIN_STORE_D2,
   FIN_PSI, FIN_RR, FIN_R4_MERGED, FIN_R4_PLAIN, FIN_PG1_MERGED, FIN_PG1_PLAIN, FIN_PG3_MERGED,
   FIN_PG3_PLAIN, FIN_TRUE, FIN_IR_SETUP, FIN_IR_RESID, FIN_STORE_D3, FIN_STORE_D4, FIN_STORE_D5, FIN_I_START,
-  FIN_I7_MERGED, FIN_I7_PLAIN
+  FIN_I7_MERGED, FIN_I7_PLAIN, FIN_G1_TH
 };
 enum Ctl_ : int { CTL_NONE = 0, CTL_START = 1, CTL_END_ITER = 2, CTL_OUTER = 3 };
 
@@ -155,6 +155,25 @@ __device__ bool i3_next(const KArgs &a, int c) {
   SC(S_TAU, c) = tau1;
   SC(S_AOLD, c) = al1;
   return true;
+}
+
+// Algorithm 2 group 1 for column c: phi = (t,s), psi = (t,t), theta = (s,s); omega = phi/psi;
+// stop test on (r_{j+1}, r_{j+1}) = theta - omega*phi.
+__device__ void g1_rule(const KArgs &a, int c, double phi, double psi, double th) {
+  Ctl *ctl = a.ctl;
+  FL(F_XUPD, c) = 0;
+  if (!FL(F_ACT, c)) return;
+  if (!fin1(phi) || !fin1(psi) || !fin1(th)) { col_stop(a, c, ST_NONFINITE); return; }
+  const double om = psi == 0.0 ? 0.0 : __ddiv_rn(phi, psi);
+  if (!fin1(om)) { col_stop(a, c, ST_NONFINITE); return; }
+  const int j = ctl->iter;
+  SC(S_OMEGA, c) = om;
+  FL(F_XUPD, c) = 1;
+  FL(F_ITERS, c) = j + 1;
+  const double est = sub_rn(th, __dmul_rn(om, phi));
+  ctl->hist[(int64_t)(j + 1) * a.kp + c] = hist_value(est);
+  if (!fin1(est)) col_stop(a, c, ST_NONFINITE);
+  else if (!(ctl->flags & 1) && est < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
 }
 
 // Column c, executed by thread c of the last block.  s[d*kp + c] = dot d of column c.
@@ -216,22 +235,10 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
     if (!fin1(al)) { col_stop(a, c, ST_NONFINITE); return; }
     SC(S_ALPHA, c) = al;
   } else if constexpr (FIN == FIN_G1) {
-    // Algorithm 2 group 1: phi = (t,s), psi = (t,t), theta = (s,s); omega = phi/psi;
-    // stop test on (r_{j+1}, r_{j+1}) = theta - omega*phi
-    FL(F_XUPD, c) = 0;
-    if (!FL(F_ACT, c)) return;
-    const double phi = s[0 * kp + c], psi = s[1 * kp + c], th = s[2 * kp + c];
-    if (!fin1(phi) || !fin1(psi) || !fin1(th)) { col_stop(a, c, ST_NONFINITE); return; }
-    const double om = psi == 0.0 ? 0.0 : __ddiv_rn(phi, psi);
-    if (!fin1(om)) { col_stop(a, c, ST_NONFINITE); return; }
-    const int j = ctl->iter;
-    SC(S_OMEGA, c) = om;
-    FL(F_XUPD, c) = 1;
-    FL(F_ITERS, c) = j + 1;
-    const double est = sub_rn(th, __dmul_rn(om, phi));
-    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(est);
-    if (!fin1(est)) col_stop(a, c, ST_NONFINITE);
-    else if (!nostop && est < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
+    g1_rule(a, c, s[0 * kp + c], s[1 * kp + c], s[2 * kp + c]);
+  } else if constexpr (FIN == FIN_G1_TH) {
+    // the same rule with theta = (s,s) stored by the s update (OP_UPD_S_TH)
+    g1_rule(a, c, s[0 * kp + c], s[1 * kp + c], SC(S_D0, c));
   } else if constexpr (FIN == FIN_RHO) {
     // rho_{j+1} = (r_{j+1}, r_0), beta_j = (rho_{j+1}/rho_j)(alpha_j/omega_j)
     if (!FL(F_ACT, c)) return;
@@ -541,6 +548,25 @@ struct OpDef<OP_G1> {  // phi = (t,s), psi = (t,t), theta = (s,s)
     dot_acc(acc[0], v[0], v[1]);
     dot_acc(acc[1], v[0], v[0]);
     dot_acc(acc[2], v[1], v[1]);
+  }
+};
+template <>
+struct OpDef<OP_UPD_S_TH> {  // s_j = r_j - alpha_j v_j with theta = (s_j, s_j), stored for group 1
+  static constexpr int ND = 1, FIN = FIN_STORE_D0, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_R), i); v[1] = ld2(V(V_V), i); }
+  __device__ static void comp(const KArgs &a, int64_t i, const double2 (&v)[NL], const Sc2 &s, double2 (&acc)[ND]) {
+    const double2 sv = fma2(neg2(s.al), v[1], v[0]);
+    st2(V(V_S), i, sv);
+    dot_acc(acc[0], sv, sv);
+  }
+};
+template <>
+struct OpDef<OP_G1_PP> {  // phi = (t,s), psi = (t,t); theta from OP_UPD_S_TH
+  static constexpr int ND = 2, FIN = FIN_G1_TH, CTL = CTL_NONE, NL = 2;
+  __device__ static void load(const KArgs &a, int64_t i, double2 (&v)[NL]) { v[0] = ld2(V(V_T), i); v[1] = ld2(V(V_S), i); }
+  __device__ static void comp(const KArgs &, int64_t, const double2 (&v)[NL], const Sc2 &, double2 (&acc)[ND]) {
+    dot_acc(acc[0], v[0], v[1]);
+    dot_acc(acc[1], v[0], v[0]);
   }
 };
 template <>
@@ -1386,6 +1412,18 @@ struct EpiG1 {  // phi = (t,s), psi = (t,t), theta = (s,s): OP_G1
   }
 };
 
+struct EpiG1PP {  // phi = (t,s), psi = (t,t), theta from the s update: OP_G1_PP
+  static constexpr int ND = 2, FIN = FIN_G1_TH, CTL = CTL_NONE;
+  __device__ static void acc2(const KArgs &a, int64_t o, double2 t, double2 (&acc)[ND]) {
+    dot_acc(acc[0], t, ld2(a.v[V_S], o));
+    dot_acc(acc[1], t, t);
+  }
+  __device__ static void acc1(const KArgs &a, int64_t o, double t, double2 (&acc)[ND]) {
+    acc[0].x = fma(t, a.v[V_S][o], acc[0].x);
+    acc[1].x = fma(t, t, acc[1].x);
+  }
+};
+
 template <int KP, class E>
 __global__ void __launch_bounds__(kSpmmThreads) spmm_dot_kernel(const SpmmArgs sp, const KArgs a) {
   double2 acc[E::ND];
@@ -1645,6 +1683,8 @@ const OpInfo kOps[OP_COUNT] = {
     OPI(OP3_D_TT, "dot_kappa", 1, 0),
     OPI(OP3_D_SS, "dot_nu", 1, 0),
     OPI(OP3_X, "upd_x", 3, 1),
+    OPI(OP_UPD_S_TH, "upd_s_theta", 2, 1),
+    OPI(OP_G1_PP, "merged_phi_psi", 2, 0),
 };
 #undef OPI
 
@@ -1726,14 +1766,18 @@ int occ_dot_e(int kp, int stage_cap) {
 cudaError_t launch_spmm_dot(int kp, int epi, const SpmmArgs &s, const KArgs &a, int grid, cudaStream_t st) {
   if (epi == EPI_DELTA) return launch_dot_e<EpiDelta>(kp, s, a, grid, st);
   if (epi == EPI_G1) return launch_dot_e<EpiG1>(kp, s, a, grid, st);
+  if (epi == EPI_G1_PP) return launch_dot_e<EpiG1PP>(kp, s, a, grid, st);
   return cudaErrorInvalidValue;
 }
 int spmm_dot_blocks_per_sm(int kp, int epi, int stage_cap) {
   if (epi == EPI_DELTA) return occ_dot_e<EpiDelta>(kp, stage_cap);
   if (epi == EPI_G1) return occ_dot_e<EpiG1>(kp, stage_cap);
+  if (epi == EPI_G1_PP) return occ_dot_e<EpiG1PP>(kp, stage_cap);
   return 1;
 }
-const char *spmm_dot_name(int epi) { return epi == EPI_DELTA ? "spmm_delta" : epi == EPI_G1 ? "spmm_g1" : "?"; }
+const char *spmm_dot_name(int epi) {
+  return epi == EPI_DELTA ? "spmm_delta" : epi == EPI_G1 ? "spmm_g1" : epi == EPI_G1_PP ? "spmm_phi_psi" : "?";
+}
 
 cudaError_t launch_pack(const double *B, const double *X0, int ld, int ncols, const KArgs &a, cudaStream_t s) {
   pack_kernel<<<1024, 256, 0, s>>>(B, X0, ld, ncols, a);

@@ -399,11 +399,12 @@ def test_jacobi_diagonal_matrix_one_iterate(bk, cuda):
 @pytest.mark.parametrize("k", [1, 2, 3, 8, 20])
 @pytest.mark.parametrize("kind", ["convdiff7_peclet", "perturbed27"])
 def test_fused_dots_match_separate_kernels(bk, cuda, variant, k, kind):
-    """The dot kernel that follows an SpMM taken into the SpMM's epilogue (BICGK_OPT_FUSED_DOTS)
-    gives the iterates of the separate kernels up to the summation order of those dots, and the
-    oracle's.  Forced on and off at every kp, so the fused one-lane-per-row kernel (kp <= 2) runs
-    with staged tiles (7-point stencil) and with tiles larger than the stage buffer (27-point
-    stencil, 256-row tiles of 6,912 entries)."""
+    """The dot kernel that follows an SpMM taken into the SpMM's epilogue (BICGK_OPT_FUSED_DOTS),
+    and theta = (s, s) taken in the s update (BICGK_OPT_THETA_IN_S), give the iterates of the
+    separate kernels up to the summation order of those dots, and the oracle's.  Each forced on
+    and off at every kp, so the fused one-lane-per-row kernel (kp <= 2) runs with staged tiles
+    (7-point stencil) and with tiles larger than the stage buffer (27-point stencil, 256-row
+    tiles of 6,912 entries)."""
     torch = cuda
     A = I.convdiff7(12, peclet=True) if kind == "convdiff7_peclet" else I.perturbed27(11, seed=5)
     B = I.rhs(A.n, k, 4)
@@ -411,14 +412,15 @@ def test_fused_dots_match_separate_kernels(bk, cuda, variant, k, kind):
     ro = oracle.solve(A, B, tol=0.0, maxit=6, variant=variant, flags=oracle.NO_STOP_TEST)
     X = {}
     with bk.Operator(A) as op:
-        for fz in (1, 2):
+        for fz, th in ((1, 1), (2, 1), (1, 2), (2, 2)):
             bk.set_option(op.handle, bk.OPT_FUSED_DOTS, fz)
+            bk.set_option(op.handle, bk.OPT_THETA_IN_S, th)
             r = op.solve(Bd, tol=0.0, maxit=6, variant=variant, flags=bk.FLAG_NO_STOP_TEST)
-            X[fz] = r.X.cpu().numpy()
-            assert np.all(_colerr(X[fz], ro.X) <= 1e-12)
+            X[fz, th] = r.X.cpu().numpy()
+            assert np.all(_colerr(X[fz, th], ro.X) <= 1e-12), (fz, th)
             np.testing.assert_allclose(r.hist[:7], ro.hist[:7], rtol=1e-10)
-        assert np.all(_colerr(X[2], X[1]) <= 1e-13)
-        r = op.solve(Bd, tol=1e-8, maxit=1000, variant=variant)  # option 2: fused
+            assert np.all(_colerr(X[fz, th], X[1, 1]) <= 1e-13), (fz, th)
+        r = op.solve(Bd, tol=1e-8, maxit=1000, variant=variant)  # both forced on
         Xf = r.X.cpu().numpy()
     rof = oracle.solve(A, B, tol=1e-8, maxit=1000, variant=variant)
     _compare(r, Xf, rof)
