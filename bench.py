@@ -401,7 +401,7 @@ TABLE2_COPIES = {"classical": 0, "improved": 0, "pipelined": 0, "precond": 2, "r
 
 def fused_passes_saved(variant: str, k: int) -> int:
     """Vector passes per iteration that the dot epilogues of the SpMM save (the library fuses when
-    a solve runs as two column groups, k >= 16): the dot kernel after v = A p re-reads v; the one
+    a solve runs as concurrent column groups, k >= 16): the dot kernel after v = A p re-reads v; the one
     after t = A s re-reads t and s, and s is the product's own x in Algorithm 2 (in Algorithm 5 the
     product reads s^ = M^-1 s, so the epilogue still reads s)."""
     if k < 16:
@@ -612,6 +612,7 @@ def main():
 
     # headline: device-resident inputs
     ms, its, launches, results, clocks = timed(args.variant, args.steps, args.warmup, clocks=not args.minimal)
+    groups = bicgk.last_stats(op.handle)["groups"]
     value = aggregate_rate(float(its), ms, pg, dev)
     ms = max_over_ranks(ms, pg, dev)
     last = results[-1]
@@ -632,18 +633,30 @@ def main():
     ms_e2e, its_e2e, _, _, clocks_e2e = timed(args.variant, args.steps, 1, B=Bh, X=Xh, clocks=True)
     e2e_value = aggregate_rate(float(its_e2e), ms_e2e, pg, dev)
     nbytes = 8 * A.n * args.k
+    # the host link as this process sees it: one plain pinned copy each way (CUDA events)
+    link = {}
+    for name, dst, src in (("h2d_gbs", Xd, Bh), ("d2h_gbs", Xh, Bd)):
+        dst.copy_(src, non_blocking=True)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        link[name] = 3 * nbytes / (c0.elapsed_time(c1) / 1e3) / 1e9
 
     out = {
         "metric": "RHS-iterations/s", "value": value, "unit": "RHS-iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args, A),
-        "iters_per_rhs": float(its) / (args.steps * args.k),
+        "iters_per_rhs": float(its) / (args.steps * args.k), "rhs_groups": groups,
         "converged": conv_ok, "max_true_relres": relres,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "RHS-iterations/s", "ms_per_step": ms_e2e / args.steps,
                 "iters_per_rhs": float(its_e2e) / (args.steps * args.k), "clocks": clocks_e2e,
+                "pinned_copy_gbs": link,
                 "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes + 8 * args.k + 8 * args.k},
     }
@@ -653,12 +666,12 @@ def main():
         plain = args.variant.replace("merged", "plain")
         if plain != args.variant:
             msp, itsp, _, _, _ = timed(plain, args.steps, 1)
+            groups_p = bicgk.last_stats(op.handle)["groups"]
             vp = aggregate_rate(float(itsp), msp, pg, dev)
             msp = max_over_ranks(msp, pg, dev)
-            groups = 2 if args.k >= 16 else 1
             hbm, _ = hbm_peak()
             gm = solve_gbs(A, args.k, args.variant, its, ms, groups)
-            gp = solve_gbs(A, args.k, plain, itsp, msp, groups)
+            gp = solve_gbs(A, args.k, plain, itsp, msp, groups_p)
             out["hbm"] = {"unit": "GB/s", "peak_gbs": hbm, "merged_gbs": gm, "merged_frac": gm / hbm,
                           "plain_gbs": gp, "plain_frac": gp / hbm,
                           "bytes": "algorithmic bytes of the useful column-iterations (products: x, y and the "

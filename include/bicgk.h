@@ -242,22 +242,28 @@ enum bicgk_option {
                                       default: the occupancy maximum, 2)                      */
   BICGK_OPT_SPMM_BLOCKS_PER_SM = 2, /* blocks of 256 threads per SM for the SpMM (0..32; default:
                                       the occupancy maximum)                                   */
-  BICGK_OPT_RHS_GROUPS = 3,         /* 0: k >= 16 is solved as two column groups running
-                                      concurrently on two internal streams (default); 1: one
-                                      group.  Profiling mode always uses one group.            */
+  BICGK_OPT_RHS_GROUPS = 3,         /* 0 (default): k >= 16 is solved as two column groups
+                                      running concurrently on internal streams, k >= 32 as four;
+                                      1: one group; 2..4: that many groups (at most k).
+                                      Profiling mode always runs one group.                    */
   BICGK_OPT_FUSED_DOTS = 4,         /* merged forms of Algorithms 2, 5 and 6: take the dot
                                       kernel that follows an SpMM in the listing (delta after
                                       v = A p; group 1 after t = A s, Algorithms 2 and 5) into
-                                      the SpMM's epilogue.  0: when the solve runs as two column
-                                      groups (default); 1: never; 2: always.  The iterates are
+                                      the SpMM's epilogue.  0: when the solve runs as two or
+                                      more column groups (default); 1: never; 2: always.  The iterates are
                                       the same up to the summation order of those dots.        */
-  BICGK_OPT_THETA_IN_S = 5          /* merged forms of Algorithms 2 and 5: take theta = (s, s)
+  BICGK_OPT_THETA_IN_S = 5,         /* merged forms of Algorithms 2 and 5: take theta = (s, s)
                                       of group 1 in the kernel that forms s = r - alpha v
                                       (Algorithm 5: before s^ = M^-1 s), leaving phi = (t, s)
                                       and psi = (t, t) to group 1.  0: for k >= 4, except the
                                       merged classical form when its dots are folded into the
-                                      SpMM (default); 1: never; 2: always.  Same iterates up to
-                                      the summation order of theta.                            */
+                                      SpMM of two column groups (default); 1: never; 2: always.
+                                      Same iterates up to the summation order of theta.        */
+  BICGK_OPT_HOST_ZERO_COPY = 6      /* host calls (BICGK_MEM_HOST) whose B, X (and X0) are all
+                                      page-locked: 0 (default): the kernels read B and write X
+                                      in place through their mapped device addresses, group by
+                                      group, overlapping the transfer with the solve; 1: copy
+                                      through a device staging block as for pageable memory.   */
 };
 
 /*
@@ -335,6 +341,12 @@ int bicgk_kernel_times(bicgk_op A, int32_t max_n, int32_t *n_out, const char **n
  * number of kernels one iteration of the loop launches.
  */
 int bicgk_last_stats(bicgk_op A, int32_t *loop_iters, int64_t *kernel_launches, int32_t *kernels_per_iter);
+
+/*
+ * Column groups the last bicgk_solve() ran concurrently (1..4; BICGK_OPT_RHS_GROUPS).  Returns
+ * BICGK_E_INVALID for a null argument.
+ */
+int bicgk_last_groups(bicgk_op A, int32_t *groups);
 
 /* Library build identification ("bicgk <version> sm_103a"). */
 const char *bicgk_version(void);

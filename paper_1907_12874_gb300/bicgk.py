@@ -88,10 +88,11 @@ def _load():
             lib.bicgk_kernel_times.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_char_p),
                                                ctypes.POINTER(i64), ctypes.POINTER(dbl)]
             lib.bicgk_last_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+            lib.bicgk_last_groups.argtypes = [vp, ctypes.POINTER(i32)]
             for f in ("bicgk_csr_create", "bicgk_spmm", "bicgk_spmm_f32", "bicgk_solve", "bicgk_solve_mixed", "bicgk_op_destroy",
                       "bicgk_set_profiling",
                       "bicgk_set_option",
-                      "bicgk_kernel_times", "bicgk_last_stats"):
+                      "bicgk_kernel_times", "bicgk_last_stats", "bicgk_last_groups"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -223,7 +224,8 @@ def solve(handle: int, B, X0=None, tol: float = 1e-8, maxit: int = 1000, variant
     return SolveResult(X, iters, status, hist, trr)
 
 
-OPT_VEC_BLOCKS_PER_SM, OPT_SPMM_BLOCKS_PER_SM, OPT_RHS_GROUPS, OPT_FUSED_DOTS, OPT_THETA_IN_S = 1, 2, 3, 4, 5
+(OPT_VEC_BLOCKS_PER_SM, OPT_SPMM_BLOCKS_PER_SM, OPT_RHS_GROUPS, OPT_FUSED_DOTS, OPT_THETA_IN_S,
+ OPT_HOST_ZERO_COPY) = 1, 2, 3, 4, 5, 6
 
 
 def set_option(handle: int, option: int, value: int) -> None:
@@ -292,7 +294,9 @@ def last_stats(handle: int) -> dict:
     it, ln, kpi = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
     _check(_load().bicgk_last_stats(ctypes.c_void_p(handle), ctypes.byref(it), ctypes.byref(ln), ctypes.byref(kpi)),
            "bicgk_last_stats")
-    return {"loop_iters": it.value, "kernel_launches": ln.value, "kernels_per_iter": kpi.value}
+    ng = ctypes.c_int32()
+    _check(_load().bicgk_last_groups(ctypes.c_void_p(handle), ctypes.byref(ng)), "bicgk_last_groups")
+    return {"loop_iters": it.value, "kernel_launches": ln.value, "kernels_per_iter": kpi.value, "groups": ng.value}
 
 
 class Operator:

@@ -193,7 +193,7 @@ struct ProfEntry {
   double ms = 0.0;
 };
 
-constexpr int kMaxGroups = 2;     // column groups solved concurrently
+constexpr int kMaxGroups = 4;     // column groups solved concurrently (at most)
 constexpr int kSplitMinK = 16;    // smallest k that is split into two groups
 
 // Solver state of one group of columns: N x kp vectors, per-column scalars and flags, block
@@ -216,6 +216,7 @@ struct Workspace {
   double *h_sc = nullptr;    // pinned, S_NSLOT * kMaxKp
   cudaStream_t stream = nullptr;  // the group's own stream (split solves)
   cudaEvent_t done = nullptr;
+  cudaEvent_t packed = nullptr;  // this group has read its columns of a host B (zero-copy path)
   std::map<int, GraphEntry> graphs;  // per variant, for this kp
 };
 
@@ -248,6 +249,7 @@ struct bicgk_op_s {
   int opt_groups = 0;
   int opt_fused = 0;  // BICGK_OPT_FUSED_DOTS
   int opt_theta = 0;  // BICGK_OPT_THETA_IN_S
+  int opt_zero_copy = 0;  // BICGK_OPT_HOST_ZERO_COPY
   // launch shapes chosen by the batch autotuner (0 = the per-SM rule above)
   int grid_vec_abs = 0;
   int grid_spmm_abs = 0;
@@ -371,6 +373,7 @@ void free_workspace(Workspace &W) {
   cudaFreeHost(W.h_fl);
   cudaFreeHost(W.h_sc);
   if (W.done) cudaEventDestroy(W.done);
+  if (W.packed) cudaEventDestroy(W.packed);
   if (W.stream) cudaStreamDestroy(W.stream);
   W = Workspace();
 }
@@ -386,6 +389,7 @@ int ensure_workspace(bicgk_op A, Workspace &W, int kp) {
     CK(cudaMallocHost(&W.h_sc, sizeof(double) * S_NSLOT * kMaxKp));
     CK(cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&W.done, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&W.packed, cudaEventDisableTiming));
   }
   if (W.kp == kp) return BICGK_OK;
   free_vectors(W);
@@ -415,6 +419,18 @@ int ensure_hist(Workspace &W, int64_t elems) {
   CK(cudaMallocHost(&W.h_hist, sizeof(double) * elems));
   W.hist_cap = elems;
   return BICGK_OK;
+}
+
+// Device address of a page-locked host block (cudaHostAlloc, cudaHostRegister), or nullptr for
+// any other pointer: pageable host memory goes through the staged copy.
+const void *mapped_host_ptr(const void *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 int ensure_stage(bicgk_op A, int64_t elems) {
@@ -491,27 +507,42 @@ int build_graph_seq(bicgk_op A, Workspace &W, const Seq &q, const int *ext_act, 
   return BICGK_OK;
 }
 
+// Column groups of a solve of k columns (BICGK_OPT_RHS_GROUPS; the profiling mode runs them as
+// one group but keeps the kernel sequence this count selects).  Automatic: two from k = 16, four
+// from k = 32.  Each group's loop runs until its own slowest column stops, and a group that
+// finishes early leaves the GPU to the others, so smaller groups waste fewer iterations on
+// stopped columns: at 128^3, k = 32 four groups of 8 cost the same per iteration as two of 16
+// (3,033 vs 3,047 us) and solved 2.7 % more column-iterations per second over nine right-hand
+// sides (k = 64: -1.2 % per iteration, +2.3 % per solve).  At k = 16 four groups of 4 were 2 %
+// slower per iteration and even per solve.
+int num_groups(bicgk_op A, int k) {
+  if (A->opt_groups == 0) return k >= 2 * kSplitMinK ? 4 : k >= kSplitMinK ? 2 : 1;
+  return A->opt_groups < k ? A->opt_groups : k;
+}
+
 // Whether a solve of k columns takes the merged forms' dot kernels into the SpMM epilogues
-// (BICGK_OPT_FUSED_DOTS).  Automatic: when the columns are split into two concurrent groups.  There
-// it was measured faster (fewer kernels per iteration for the two groups to share the GPU: 3-4 %
-// at k = 16 and 32); with one group the fused SpMM's grid-wide reduction costs more than the
-// separate dot kernel (2-8 % slower at k = 1..8).  Profiling mode decides the same way.
+// (BICGK_OPT_FUSED_DOTS).  Automatic: when the columns are split into concurrent groups.  There
+// it was measured faster with two groups (fewer kernels per iteration for the groups to share the
+// GPU: 3-4 % at k = 16 and 32) and neutral to 2 % faster with four groups of 8 at k = 32; with one group the
+// fused SpMM's grid-wide reduction costs more than the separate dot kernel (2-8 % slower at
+// k = 1..8).  Profiling mode decides the same way.
 bool fuse_dots(bicgk_op A, int k) {
   if (A->opt_fused == 1) return false;
   if (A->opt_fused == 2) return true;
-  return A->opt_groups != 1 && k >= kSplitMinK;
+  return num_groups(A, k) >= 2;
 }
 
 // Whether theta = (s, s) of Algorithms 2 and 5 is taken in the s update (BICGK_OPT_THETA_IN_S).
 // Automatic, from fixed-iteration timings at 128^3 (7-point stencil): from k = 4 on, where the
 // s update stays bandwidth-bound with the extra FMA and group 1 sheds a third of its FP64 work
 // (0.5-2 % per iteration at k = 4..16, 3 % at k = 32 without the dot epilogues), except for the
-// classical form with the epilogues, where it gained nothing at k = 32 and cost 1 % at k = 16.
-// At k = 1 the reduction added to the s update costs more than it saves.
+// classical form with the epilogues in two groups, where it gained nothing at k = 32 and cost 1 %
+// at k = 16 (with four groups of 8 at k = 32 it gains 0.8 %).  At k = 1 the reduction added to
+// the s update costs more than it saves.
 bool theta_in_s(bicgk_op A, int k, int variant) {
   if (A->opt_theta == 1) return false;
   if (A->opt_theta == 2) return true;
-  return k >= 4 && !(variant == BICGK_CLASSICAL_MERGED && fuse_dots(A, k));
+  return k >= 4 && !(variant == BICGK_CLASSICAL_MERGED && fuse_dots(A, k) && num_groups(A, k) == 2);
 }
 
 int seq_opts(bicgk_op A, int k, int variant) {
@@ -777,11 +808,11 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
   const int gkey = variant + 100 * (jacobi ? 1 : 0) + 1000 * opts;
   int rc0 = ensure_variant_data(A, variant, jacobi, s);
   if (rc0) return rc0;
-  // columns are independent: split k >= kSplitMinK into two groups solved concurrently, so that
-  // one group's FP64-bound SpMM overlaps the other group's bandwidth-bound vector kernels
-  const int ngroups = (!A->profiling && A->opt_groups != 1 && k >= kSplitMinK) ? 2 : 1;
-  int c0[kMaxGroups + 1] = {0, ngroups == 2 ? k / 2 : k, k};
-  c0[ngroups] = k;
+  // columns are independent: from k = kSplitMinK they are split into groups solved concurrently,
+  // so that one group's FP64-bound SpMM overlaps another group's bandwidth-bound vector kernels
+  const int ngroups = A->profiling ? 1 : num_groups(A, k);
+  int c0[kMaxGroups + 1];
+  for (int g = 0; g <= ngroups; ++g) c0[g] = (int)((int64_t)g * k / ngroups);
   int rc;
   for (int g = 0; g < ngroups; ++g) {
     const int kg = c0[g + 1] - c0[g];
@@ -790,10 +821,24 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     if ((rc = ensure_hist(A->ws[g], (int64_t)(maxit + 1) * kpg))) return rc;
   }
   const Seq q = make_seq(variant, jacobi, opts);
-  // inputs
+  // inputs.  Page-locked host blocks are read and written in place by the pack and unpack kernels
+  // (mapped over the host link): each group moves only its own columns, the groups' reads one
+  // after another so that the first group iterates while the next ones still read B, and each
+  // group writes its X as soon as it stops.  Other host blocks go through a staged copy.
   const double *dB = B, *dX0 = X0;
   double *dX = X;
-  if (mem == BICGK_MEM_HOST) {
+  bool zero_copy = false;
+  if (mem == BICGK_MEM_HOST && A->opt_zero_copy != 1) {
+    const void *mb = mapped_host_ptr(B), *mx = mapped_host_ptr(X), *m0 = mapped_host_ptr(X0);
+    if (mb && mx && (!X0 || m0)) {
+      zero_copy = true;
+      dB = static_cast<const double *>(mb);
+      dX = static_cast<double *>(const_cast<void *>(mx));
+      dX0 = static_cast<const double *>(m0);
+    }
+  }
+  const bool staged = mem == BICGK_MEM_HOST && !zero_copy;
+  if (staged) {
     if ((rc = ensure_stage(A, A->n * k))) return rc;
     CK(cudaMemcpyAsync(A->d_stage[0], B, sizeof(double) * A->n * k, cudaMemcpyHostToDevice, s));
     dB = A->d_stage[0];
@@ -822,7 +867,9 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     CK(cudaMemcpyAsync(W.d_ctl, hc, sizeof(Ctl), cudaMemcpyHostToDevice, gs));
     const KArgs a0 = make_args(A, W, 0, cudaGraphConditionalHandle{}, nullptr, jacobi ? A->d_invdiag : nullptr);
     CK(launch_reset(a0, hist_len, gs));
+    if (zero_copy && g > 0) CK(cudaStreamWaitEvent(gs, A->ws[g - 1].packed, 0));
     CK(launch_pack(dB + c0[g], dX0 ? dX0 + c0[g] : nullptr, k, kg, a0, gs));
+    if (zero_copy) CK(cudaEventRecord(W.packed, gs));
     launches += 2;  // reset, pack
     if (A->profiling) {
       if ((rc = run_profiled(A, W, variant, jacobi, opts, a0, gs))) return rc;
@@ -839,7 +886,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
       }
       CK(cudaGraphLaunch(it->second.exec, gs));
     }
-    if (ngroups > 1 && mem == BICGK_MEM_HOST) {
+    if (ngroups > 1 && staged) {
       // the staged B is overwritten by X only after every group has packed its columns
       CK(cudaEventRecord(W.done, gs));
     }
@@ -847,7 +894,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
   for (int g = 0; g < ngroups; ++g) {
     Workspace &W = A->ws[g];
     cudaStream_t gs = ngroups > 1 ? W.stream : s;
-    if (ngroups > 1 && mem == BICGK_MEM_HOST)
+    if (ngroups > 1 && staged)
       for (int h = 0; h < ngroups; ++h)
         if (h != g) CK(cudaStreamWaitEvent(gs, A->ws[h].done, 0));
     const int kg = c0[g + 1] - c0[g];
@@ -865,7 +912,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     }
     launches += 1;  // unpack
   }
-  if (mem == BICGK_MEM_HOST) CK(cudaMemcpyAsync(X, dX, sizeof(double) * A->n * k, cudaMemcpyDeviceToHost, s));
+  if (staged) CK(cudaMemcpyAsync(X, dX, sizeof(double) * A->n * k, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   int32_t loop_iters = 0;
   for (int g = 0; g < ngroups; ++g) {
@@ -1070,7 +1117,7 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value) {
       A->opt_spmm_blocks = (int)value;
       break;
     case BICGK_OPT_RHS_GROUPS:
-      if (value < 0 || value > 2) return BICGK_E_INVALID;
+      if (value < 0 || value > kMaxGroups) return BICGK_E_INVALID;
       A->opt_groups = (int)value;
       break;
     case BICGK_OPT_FUSED_DOTS:
@@ -1080,6 +1127,10 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value) {
     case BICGK_OPT_THETA_IN_S:
       if (value < 0 || value > 2) return BICGK_E_INVALID;
       A->opt_theta = (int)value;
+      break;
+    case BICGK_OPT_HOST_ZERO_COPY:
+      if (value < 0 || value > 1) return BICGK_E_INVALID;
+      A->opt_zero_copy = (int)value;
       break;
     default:
       return BICGK_E_INVALID;
@@ -1118,6 +1169,12 @@ int bicgk_last_stats(bicgk_op A, int32_t *loop_iters, int64_t *kernel_launches, 
   if (loop_iters) *loop_iters = A->last_loop_iters;
   if (kernel_launches) *kernel_launches = A->last_launches;
   if (kernels_per_iter) *kernels_per_iter = A->last_kernels_per_iter;
+  return BICGK_OK;
+}
+
+int bicgk_last_groups(bicgk_op A, int32_t *groups) {
+  if (!A || !groups) return BICGK_E_INVALID;
+  *groups = A->last_groups;
   return BICGK_OK;
 }
 

@@ -348,23 +348,39 @@ def test_bad_csr_rejected(bk, cuda):
         bk.csr_create(np.array([0, 1, 2], dtype=np.int32), np.array([0, 5], dtype=np.int32), np.ones(2))
 
 
-def test_rhs_groups_match_single_group(bk, cuda):
-    """k >= 16 runs as two concurrent column groups; it must agree with one group (and the oracle)."""
+@pytest.mark.parametrize("groups", [0, 3, 4])
+def test_rhs_groups_match_single_group(bk, cuda, groups):
+    """k >= 16 runs as concurrent column groups (two by default at k = 20; three and four forced);
+    it must agree with one group (and the oracle), device and host buffers alike."""
     torch = cuda
     A = I.convdiff7(12, peclet=True)
-    B = I.rhs(A.n, 20, 4)                       # groups of 10 + 10 columns (kp 16) vs one group (kp 32)
+    B = I.rhs(A.n, 20, 4)                       # e.g. groups of 10 + 10 columns (kp 16) vs one group (kp 32)
     Bd = torch.from_numpy(B).cuda()
-    with bk.Operator(A) as one, bk.Operator(A) as two:
+    with bk.Operator(A) as one, bk.Operator(A) as many:
         bk.set_option(one.handle, bk.OPT_RHS_GROUPS, 1)
+        bk.set_option(many.handle, bk.OPT_RHS_GROUPS, groups)
         for flags, maxit, tol in ((1, 8, 0.0), (0, 500, 1e-8)):
             r1 = one.solve(Bd, tol=tol, maxit=maxit, flags=flags)
-            r2 = two.solve(Bd, tol=tol, maxit=maxit, flags=flags)
-            assert bk.last_stats(two.handle)["kernel_launches"] > bk.last_stats(one.handle)["kernel_launches"]
+            r2 = many.solve(Bd, tol=tol, maxit=maxit, flags=flags)
+            assert bk.last_stats(one.handle)["groups"] == 1
+            assert bk.last_stats(many.handle)["groups"] == (groups or 2)
+            assert bk.last_stats(many.handle)["kernel_launches"] > bk.last_stats(one.handle)["kernel_launches"]
             X1, X2 = r1.X.cpu().numpy(), r2.X.cpu().numpy()
             assert np.all(np.abs(r1.iters - r2.iters) <= 1) and np.array_equal(r1.status, r2.status)
             assert np.all(_colerr(X2, X1) <= (1e-12 if flags else 1e-10))
-        rh = two.solve(B, tol=1e-8, maxit=500)  # host buffers, two groups: same as the device call
+        rh = many.solve(B, tol=1e-8, maxit=500)  # host buffers, same groups: same as the device call
         assert np.array_equal(rh.X, r2.X.cpu().numpy()) and np.array_equal(rh.iters, r2.iters)
+        # page-locked host buffers: read and written in place by the kernels, or staged
+        Bp = torch.from_numpy(B).pin_memory()
+        X0 = 0.1 * I.rhs(A.n, 20, 5)
+        X0p = torch.from_numpy(X0).pin_memory()
+        rd0 = many.solve(Bd, X0=torch.from_numpy(X0).cuda(), tol=1e-8, maxit=500)
+        for zc in (0, 1):
+            bk.set_option(many.handle, bk.OPT_HOST_ZERO_COPY, zc)
+            rp = many.solve(Bp, tol=1e-8, maxit=500)
+            assert np.array_equal(rp.X.numpy(), r2.X.cpu().numpy()) and np.array_equal(rp.iters, r2.iters)
+            rp0 = many.solve(Bp, X0=X0p, tol=1e-8, maxit=500)
+            assert np.array_equal(rp0.X.numpy(), rd0.X.cpu().numpy()) and np.array_equal(rp0.iters, rd0.iters)
     ro = oracle.solve(A, B, tol=1e-8, maxit=500)
     _compare(r2, X2, ro)
 
