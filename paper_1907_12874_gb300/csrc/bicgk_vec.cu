@@ -1323,6 +1323,18 @@ BICGK_ONE_BLOCK(OP3_L1)
 BICGK_ONE_BLOCK(OP3_L2)
 #undef BICGK_ONE_BLOCK
 
+// Chunks of two doubles each thread loads before computing (memory-level parallelism).  Group 3
+// of Algorithm 2 streams five vectors: one chunk already keeps 80 KB per SM in flight, more than
+// the ~36 KB the copy bandwidth needs at DRAM latency, and two spilled under the 64-register cap.
+template <int OP>
+struct VecChunks {
+  static constexpr int value = 2;
+};
+template <>
+struct VecChunks<OP_G3> {
+  static constexpr int value = 1;
+};
+
 template <int OP>
 __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<OP>::value) vec_kernel(const KArgs a) {
   using D = OpDef<OP>;
@@ -1354,12 +1366,20 @@ __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<OP>::value) vec_kern
   // chunks of two doubles; an odd total (kp == 1, odd n) ends in a zero pad element
   const int64_t n2 = (a.n * kp + 1) >> 1;
   int64_t i = gtid;
-  for (; i + stride < n2; i += 2 * stride) {
-    V2 va[D::NL], vb[D::NL];
-    D::load(a, i, va);
-    D::load(a, i + stride, vb);
-    D::comp(a, i, va, s, acc);
-    D::comp(a, i + stride, vb, s, acc);
+  if constexpr (VecChunks<OP>::value == 2) {
+    for (; i + stride < n2; i += 2 * stride) {
+      V2 va[D::NL], vb[D::NL];
+      D::load(a, i, va);
+      D::load(a, i + stride, vb);
+      D::comp(a, i, va, s, acc);
+      D::comp(a, i + stride, vb, s, acc);
+    }
+  } else {
+    for (; i + stride < n2; i += stride) {  // the last chunk is the tail's
+      V2 va[D::NL];
+      D::load(a, i, va);
+      D::comp(a, i, va, s, acc);
+    }
   }
   if (i < n2) {
     V2 va[D::NL];
