@@ -212,7 +212,9 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
  * bicgk_csr_create, not validated here) and B, X0 (nullable), X are DEVICE
  * pointers in the layout of bicgk_solve; iters, status, resid_hist and
  * true_relres are host arrays as there, and every other argument means the
- * same.  Results equal bicgk_solve's within rounding of the same kernels.
+ * same.  Results equal bicgk_solve's with one column group and no column
+ * compaction (BICGK_OPT_RHS_GROUPS = 1, BICGK_OPT_COMPACT = 1), within rounding
+ * of the same kernels.
  *
  * Scratch: one 16 MiB file-scope device array in this library, which every
  * GPU that loads the library keeps until the process exits.  A problem fits if
@@ -259,11 +261,17 @@ enum bicgk_option {
                                       merged classical form when its dots are folded into the
                                       SpMM of two column groups (default); 1: never; 2: always.
                                       Same iterates up to the summation order of theta.        */
-  BICGK_OPT_HOST_ZERO_COPY = 6      /* host calls (BICGK_MEM_HOST) whose B, X (and X0) are all
+  BICGK_OPT_HOST_ZERO_COPY = 6,     /* host calls (BICGK_MEM_HOST) whose B, X (and X0) are all
                                       page-locked: 0 (default): the kernels read B and write X
                                       in place through their mapped device addresses, group by
                                       group, overlapping the transfer with the solve; 1: copy
                                       through a device staging block as for pageable memory.   */
+  BICGK_OPT_COMPACT = 7             /* classical and preconditioned BiCGStab (basic and merged):
+                                      0 (default): when at most half of a column group's
+                                      columns are still iterating, the group continues in a
+                                      layout of half the width (down to one column), so stopped
+                                      columns stop costing arithmetic; 1: never.  The iterates
+                                      are those of the full layout up to summation order.     */
 };
 
 /*
@@ -295,9 +303,9 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value);
  *   mode BICGK_BATCH_GRAPH: one CUDA-graph launch with an independent branch (set-up,
  *   conditional WHILE loop, true residual) per system; BICGK_BATCH_LOOP: bicgk_solve on each
  *   system in turn (the per-system launch loop).  Both modes run every system as one column
- *   group without dot epilogues (BICGK_OPT_RHS_GROUPS = 1, BICGK_OPT_FUSED_DOTS = 1) and the
- *   same kernel sequence, so their results are bitwise equal.  Residual histories are not
- *   returned.
+ *   group without dot epilogues or column compaction (BICGK_OPT_RHS_GROUPS = 1,
+ *   BICGK_OPT_FUSED_DOTS = 1, BICGK_OPT_COMPACT = 1) and the same kernel sequence, so their
+ *   results are bitwise equal.  Residual histories are not returned.
  * bicgk_batch_last_launches: kernels the last bicgk_batch_solve launched.
  */
 typedef struct bicgk_batch_s *bicgk_batch;

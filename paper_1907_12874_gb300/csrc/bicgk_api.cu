@@ -195,6 +195,7 @@ struct ProfEntry {
 
 constexpr int kMaxGroups = 4;     // column groups solved concurrently (at most)
 constexpr int kSplitMinK = 16;    // smallest k that is split into two groups
+constexpr int kMaxLevels = 6;     // column compaction: layouts of kp, kp/2, ..., 1 columns (kp <= 64)
 
 // Solver state of one group of columns: N x kp vectors, per-column scalars and flags, block
 // partials, control block, history, the group's stream and its captured graphs.
@@ -217,6 +218,12 @@ struct Workspace {
   cudaStream_t stream = nullptr;  // the group's own stream (split solves)
   cudaEvent_t done = nullptr;
   cudaEvent_t packed = nullptr;  // this group has read its columns of a host B (zero-copy path)
+  // column compaction: per layout level the solve's column of each layout column, the kept source
+  // columns of the current boundary, and the final per-column scalars and flags (solve's columns)
+  int *d_cmap = nullptr;     // [kMaxLevels + 1][kMaxKp]
+  int *d_act = nullptr;      // [kMaxKp]
+  double *d_fin_sc = nullptr;  // [S_NSLOT][kMaxKp]
+  int *d_fin_fl = nullptr;     // [F_NFLAG][kMaxKp]
   std::map<int, GraphEntry> graphs;  // per variant, for this kp
 };
 
@@ -250,6 +257,7 @@ struct bicgk_op_s {
   int opt_fused = 0;  // BICGK_OPT_FUSED_DOTS
   int opt_theta = 0;  // BICGK_OPT_THETA_IN_S
   int opt_zero_copy = 0;  // BICGK_OPT_HOST_ZERO_COPY
+  int opt_compact = 0;    // BICGK_OPT_COMPACT
   // launch shapes chosen by the batch autotuner (0 = the per-SM rule above)
   int grid_vec_abs = 0;
   int grid_spmm_abs = 0;
@@ -277,6 +285,9 @@ KArgs make_args(bicgk_op A, const Workspace &W, int use_cond, cudaGraphCondition
   a.kp = W.kp;
   a.use_cond = use_cond;
   a.cond = h;
+  a.cmap = nullptr;
+  a.kp_out = W.kp;
+  a.compact = 0;
   return a;
 }
 
@@ -372,6 +383,10 @@ void free_workspace(Workspace &W) {
   cudaFreeHost(W.h_hist);
   cudaFreeHost(W.h_fl);
   cudaFreeHost(W.h_sc);
+  cudaFree(W.d_cmap);
+  cudaFree(W.d_act);
+  cudaFree(W.d_fin_sc);
+  cudaFree(W.d_fin_fl);
   if (W.done) cudaEventDestroy(W.done);
   if (W.packed) cudaEventDestroy(W.packed);
   if (W.stream) cudaStreamDestroy(W.stream);
@@ -390,6 +405,10 @@ int ensure_workspace(bicgk_op A, Workspace &W, int kp) {
     CK(cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&W.done, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&W.packed, cudaEventDisableTiming));
+    CK(cudaMalloc(&W.d_cmap, sizeof(int) * (kMaxLevels + 1) * kMaxKp));
+    CK(cudaMalloc(&W.d_act, sizeof(int) * kMaxKp));
+    CK(cudaMalloc(&W.d_fin_sc, sizeof(double) * S_NSLOT * kMaxKp));
+    CK(cudaMalloc(&W.d_fin_fl, sizeof(int) * F_NFLAG * kMaxKp));
   }
   if (W.kp == kp) return BICGK_OK;
   free_vectors(W);
@@ -503,6 +522,110 @@ int build_graph_seq(bicgk_op A, Workspace &W, const Seq &q, const int *ext_act, 
     }
     CK(cudaStreamEndCapture(cs, &tmp));
   }
+  CK(cudaGraphInstantiate(&ge->exec, g, 0));
+  return BICGK_OK;
+}
+
+// Arguments of compaction level l (kp0 >> l columns): the live vectors alternate between two slot
+// sets so that each boundary gathers into vectors the previous level does not read; the other
+// roles of the loop are rewritten every iteration before they are read.
+KArgs level_args(bicgk_op A, const Workspace &W, int l, cudaGraphConditionalHandle h, const double *invdiag) {
+  KArgs a = make_args(A, W, 1, h, nullptr, invdiag);
+  a.kp = W.kp >> l;
+  a.kp_out = W.kp;
+  a.cmap = l > 0 ? W.d_cmap + l * kMaxKp : nullptr;
+  a.compact = a.kp > 1;
+  if (l & 1) {
+    a.v[V_X] = W.d_vec + (int64_t)V_W * W.vstride;
+    a.v[V_R] = W.d_vec + (int64_t)V_Z * W.vstride;
+    a.v[V_R0] = W.d_vec + (int64_t)V_RT * W.vstride;
+    a.v[V_P] = W.d_vec + (int64_t)V_SH * W.vstride;
+  }
+  return a;
+}
+
+// Arguments of the final kernels and the unpack of a compacted solve: the full layout, x from the
+// final block (V_WH), the final per-column scalars and flags.
+KArgs final_args(bicgk_op A, const Workspace &W, const double *invdiag) {
+  KArgs a = make_args(A, W, 0, cudaGraphConditionalHandle{}, nullptr, invdiag);
+  a.v[V_X] = W.d_vec + (int64_t)V_WH * W.vstride;
+  a.sc = W.d_fin_sc;
+  a.fl = W.d_fin_fl;
+  return a;
+}
+
+// Whether a solve's group of kp columns narrows its layout as its columns stop
+// (BICGK_OPT_COMPACT).  The forms whose live vectors at the top of an iteration are x, r, r^0, p:
+// classical BiCGStab (Algorithms 1, 2) and preconditioned BiCGStab (Algorithm 5).
+bool compact_columns(bicgk_op A, int variant, int kp) {
+  if (A->opt_compact == 1 || A->profiling || kp < 2) return false;
+  return variant == BICGK_CLASSICAL_MERGED || variant == BICGK_CLASSICAL_PLAIN ||
+         variant == BICGK_PRECOND_MERGED || variant == BICGK_PRECOND_PLAIN;
+}
+
+// The graph of a compacted solve: set-up; WHILE(level 0); then per level l = 1..L a compaction
+// boundary (plan + move kernels) and WHILE(level l); a last boundary that writes the final values
+// of the last level; the final kernels on the full layout.  Levels that are not reached cost their
+// boundary kernels' launches only (they return at once).
+int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, const double *invdiag) {
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  ge->graph = g;
+  int L = 0;
+  while ((W.kp >> L) > 1) ++L;
+  cudaGraphConditionalHandle h[kMaxLevels + 1];
+  for (int l = 0; l <= L; ++l) CK(cudaGraphConditionalHandleCreate(&h[l], g, 0, 0));
+  KArgs lv[kMaxLevels + 1];
+  for (int l = 0; l <= L; ++l) lv[l] = level_args(A, W, l, h[l], invdiag);
+  const KArgs af = final_args(A, W, invdiag);
+  double *xf = W.d_vec + (int64_t)V_WH * W.vstride;
+  cudaStream_t cs = A->cap_stream;
+  cudaGraph_t tmp;
+  auto fail = [&](cudaError_t e, const char *what) {
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(cs, &dummy);
+    return cuda_fail(e, what);
+  };
+  // set-up, then per level: WHILE(body), boundary
+  CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  for (const Step &st : q.setup) {
+    cudaError_t e = launch_step(A, st, lv[0], cs);
+    if (e != cudaSuccess) return fail(e, "capture set-up");
+  }
+  for (int l = 0; l <= L; ++l) {
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+    std::vector<cudaGraphNode_t> leaves(deps, deps + ndeps);
+    CK(cudaStreamEndCapture(cs, &tmp));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h[l];
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, g, leaves.data(), nullptr, leaves.size(), &p));
+    CK(cudaStreamBeginCaptureToGraph(cs, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    for (const Step &st : q.body) {
+      cudaError_t e = launch_step(A, st, lv[l], cs);
+      if (e != cudaSuccess) return fail(e, "capture body");
+    }
+    CK(cudaStreamEndCapture(cs, &tmp));
+    CK(cudaStreamBeginCaptureToGraph(cs, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    const bool last = l == L;
+    const KArgs &dst = last ? lv[l] : lv[l + 1];
+    cudaError_t e = launch_compact(lv[l], dst, l + 1, last ? 1 : 0, last ? h[l] : h[l + 1], W.d_fin_sc,
+                                   W.d_fin_fl, last ? W.d_act : W.d_cmap + (l + 1) * kMaxKp, W.d_act, xf,
+                                   A->nsm * 4, cs);
+    if (e != cudaSuccess) return fail(e, "capture compaction");
+  }
+  for (const Step &st : q.fin) {
+    cudaError_t e = launch_step(A, st, af, cs);
+    if (e != cudaSuccess) return fail(e, "capture final");
+  }
+  CK(cudaStreamEndCapture(cs, &tmp));
   CK(cudaGraphInstantiate(&ge->exec, g, 0));
   return BICGK_OK;
 }
@@ -874,15 +997,19 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     if (A->profiling) {
       if ((rc = run_profiled(A, W, variant, jacobi, opts, a0, gs))) return rc;
     } else {
-      auto it = W.graphs.find(gkey);
+      const bool cg = compact_columns(A, variant, W.kp);
+      const int key = gkey + 10000 * (cg ? 1 : 0);
+      auto it = W.graphs.find(key);
       if (it == W.graphs.end()) {
         GraphEntry ge;
-        if ((rc = build_graph(A, W, variant, jacobi, opts, &ge))) {
+        rc = cg ? build_graph_compact(A, W, q, &ge, jacobi ? A->d_invdiag : nullptr)
+                : build_graph(A, W, variant, jacobi, opts, &ge);
+        if (rc) {
           if (ge.exec) cudaGraphExecDestroy(ge.exec);
           if (ge.graph) cudaGraphDestroy(ge.graph);
           return rc;
         }
-        it = W.graphs.emplace(gkey, ge).first;
+        it = W.graphs.emplace(key, ge).first;
       }
       CK(cudaGraphLaunch(it->second.exec, gs));
     }
@@ -899,11 +1026,18 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
         if (h != g) CK(cudaStreamWaitEvent(gs, A->ws[h].done, 0));
     const int kg = c0[g + 1] - c0[g];
     const int64_t hist_len = (int64_t)(maxit + 1) * W.kp;
-    const KArgs a0 = make_args(A, W, 0, cudaGraphConditionalHandle{});
+    // a compacted solve reports from the final block and arrays
+    const bool cg = compact_columns(A, variant, W.kp);
+    const KArgs a0 = cg ? final_args(A, W, nullptr) : make_args(A, W, 0, cudaGraphConditionalHandle{});
     CK(launch_unpack_role(dX + c0[g], k, kg, a0, V_X, 1, gs));
     CK(cudaMemcpyAsync(W.h_ctl, W.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, gs));
-    CK(cudaMemcpyAsync(W.h_fl, W.d_fl, sizeof(int) * F_NFLAG * kMaxKp, cudaMemcpyDeviceToHost, gs));
-    CK(cudaMemcpyAsync(W.h_sc, W.d_sc, sizeof(double) * S_NSLOT * kMaxKp, cudaMemcpyDeviceToHost, gs));
+    CK(cudaMemcpyAsync(W.h_fl, a0.fl, sizeof(int) * F_NFLAG * kMaxKp, cudaMemcpyDeviceToHost, gs));
+    CK(cudaMemcpyAsync(W.h_sc, a0.sc, sizeof(double) * S_NSLOT * kMaxKp, cudaMemcpyDeviceToHost, gs));
+    if (cg) {
+      int levels = 0;
+      while ((W.kp >> levels) > 1) ++levels;
+      launches += 2 * (levels + 1);  // the compaction boundaries' plan and move kernels
+    }
     if (resid_hist)
       CK(cudaMemcpyAsync(W.h_hist, W.d_hist, sizeof(double) * hist_len, cudaMemcpyDeviceToHost, gs));
     if (ngroups > 1) {
@@ -1132,6 +1266,10 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value) {
       if (value < 0 || value > 1) return BICGK_E_INVALID;
       A->opt_zero_copy = (int)value;
       break;
+    case BICGK_OPT_COMPACT:
+      if (value < 0 || value > 1) return BICGK_E_INVALID;
+      A->opt_compact = (int)value;
+      break;
     default:
       return BICGK_E_INVALID;
   }
@@ -1332,11 +1470,12 @@ int bicgk_batch_create(bicgk_batch *out, int32_t nsys, const int64_t *n_rows, co
   int rc = BICGK_OK;
   for (int i = 0; i < nsys && rc == BICGK_OK; ++i)
     rc = bicgk_csr_create(&b->ops[i], n_rows[i], nnz[i], rowptr[i], colidx[i], vals[i], mem, stream);
-  // each system runs as one column group without dot epilogues, in the graph and in the launch
-  // loop alike (the loop calls bicgk_solve with these operators)
+  // each system runs as one column group without dot epilogues or column compaction, in the
+  // graph and in the launch loop alike (the loop calls bicgk_solve with these operators)
   for (int i = 0; i < nsys && rc == BICGK_OK; ++i) {
     b->ops[i]->opt_groups = 1;
     b->ops[i]->opt_fused = 1;
+    b->ops[i]->opt_compact = 1;
   }
   cudaError_t e = cudaSuccess;
   if (rc == BICGK_OK) {

@@ -49,6 +49,9 @@ struct Ctl {
   int flags;      // bicgk_flags
   int any_active; // some column still iterating
   int loop_iters; // iterations the loop completed
+  int compact_req; // the loop stopped to narrow the layout (at most kp/2 columns still active)
+  int level;      // layout level of the column compaction (-1 once the final values are out)
+  int mode;       // action of the current compaction boundary: 0 none, 1 narrow, 2 final
   unsigned int ticket; // arrival counter of the grid reduction's second level (reset by its last block)
   unsigned int gticket[kMaxRedGroups]; // arrival counters of the first level, one per group of blocks
 };
@@ -72,6 +75,11 @@ struct KArgs {
   cudaGraphConditionalHandle cond;
   const int *ext_act;  // inner solves of the refinement: columns the outer loop still iterates
   const double *invdiag;  // Jacobi preconditioner 1/a_ii per row (nullptr: M = identity, a copy)
+  // column compaction: the solve's column of each layout column (nullptr: the same; -1: padding),
+  // the history's row length, and whether the loop may stop to narrow the layout
+  const int *cmap;
+  int kp_out;
+  int compact;
 };
 
 // Streaming kernel identifiers (one per fused vector operation of the listings).
@@ -178,5 +186,15 @@ cudaError_t launch_invdiag(const int32_t *rowptr, const int32_t *colidx, const d
                            int64_t n, cudaStream_t s);
 // Fill the history with NaN and clear the per-column state.
 cudaError_t launch_reset(const KArgs &a, int64_t hist_len, cudaStream_t s);
+// Column compaction boundary `boundary` (1..L+1) between layout level boundary-1 (src) and
+// boundary (dst, half as many columns; unused when `last`).  The plan kernel decides from the
+// control block (narrow, write the final values, or nothing), moves the per-column scalars and
+// flags of the columns that leave to fin_sc / fin_fl (indexed by the solve's column), compacts
+// the rest, writes dst's column map to cmap_out and the kept source columns to act, and sets the
+// next level's loop condition.  The move kernel writes the x of the columns that leave to xf
+// (kp_out layout) and gathers the live vectors (x, r, r^0, p) of the kept ones into dst's slots.
+cudaError_t launch_compact(const KArgs &src, const KArgs &dst, int boundary, int last,
+                           cudaGraphConditionalHandle next, double *fin_sc, int *fin_fl, int *cmap_out,
+                           int *act, double *xf, int grid, cudaStream_t s);
 
 }  // namespace bicgk

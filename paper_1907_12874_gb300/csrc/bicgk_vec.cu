@@ -116,6 +116,11 @@ __device__ __forceinline__ double hist_value(double est) {
   if (isnan(est)) return est;
   return est > 0.0 ? __dsqrt_rn(est) : 0.0;
 }
+// History entry of iteration row `row` for layout column c: rows of kp_out entries, indexed by the
+// solve's column (the layouts of a compacted solve keep their columns' original places).
+__device__ __forceinline__ double &hist_at(const KArgs &a, int64_t row, int c) {
+  return a.ctl->hist[row * a.kp_out + (a.cmap ? a.cmap[c] : c)];
+}
 __device__ __forceinline__ void col_stop(const KArgs &a, int c, int st) {
   FL(F_ACT, c) = 0;
   FL(F_STATUS, c) = st;
@@ -171,7 +176,7 @@ __device__ void g1_rule(const KArgs &a, int c, double phi, double psi, double th
   FL(F_XUPD, c) = 1;
   FL(F_ITERS, c) = j + 1;
   const double est = sub_rn(th, __dmul_rn(om, phi));
-  ctl->hist[(int64_t)(j + 1) * a.kp + c] = hist_value(est);
+  hist_at(a, j + 1, c) = hist_value(est);
   if (!fin1(est)) col_stop(a, c, ST_NONFINITE);
   else if (!(ctl->flags & 1) && est < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
 }
@@ -213,7 +218,7 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
       st = ST_CONVERGED;
       act = 0;
     }
-    ctl->hist[c] = h0;
+    hist_at(a, 0, c) = h0;
     FL(F_ACT, c) = act;
     FL(F_STATUS, c) = st;
   } else if constexpr (FIN == FIN_RW0) {
@@ -271,7 +276,7 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
     const int j = ctl->iter;
     FL(F_ITERS, c) = j + 1;
     const double rr = s[c];
-    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(rr);
+    hist_at(a, j + 1, c) = hist_value(rr);
     if (!fin1(rr)) col_stop(a, c, ST_NONFINITE);
     else if (!nostop && rr < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
   } else if constexpr (FIN == FIN_R4_MERGED || FIN == FIN_R4_PLAIN) {
@@ -293,7 +298,7 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
     FL(F_XUPD, c) = 1;
     FL(F_ITERS, c) = j + 1;
     const double est = sub_rn(eta, __dmul_rn(om, th));
-    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(est);
+    hist_at(a, j + 1, c) = hist_value(est);
     if (!fin1(est)) { col_stop(a, c, ST_NONFINITE); return; }
     if (!nostop && est < SC(S_EPS2, c)) { col_stop(a, c, ST_CONVERGED); return; }
     const double r1 = __dmul_rn(-om, psi);
@@ -322,7 +327,7 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
     FL(F_XUPD, c) = 1;
     FL(F_ITERS, c) = j + 1;
     const double est = sub_rn(pi, __dmul_rn(om, th));
-    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(est);
+    hist_at(a, j + 1, c) = hist_value(est);
     if (!fin1(est)) col_stop(a, c, ST_NONFINITE);
     else if (!nostop && est < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
   } else if constexpr (FIN == FIN_PG3_MERGED || FIN == FIN_PG3_PLAIN) {
@@ -379,7 +384,7 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
     if (!FL(F_ACT, c)) return;
     const int j = ctl->iter;
     const double rr = s[c], bn2 = SC(S_BN2, c);
-    ctl->hist[(int64_t)j * kp + c] = hist_value(rr);
+    hist_at(a, j, c) = hist_value(rr);
     SC(S_TRUE, c) = __ddiv_rn(__dsqrt_rn(rr), __dsqrt_rn(bn2));
     if (!fin1(rr)) col_stop(a, c, ST_NONFINITE);
     else if (rr < SC(S_EPS2, c)) col_stop(a, c, ST_CONVERGED);
@@ -429,7 +434,7 @@ __device__ void fin_col(const KArgs &a, int c, const double *s, int kp) {
     FL(F_XUPD, c) = 1;
     FL(F_ITERS, c) = j + 1;
     const double est = sub_rn(nu, __dmul_rn(om, th));
-    ctl->hist[(int64_t)(j + 1) * kp + c] = hist_value(est);
+    hist_at(a, j + 1, c) = hist_value(est);
     if (!fin1(est)) { col_stop(a, c, ST_NONFINITE); return; }
     if (!nostop && est < SC(S_EPS2, c)) { col_stop(a, c, ST_CONVERGED); return; }
     SC(S_SIGP, c) = SC(S_SIGMA, c);
@@ -461,6 +466,14 @@ __device__ void fin_ctl(const KArgs &a) {
       ctl->iter = j;
       ctl->loop_iters = j;
       go = any && j < ctl->maxit;
+      if (go && a.compact) {  // at most half of the layout's columns left: stop to narrow it
+        int cnt = 0;
+        for (int c = 0; c < a.kp; ++c) cnt += FL(F_ACT, c) != 0;
+        if (2 * cnt <= a.kp) {
+          ctl->compact_req = 1;
+          go = 0;
+        }
+      }
     }
     if (a.use_cond) cudaGraphSetConditional(a.cond, go ? 1u : 0u);
   }
@@ -1882,6 +1895,118 @@ cudaError_t launch_to_float(const double *src, float *dst, int64_t n, cudaStream
 
 cudaError_t launch_reset(const KArgs &a, int64_t hist_len, cudaStream_t s) {
   reset_kernel<<<64, 256, 0, s>>>(a, hist_len);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ column compaction
+//
+// A group's loop runs until its slowest column stops, and a stopped column still costs its FP64
+// FMAs in every kernel.  When at most half of a layout's columns are still active, the loop stops
+// (fin_ctl) and the group continues in a layout of half the width: the active columns keep their
+// order, the live vectors of the classical and preconditioned forms at the top of an iteration
+// (x, r, r^0, p) are gathered into it, and everything a column reports (x, iterations, status,
+// the scalars the final kernels read) leaves for final arrays indexed by the solve's column.
+
+namespace {
+__global__ void compact_plan_kernel(KArgs a, KArgs dst, int boundary, int last, cudaGraphConditionalHandle next,
+                                    double *fin_sc, int *fin_fl, int *cmap_out, int *act) {
+  __shared__ int s_act[kMaxKp];
+  __shared__ int s_m, s_mode;
+  __shared__ double s_sc[S_NSLOT][kMaxKp];
+  __shared__ int s_fl[F_NFLAG][kMaxKp];
+  Ctl *ctl = a.ctl;
+  const int kps = a.kp, t = threadIdx.x;
+  if (t == 0) {
+    int mode = 0;
+    if (ctl->level == boundary - 1) mode = (!last && ctl->compact_req) ? 1 : 2;
+    int m = 0;
+    if (mode == 1)
+      for (int c = 0; c < kps; ++c)
+        if (FL(F_ACT, c)) s_act[m++] = c;
+    s_m = m;
+    s_mode = mode;
+    ctl->mode = mode;
+    ctl->compact_req = 0;
+    if (mode == 1) ctl->level = boundary;
+    if (mode == 2) ctl->level = -1;
+    if (!last) cudaGraphSetConditional(next, mode == 1 ? 1u : 0u);
+  }
+  __syncthreads();
+  const int mode = s_mode, m = s_m;
+  if (mode == 0) return;
+  // the state of the columns that leave (all of them for the final values, else the stopped ones)
+  if (t < kps) {
+    const int orig = a.cmap ? a.cmap[t] : t;
+    const bool leaving = mode == 2 || !FL(F_ACT, t);
+    if (orig >= 0 && leaving) {
+      for (int q = 0; q < S_NSLOT; ++q) fin_sc[q * kMaxKp + orig] = SC(q, t);
+      for (int f = 0; f < F_NFLAG; ++f) fin_fl[f * kMaxKp + orig] = FL(f, t);
+    }
+    for (int q = 0; q < S_NSLOT; ++q) s_sc[q][t] = SC(q, t);
+    for (int f = 0; f < F_NFLAG; ++f) s_fl[f][t] = FL(f, t);
+  }
+  __syncthreads();
+  if (mode != 1) return;
+  // the kept columns, in order, at the front of the narrower layout; zero padding after them
+  const int kpd = dst.kp;
+  if (t < kpd) {
+    const int src = t < m ? s_act[t] : -1;
+    for (int q = 0; q < S_NSLOT; ++q) a.sc[q * kMaxKp + t] = src >= 0 ? s_sc[q][src] : 0.0;
+    for (int f = 0; f < F_NFLAG; ++f) a.fl[f * kMaxKp + t] = src >= 0 ? s_fl[f][src] : 0;
+    cmap_out[t] = src >= 0 ? (a.cmap ? a.cmap[src] : src) : -1;
+    act[t] = src;
+  }
+}
+
+__global__ void compact_move_kernel(KArgs a, KArgs dst, const int *act, double *xf) {
+  // roles of the classical and preconditioned loops (Algorithms 1, 2, 5): the live ones at the top
+  // of an iteration, and all of them (their padding element is zeroed at an odd length)
+  const int kLive[4] = {V_X, V_R, V_R0, V_P};
+  const int kLoopRoles[9] = {V_X, V_R, V_R0, V_P, V_V, V_S, V_T, V_Q, V_Y};
+  __shared__ int s_orig[kMaxKp], s_keep[kMaxKp], s_act[kMaxKp];
+  const int mode = a.ctl->mode;
+  if (mode == 0) return;
+  const int kps = a.kp, kpd = dst.kp, kp0 = a.kp_out;
+  for (int c = threadIdx.x; c < kMaxKp; c += blockDim.x) {
+    s_orig[c] = c < kps ? (a.cmap ? a.cmap[c] : c) : -1;
+    s_keep[c] = 0;
+  }
+  __syncthreads();
+  if (mode == 1)
+    for (int c = threadIdx.x; c < kpd; c += blockDim.x) {
+      s_act[c] = act[c];
+      if (act[c] >= 0) s_keep[act[c]] = 1;
+    }
+  __syncthreads();
+  const int64_t n = a.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int shs = __ffs(kps) - 1, shd = __ffs(kpd) - 1;  // kp is a power of two
+  // x of the columns that leave, at their place in the final block
+  for (int64_t e = t0; e < n * kps; e += stride) {
+    const int c = (int)(e & (kps - 1));
+    const int orig = s_orig[c];
+    if (orig >= 0 && !s_keep[c]) xf[(e >> shs) * kp0 + orig] = a.v[V_X][e];
+  }
+  if (mode != 1) return;
+  for (int64_t e = t0; e < n * kpd; e += stride) {
+    const int64_t i = e >> shd;
+    const int src = s_act[e & (kpd - 1)];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) dst.v[kLive[r]][e] = src >= 0 ? a.v[kLive[r]][(i << shs) + src] : 0.0;
+  }
+  if (((n * kpd) & 1) && t0 == 0)
+    for (int r = 0; r < 9; ++r) dst.v[kLoopRoles[r]][n * kpd] = 0.0;
+}
+}  // namespace
+
+cudaError_t launch_compact(const KArgs &src, const KArgs &dst, int boundary, int last,
+                           cudaGraphConditionalHandle next, double *fin_sc, int *fin_fl, int *cmap_out,
+                           int *act, double *xf, int grid, cudaStream_t s) {
+  compact_plan_kernel<<<1, kMaxKp, 0, s>>>(src, dst, boundary, last, next, fin_sc, fin_fl, cmap_out, act);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  compact_move_kernel<<<grid, 256, 0, s>>>(src, dst, act, xf);
   return cudaGetLastError();
 }
 

@@ -440,3 +440,94 @@ def test_fused_dots_match_separate_kernels(bk, cuda, variant, k, kind):
         Xf = r.X.cpu().numpy()
     rof = oracle.solve(A, B, tol=1e-8, maxit=1000, variant=variant)
     _compare(r, Xf, rof)
+
+
+COMPACT_VARIANTS = ["classical_merged", "classical_plain", "precond_merged", "precond_plain"]
+
+
+@pytest.mark.parametrize("variant", COMPACT_VARIANTS)
+@pytest.mark.parametrize("k", [2, 5, 8, 20])
+def test_column_compaction_matches_full_layout(bk, cuda, variant, k):
+    """A column group narrows its layout whenever at most half of its columns still iterate
+    (BICGK_OPT_COMPACT).  Columns of very different difficulty make the groups pass through
+    several layouts: initial guesses whose error is the exact solution's times 10^-d, d from 0
+    to 8, so the columns meet the relative tolerance after very different iteration counts,
+    plus zero columns that stop at the set-up.  The solve must agree with the full layout and
+    with the oracle: same status, iterations within one, solutions within the solution
+    tolerance, residual histories at the solve's own columns."""
+    import scipy.sparse.linalg as sla
+    torch = cuda
+    A = I.convdiff7(12, peclet=True)
+    B = I.rhs(A.n, k, 21)
+    rng = np.random.default_rng(k)
+    B[:, rng.permutation(k)[: k // 3]] = 0.0          # zero columns: stopped before the loop
+    Xs = sla.splu(A.to_scipy().tocsc()).solve(B)
+    G0 = Xs + 10.0 ** -rng.integers(0, 9, size=k) * rng.standard_normal(B.shape) * np.abs(Xs).max(axis=0)
+    G0[:, np.all(B == 0, axis=0)] = 0.0
+    flags = 2 if variant.startswith("precond") and k % 2 else 0   # Jacobi for some
+    Bd = torch.from_numpy(B).cuda()
+    G0d = torch.from_numpy(G0).cuda()
+    res = {}
+    with bk.Operator(A) as op:
+        for compact in (1, 0):
+            bk.set_option(op.handle, bk.OPT_COMPACT, compact)
+            r = op.solve(Bd, X0=G0d, tol=1e-9, maxit=600, variant=variant, flags=flags)
+            res[compact] = (r, r.X.cpu().numpy())
+    (r1, X1), (r0, X0) = res[1], res[0]
+    assert np.array_equal(r0.status, r1.status)
+    assert np.all(np.abs(r0.iters - r1.iters) <= 1), (r0.iters, r1.iters)
+    assert np.all(_colerr(X0, X1) <= 1e-9), _colerr(X0, X1)
+    assert np.all(X0[:, np.all(B == 0, axis=0)] == 0.0)
+    # histories: every column's entries sit at its own column, NaN after it stopped.  The two
+    # layouts sum the dots in different orders, and the difference grows as the residual falls
+    # (2e-6 relative at 1e-8 of the initial residual), so the entries agree to 1e-4.
+    for c in range(k):
+        m = int(min(r0.iters[c], r1.iters[c]))
+        np.testing.assert_allclose(r0.hist[: m + 1, c], r1.hist[: m + 1, c], rtol=1e-4)
+        assert np.all(np.isfinite(r0.hist[: r0.iters[c] + 1, c]))
+        assert np.all(np.isnan(r0.hist[r0.iters[c] + 1:, c]))
+    ro = oracle.solve(A, B, X0=G0, tol=1e-9, maxit=600, variant=variant,
+                      flags=oracle.JACOBI if flags else 0)
+    if k >= 5:
+        assert len(set(ro.iters.tolist())) >= 3       # the columns stop at different iterations
+    _compare(r0, X0, ro)
+
+
+@pytest.mark.parametrize("variant", COMPACT_VARIANTS)
+def test_column_compaction_down_to_one_column(bk, cuda, variant):
+    """Seven of eight columns zero: the group narrows 8 -> 4 -> 2 -> 1 after its first iterations
+    and the last column finishes alone in the one-column layout (odd row count, so the padding
+    element of every vector is in play).  Host and device buffers, against the oracle."""
+    torch = cuda
+    A = I.convdiff7(11, peclet=True)                  # 1331 rows
+    B = np.zeros((A.n, 8))
+    B[:, 5] = I.rhs(A.n, 1, 3)[:, 0]
+    ro = oracle.solve(A, B, tol=1e-10, maxit=500, variant=variant)
+    with bk.Operator(A) as op:
+        r = op.solve(torch.from_numpy(B).cuda(), tol=1e-10, maxit=500, variant=variant)
+        X = r.X.cpu().numpy()
+        rh = op.solve(torch.from_numpy(B).pin_memory(), tol=1e-10, maxit=500, variant=variant)
+        bk.set_option(op.handle, bk.OPT_COMPACT, 1)
+        rf = op.solve(torch.from_numpy(B).cuda(), tol=1e-10, maxit=500, variant=variant)
+    _compare(r, X, ro)
+    assert np.array_equal(rh.X.numpy(), X) and np.array_equal(rh.iters, r.iters)
+    assert np.all(np.abs(rf.iters - r.iters) <= 1)
+    assert np.all(_colerr(rf.X.cpu().numpy(), X) <= 1e-9)
+    assert np.all(r.iters[[0, 1, 2, 3, 4, 6, 7]] == 0) and r.iters[5] > 10
+
+
+@pytest.mark.parametrize("variant", COMPACT_VARIANTS)
+def test_column_compaction_idle_without_stops(bk, cuda, variant):
+    """With the stop test off no column stops, the layout never narrows, and the compacted graph
+    (its boundaries write the final values only) gives bitwise the full layout's iterates."""
+    torch = cuda
+    A = I.perturbed27(10, seed=4)
+    B = torch.from_numpy(I.rhs(A.n, 6, 8)).cuda()
+    out = []
+    with bk.Operator(A) as op:
+        for compact in (1, 0):
+            bk.set_option(op.handle, bk.OPT_COMPACT, compact)
+            r = op.solve(B, tol=0.0, maxit=7, variant=variant, flags=bk.FLAG_NO_STOP_TEST)
+            out.append((r.X.cpu().numpy(), r.hist.copy(), r.iters.copy(), r.true_relres.copy()))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b, equal_nan=True)
