@@ -3,7 +3,8 @@
 Workload: the 128^3 upwind convection-diffusion operator (2,097,152 rows, 14,581,760 nonzeros),
 k = 32 right-hand sides U[-1,1] (seed 2), x0 = 0, relative tolerance 1e-8, merged classical
 BiCGStab (Algorithm 2), solved as the benchmark solves it: graph mode with the device-side loop,
-two concurrent column groups, default launch shapes.
+four concurrent column groups of 8 that narrow their layout as their columns stop, default
+launch shapes.
 
 What the oracle can check at this size:
   * the SpMM output, every element (the oracle's product is cheap);
@@ -24,7 +25,7 @@ from paper_1907_12874_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 N_GRID, K, SEED, TOL = 128, 32, 2, 1e-8
-SAMPLE = [0, 17, 31]                  # columns the oracle follows (one in each group, one at the end)
+SAMPLE = [0, 9, 18, 31]               # columns the oracle follows (one in each of the four groups)
 
 
 @pytest.fixture(scope="module")
