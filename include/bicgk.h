@@ -148,6 +148,13 @@ int bicgk_spmm_f32(bicgk_op A, int32_t k, const float *X, float *Y, void *stream
  * Per-column rules where the paper is silent: b_c = 0 gives x_c = 0 with 0
  * iterations; a column whose ||r_0|| already passes the test keeps x0; a
  * column stops independently of the others and is not written afterwards.
+ * Execution (bicgk_set_option): from k = 16 the columns run as concurrent
+ * groups on internal streams joined back to `stream`; the classical and
+ * preconditioned forms narrow a group's layout as its columns stop; host
+ * blocks that are page-locked are read and written in place.  Columns never
+ * interact, so these change summation orders only: iterates agree with a
+ * one-group solve to rounding, and a column's iteration count can differ by
+ * the few iterations that rounding moves near the tolerance.
  * The first call per (variant, k) builds and caches a CUDA graph; callers must
  * not capture this call into a graph of their own.
  */
