@@ -272,7 +272,7 @@ def run_reference(args):
         rates.append(r)
         secs += dt
     value = args.steps * cols * iters / secs
-    sample = f"{cols} column x {iters} fixed iterations of the {args.grid}^3 k={args.k} workload per step"
+    sample = f"{cols} columns x {iters} fixed iterations of the {args.grid}^3 k={args.k} workload per step"
     line = {
         "impl": "reference", "metric": "RHS-iterations/s", "value": value, "unit": "RHS-iterations/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,

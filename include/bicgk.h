@@ -252,9 +252,10 @@ enum bicgk_option {
   BICGK_OPT_SPMM_BLOCKS_PER_SM = 2, /* blocks of 256 threads per SM for the SpMM (0..32; default:
                                       the occupancy maximum)                                   */
   BICGK_OPT_RHS_GROUPS = 3,         /* 0 (default): k >= 16 is solved as two column groups
-                                      running concurrently on internal streams, k >= 32 as four;
-                                      1: one group; 2..4: that many groups (at most k).
-                                      Profiling mode always runs one group.                    */
+                                      running concurrently on internal streams, k >= 32 as four
+                                      (bicgk_solve_mixed: two from k = 16); 1: one group;
+                                      2..4: that many groups (at most k).  Profiling mode always
+                                      runs one group.                                          */
   BICGK_OPT_FUSED_DOTS = 4,         /* merged forms of Algorithms 2, 5 and 6: take the dot
                                       kernel that follows an SpMM in the listing (delta after
                                       v = A p; group 1 after t = A s, Algorithms 2 and 5) into
