@@ -401,10 +401,10 @@ TABLE2_COPIES = {"classical": 0, "improved": 0, "pipelined": 0, "precond": 2, "r
 
 def fused_passes_saved(variant: str, k: int) -> int:
     """Vector passes per iteration that the dot epilogues of the SpMM save (the library fuses when
-    a solve runs as concurrent column groups, k >= 16): the dot kernel after v = A p re-reads v; the one
+    a solve runs as concurrent column groups, k >= 8): the dot kernel after v = A p re-reads v; the one
     after t = A s re-reads t and s, and s is the product's own x in Algorithm 2 (in Algorithm 5 the
     product reads s^ = M^-1 s, so the epilogue still reads s)."""
-    if k < 16:
+    if k < 8:
         return 0
     return {"classical_merged": 3, "precond_merged": 2, "reordered_merged": 1}.get(variant, 0)
 

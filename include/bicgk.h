@@ -148,7 +148,7 @@ int bicgk_spmm_f32(bicgk_op A, int32_t k, const float *X, float *Y, void *stream
  * Per-column rules where the paper is silent: b_c = 0 gives x_c = 0 with 0
  * iterations; a column whose ||r_0|| already passes the test keeps x0; a
  * column stops independently of the others and is not written afterwards.
- * Execution (bicgk_set_option): from k = 16 the columns run as concurrent
+ * Execution (bicgk_set_option): from k = 8 the columns run as concurrent
  * groups on internal streams joined back to `stream`; the classical and
  * preconditioned forms narrow a group's layout as its columns stop; host
  * blocks that are page-locked are read and written in place.  Columns never
@@ -251,7 +251,7 @@ enum bicgk_option {
                                       default: the occupancy maximum, 2)                      */
   BICGK_OPT_SPMM_BLOCKS_PER_SM = 2, /* blocks of 256 threads per SM for the SpMM (0..32; default:
                                       the occupancy maximum)                                   */
-  BICGK_OPT_RHS_GROUPS = 3,         /* 0 (default): k >= 16 is solved as two column groups
+  BICGK_OPT_RHS_GROUPS = 3,         /* 0 (default): k >= 8 is solved as two column groups
                                       running concurrently on internal streams, k >= 32 as four
                                       (bicgk_solve_mixed: two from k = 16); 1: one group;
                                       2..4: that many groups (at most k).  Profiling mode always

@@ -194,7 +194,9 @@ struct ProfEntry {
 };
 
 constexpr int kMaxGroups = 4;     // column groups solved concurrently (at most)
-constexpr int kSplitMinK = 16;    // smallest k that is split into two groups
+constexpr int kSplitMinK = 8;     // smallest k that is split into two groups
+constexpr int kSplit4MinK = 32;   // smallest k that is split into four groups
+constexpr int kMixedSplitMinK = 16;  // the same for the mixed-precision refinement (two groups)
 constexpr int kMaxLevels = 6;     // column compaction: layouts of kp, kp/2, ..., 1 columns (kp <= 64)
 
 // Solver state of one group of columns: N x kp vectors, per-column scalars and flags, block
@@ -631,15 +633,16 @@ int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, 
 }
 
 // Column groups of a solve of k columns (BICGK_OPT_RHS_GROUPS; the profiling mode runs them as
-// one group but keeps the kernel sequence this count selects).  Automatic: two from k = 16, four
+// one group but keeps the kernel sequence this count selects).  Automatic: two from k = 8, four
 // from k = 32.  Each group's loop runs until its own slowest column stops, and a group that
 // finishes early leaves the GPU to the others, so smaller groups waste fewer iterations on
 // stopped columns: at 128^3, k = 32 four groups of 8 cost the same per iteration as two of 16
 // (3,033 vs 3,047 us) and solved 2.7 % more column-iterations per second over nine right-hand
 // sides (k = 64: -1.2 % per iteration, +2.3 % per solve).  At k = 16 four groups of 4 were 2 %
-// slower per iteration and even per solve.
+// slower per iteration and even per solve; at k = 8 two groups of 4 beat one of 8 (830 vs
+// 872 us per iteration, +4.4 % per solve); at k = 4 two groups of 2 were 17 % slower.
 int num_groups(bicgk_op A, int k) {
-  if (A->opt_groups == 0) return k >= 2 * kSplitMinK ? 4 : k >= kSplitMinK ? 2 : 1;
+  if (A->opt_groups == 0) return k >= kSplit4MinK ? 4 : k >= kSplitMinK ? 2 : 1;
   return A->opt_groups < k ? A->opt_groups : k;
 }
 
@@ -1086,7 +1089,7 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
   // groups from k = 16 (27-point operator, 128^3, k = 32: 98.9 ms against 101.0 for one group and
   // 110.6 for four of 8, whose FP32 products are less efficient)
   const int ngroups =
-      A->profiling ? 1 : A->opt_groups == 0 ? (k >= kSplitMinK ? 2 : 1) : num_groups(A, k);
+      A->profiling ? 1 : A->opt_groups == 0 ? (k >= kMixedSplitMinK ? 2 : 1) : num_groups(A, k);
   int c0[kMaxGroups + 1];
   for (int g = 0; g <= ngroups; ++g) c0[g] = (int)((int64_t)g * k / ngroups);
   int rc;
