@@ -274,7 +274,8 @@ enum bicgk_option {
                                       in place through their mapped device addresses, group by
                                       group, overlapping the transfer with the solve; 1: copy
                                       through a device staging block as for pageable memory.   */
-  BICGK_OPT_COMPACT = 7             /* classical and preconditioned BiCGStab (basic and merged):
+  BICGK_OPT_COMPACT = 7             /* classical, preconditioned and Reordered BiCGStab (basic
+                                      and merged forms):
                                       0 (default): when at most half of a column group's
                                       columns are still iterating, the group continues in a
                                       layout of half the width (down to one column), so stopped

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <string>
 #include <utility>
@@ -528,21 +529,56 @@ int build_graph_seq(bicgk_op A, Workspace &W, const Seq &q, const int *ext_act, 
   return BICGK_OK;
 }
 
+// Roles of a compacted form: the live vectors at the top of an iteration (read before written in
+// the loop body; gathered at a boundary), a slot the form never uses for each of them (the odd
+// levels' copy), and every role the loop uses.
+struct CompactRoles {
+  int nlive = 0;
+  int live[6] = {0, 0, 0, 0, 0, 0};
+  int alt[6] = {0, 0, 0, 0, 0, 0};
+  unsigned loop_mask = 0;
+  unsigned live_mask() const {
+    unsigned m = 0;
+    for (int i = 0; i < nlive; ++i) m |= 1u << live[i];
+    return m;
+  }
+};
+
+CompactRoles compact_roles(int variant) {
+  CompactRoles c;
+  auto mask = [](std::initializer_list<int> roles) {
+    unsigned m = 0;
+    for (int r : roles) m |= 1u << r;
+    return m;
+  };
+  if (variant == BICGK_REORDERED_MERGED || variant == BICGK_REORDERED_PLAIN) {
+    // Algorithm 6: x, r, r^0, v^ (in V_P) and z; the loop also uses v, s, t, q, t^, r~
+    const int live[5] = {V_X, V_R, V_R0, V_P, V_Z}, alt[5] = {V_W, V_Y, V_SH, V_ZH, V_RH};
+    c.nlive = 5;
+    for (int i = 0; i < 5; ++i) c.live[i] = live[i], c.alt[i] = alt[i];
+    c.loop_mask = mask({V_X, V_R, V_R0, V_P, V_V, V_S, V_T, V_Z, V_Q, V_TMP, V_RT});
+  } else {
+    // Algorithms 1, 2, 5: x, r, r^0, p; the loop also uses v, s, t and p^, s^ (in V_Q, V_Y)
+    const int live[4] = {V_X, V_R, V_R0, V_P}, alt[4] = {V_W, V_Z, V_RT, V_SH};
+    c.nlive = 4;
+    for (int i = 0; i < 4; ++i) c.live[i] = live[i], c.alt[i] = alt[i];
+    c.loop_mask = mask({V_X, V_R, V_R0, V_P, V_V, V_S, V_T, V_Q, V_Y});
+  }
+  return c;
+}
+
 // Arguments of compaction level l (kp0 >> l columns): the live vectors alternate between two slot
 // sets so that each boundary gathers into vectors the previous level does not read; the other
 // roles of the loop are rewritten every iteration before they are read.
-KArgs level_args(bicgk_op A, const Workspace &W, int l, cudaGraphConditionalHandle h, const double *invdiag) {
+KArgs level_args(bicgk_op A, const Workspace &W, int l, cudaGraphConditionalHandle h, const double *invdiag,
+                 const CompactRoles &cr) {
   KArgs a = make_args(A, W, 1, h, nullptr, invdiag);
   a.kp = W.kp >> l;
   a.kp_out = W.kp;
   a.cmap = l > 0 ? W.d_cmap + l * kMaxKp : nullptr;
   a.compact = a.kp > 1;
-  if (l & 1) {
-    a.v[V_X] = W.d_vec + (int64_t)V_W * W.vstride;
-    a.v[V_R] = W.d_vec + (int64_t)V_Z * W.vstride;
-    a.v[V_R0] = W.d_vec + (int64_t)V_RT * W.vstride;
-    a.v[V_P] = W.d_vec + (int64_t)V_SH * W.vstride;
-  }
+  if (l & 1)
+    for (int i = 0; i < cr.nlive; ++i) a.v[cr.live[i]] = W.d_vec + (int64_t)cr.alt[i] * W.vstride;
   return a;
 }
 
@@ -557,19 +593,22 @@ KArgs final_args(bicgk_op A, const Workspace &W, const double *invdiag) {
 }
 
 // Whether a solve's group of kp columns narrows its layout as its columns stop
-// (BICGK_OPT_COMPACT).  The forms whose live vectors at the top of an iteration are x, r, r^0, p:
-// classical BiCGStab (Algorithms 1, 2) and preconditioned BiCGStab (Algorithm 5).
+// (BICGK_OPT_COMPACT): classical (Algorithms 1, 2), preconditioned (Algorithm 5) and Reordered
+// (Algorithm 6) BiCGStab, whose live vectors at the top of an iteration are listed above.
 bool compact_columns(bicgk_op A, int variant, int kp) {
   if (A->opt_compact == 1 || A->profiling || kp < 2) return false;
   return variant == BICGK_CLASSICAL_MERGED || variant == BICGK_CLASSICAL_PLAIN ||
-         variant == BICGK_PRECOND_MERGED || variant == BICGK_PRECOND_PLAIN;
+         variant == BICGK_PRECOND_MERGED || variant == BICGK_PRECOND_PLAIN ||
+         variant == BICGK_REORDERED_MERGED || variant == BICGK_REORDERED_PLAIN;
 }
 
 // The graph of a compacted solve: set-up; WHILE(level 0); then per level l = 1..L a compaction
 // boundary (plan + move kernels) and WHILE(level l); a last boundary that writes the final values
 // of the last level; the final kernels on the full layout.  Levels that are not reached cost their
 // boundary kernels' launches only (they return at once).
-int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, const double *invdiag) {
+int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, const double *invdiag,
+                        int variant) {
+  const CompactRoles cr = compact_roles(variant);
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   ge->graph = g;
@@ -578,7 +617,7 @@ int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, 
   cudaGraphConditionalHandle h[kMaxLevels + 1];
   for (int l = 0; l <= L; ++l) CK(cudaGraphConditionalHandleCreate(&h[l], g, 0, 0));
   KArgs lv[kMaxLevels + 1];
-  for (int l = 0; l <= L; ++l) lv[l] = level_args(A, W, l, h[l], invdiag);
+  for (int l = 0; l <= L; ++l) lv[l] = level_args(A, W, l, h[l], invdiag, cr);
   const KArgs af = final_args(A, W, invdiag);
   double *xf = W.d_vec + (int64_t)V_WH * W.vstride;
   cudaStream_t cs = A->cap_stream;
@@ -620,7 +659,7 @@ int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, 
     const KArgs &dst = last ? lv[l] : lv[l + 1];
     cudaError_t e = launch_compact(lv[l], dst, l + 1, last ? 1 : 0, last ? h[l] : h[l + 1], W.d_fin_sc,
                                    W.d_fin_fl, last ? W.d_act : W.d_cmap + (l + 1) * kMaxKp, W.d_act, xf,
-                                   A->nsm * 4, cs);
+                                   cr.live_mask(), cr.loop_mask, A->nsm * 4, cs);
     if (e != cudaSuccess) return fail(e, "capture compaction");
   }
   for (const Step &st : q.fin) {
@@ -1005,7 +1044,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
       auto it = W.graphs.find(key);
       if (it == W.graphs.end()) {
         GraphEntry ge;
-        rc = cg ? build_graph_compact(A, W, q, &ge, jacobi ? A->d_invdiag : nullptr)
+        rc = cg ? build_graph_compact(A, W, q, &ge, jacobi ? A->d_invdiag : nullptr, variant)
                 : build_graph(A, W, variant, jacobi, opts, &ge);
         if (rc) {
           if (ge.exec) cudaGraphExecDestroy(ge.exec);

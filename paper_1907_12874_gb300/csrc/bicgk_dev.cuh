@@ -192,9 +192,12 @@ cudaError_t launch_reset(const KArgs &a, int64_t hist_len, cudaStream_t s);
 // flags of the columns that leave to fin_sc / fin_fl (indexed by the solve's column), compacts
 // the rest, writes dst's column map to cmap_out and the kept source columns to act, and sets the
 // next level's loop condition.  The move kernel writes the x of the columns that leave to xf
-// (kp_out layout) and gathers the live vectors (x, r, r^0, p) of the kept ones into dst's slots.
+// (kp_out layout) and gathers the roles in live_mask (bit r for role r: the vectors an iteration
+// reads before writing them) of the kept ones into dst's slots; at an odd length it zeroes the
+// padding element of dst's roles in loop_mask.
 cudaError_t launch_compact(const KArgs &src, const KArgs &dst, int boundary, int last,
                            cudaGraphConditionalHandle next, double *fin_sc, int *fin_fl, int *cmap_out,
-                           int *act, double *xf, int grid, cudaStream_t s);
+                           int *act, double *xf, unsigned live_mask, unsigned loop_mask, int grid,
+                           cudaStream_t s);
 
 }  // namespace bicgk

@@ -1958,11 +1958,10 @@ __global__ void compact_plan_kernel(KArgs a, KArgs dst, int boundary, int last, 
   }
 }
 
-__global__ void compact_move_kernel(KArgs a, KArgs dst, const int *act, double *xf) {
-  // roles of the classical and preconditioned loops (Algorithms 1, 2, 5): the live ones at the top
-  // of an iteration, and all of them (their padding element is zeroed at an odd length)
-  const int kLive[4] = {V_X, V_R, V_R0, V_P};
-  const int kLoopRoles[9] = {V_X, V_R, V_R0, V_P, V_V, V_S, V_T, V_Q, V_Y};
+// live_mask: the roles an iteration reads before writing (gathered); loop_mask: every role the
+// loop uses (its padding element is zeroed at an odd length); bit r for role r.
+__global__ void compact_move_kernel(KArgs a, KArgs dst, const int *act, double *xf, unsigned live_mask,
+                                    unsigned loop_mask) {
   __shared__ int s_orig[kMaxKp], s_keep[kMaxKp], s_act[kMaxKp];
   const int mode = a.ctl->mode;
   if (mode == 0) return;
@@ -1992,21 +1991,23 @@ __global__ void compact_move_kernel(KArgs a, KArgs dst, const int *act, double *
   for (int64_t e = t0; e < n * kpd; e += stride) {
     const int64_t i = e >> shd;
     const int src = s_act[e & (kpd - 1)];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) dst.v[kLive[r]][e] = src >= 0 ? a.v[kLive[r]][(i << shs) + src] : 0.0;
+    for (int r = 0; r < V_NVEC; ++r)
+      if ((live_mask >> r) & 1u) dst.v[r][e] = src >= 0 ? a.v[r][(i << shs) + src] : 0.0;
   }
   if (((n * kpd) & 1) && t0 == 0)
-    for (int r = 0; r < 9; ++r) dst.v[kLoopRoles[r]][n * kpd] = 0.0;
+    for (int r = 0; r < V_NVEC; ++r)
+      if ((loop_mask >> r) & 1u) dst.v[r][n * kpd] = 0.0;
 }
 }  // namespace
 
 cudaError_t launch_compact(const KArgs &src, const KArgs &dst, int boundary, int last,
                            cudaGraphConditionalHandle next, double *fin_sc, int *fin_fl, int *cmap_out,
-                           int *act, double *xf, int grid, cudaStream_t s) {
+                           int *act, double *xf, unsigned live_mask, unsigned loop_mask, int grid,
+                           cudaStream_t s) {
   compact_plan_kernel<<<1, kMaxKp, 0, s>>>(src, dst, boundary, last, next, fin_sc, fin_fl, cmap_out, act);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  compact_move_kernel<<<grid, 256, 0, s>>>(src, dst, act, xf);
+  compact_move_kernel<<<grid, 256, 0, s>>>(src, dst, act, xf, live_mask, loop_mask);
   return cudaGetLastError();
 }
 

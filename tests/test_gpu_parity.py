@@ -442,7 +442,8 @@ def test_fused_dots_match_separate_kernels(bk, cuda, variant, k, kind):
     _compare(r, Xf, rof)
 
 
-COMPACT_VARIANTS = ["classical_merged", "classical_plain", "precond_merged", "precond_plain"]
+COMPACT_VARIANTS = ["classical_merged", "classical_plain", "precond_merged", "precond_plain",
+                    "reordered_merged", "reordered_plain"]
 
 
 @pytest.mark.parametrize("variant", COMPACT_VARIANTS)
@@ -464,7 +465,7 @@ def test_column_compaction_matches_full_layout(bk, cuda, variant, k):
     Xs = sla.splu(A.to_scipy().tocsc()).solve(B)
     G0 = Xs + 10.0 ** -rng.integers(0, 9, size=k) * rng.standard_normal(B.shape) * np.abs(Xs).max(axis=0)
     G0[:, np.all(B == 0, axis=0)] = 0.0
-    flags = 2 if variant.startswith("precond") and k % 2 else 0   # Jacobi for some
+    flags = 2 if variant.startswith(("precond", "reordered")) and k % 2 else 0   # Jacobi for some
     Bd = torch.from_numpy(B).cuda()
     G0d = torch.from_numpy(G0).cuda()
     res = {}
