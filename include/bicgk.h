@@ -149,8 +149,8 @@ int bicgk_spmm_f32(bicgk_op A, int32_t k, const float *X, float *Y, void *stream
  * iterations; a column whose ||r_0|| already passes the test keeps x0; a
  * column stops independently of the others and is not written afterwards.
  * Execution (bicgk_set_option): from k = 8 the columns run as concurrent
- * groups on internal streams joined back to `stream`; the classical and
- * preconditioned forms narrow a group's layout as its columns stop; host
+ * groups on internal streams joined back to `stream`; a group narrows its
+ * layout as its columns stop; host
  * blocks that are page-locked are read and written in place.  Columns never
  * interact, so these change summation orders only: iterates agree with a
  * one-group solve to rounding, and a column's iteration count can differ by
@@ -274,13 +274,12 @@ enum bicgk_option {
                                       in place through their mapped device addresses, group by
                                       group, overlapping the transfer with the solve; 1: copy
                                       through a device staging block as for pageable memory.   */
-  BICGK_OPT_COMPACT = 7             /* classical, preconditioned and Reordered BiCGStab (basic
-                                      and merged forms):
-                                      0 (default): when at most half of a column group's
-                                      columns are still iterating, the group continues in a
-                                      layout of half the width (down to one column), so stopped
-                                      columns stop costing arithmetic; 1: never.  The iterates
-                                      are those of the full layout up to summation order.     */
+  BICGK_OPT_COMPACT = 7             /* every form.  0 (default): when at most half of a
+                                      column group's columns are still iterating, the group
+                                      continues in a layout of half the width (down to one
+                                      column), so stopped columns stop costing arithmetic;
+                                      1: never.  The iterates are those of the full layout up
+                                      to summation order.                                      */
 };
 
 /*

@@ -227,6 +227,9 @@ struct Workspace {
   int *d_act = nullptr;      // [kMaxKp]
   double *d_fin_sc = nullptr;  // [S_NSLOT][kMaxKp]
   int *d_fin_fl = nullptr;     // [F_NFLAG][kMaxKp]
+  double *d_xf = nullptr;      // final x of a compacted solve (n_rows*kp + 2; made on first use)
+  double *d_cscratch = nullptr;  // in-place compaction scratch (n_rows*kp/2 + 2)
+  int64_t cbuf_elems = 0;      // n_rows*kp the two blocks above were made for
   std::map<int, GraphEntry> graphs;  // per variant, for this kp
 };
 
@@ -390,6 +393,8 @@ void free_workspace(Workspace &W) {
   cudaFree(W.d_act);
   cudaFree(W.d_fin_sc);
   cudaFree(W.d_fin_fl);
+  cudaFree(W.d_xf);
+  cudaFree(W.d_cscratch);
   if (W.done) cudaEventDestroy(W.done);
   if (W.packed) cudaEventDestroy(W.packed);
   if (W.stream) cudaStreamDestroy(W.stream);
@@ -537,6 +542,7 @@ struct CompactRoles {
   int live[6] = {0, 0, 0, 0, 0, 0};
   int alt[6] = {0, 0, 0, 0, 0, 0};
   unsigned loop_mask = 0;
+  unsigned inplace_mask = 0;  // roles compacted in place through a scratch block (no second copy)
   unsigned live_mask() const {
     unsigned m = 0;
     for (int i = 0; i < nlive; ++i) m |= 1u << live[i];
@@ -551,6 +557,15 @@ CompactRoles compact_roles(int variant) {
     for (int r : roles) m |= 1u << r;
     return m;
   };
+  if (variant == BICGK_PIPELINED_MERGED || variant == BICGK_PIPELINED_PLAIN || variant == BICGK_PPIPE_MERGED ||
+      variant == BICGK_PPIPE_PLAIN || variant == BICGK_IMPROVED_MERGED || variant == BICGK_IMPROVED_PLAIN) {
+    // Algorithms 3, 4, 7 carry many vectors from one iteration to the next and use nearly every
+    // slot: every role but b is compacted in place (the ones the loop does not carry cost a
+    // copy of dead data at the few boundaries a solve reaches)
+    for (int r = 0; r < V_NVEC; ++r)
+      if (r != V_B) c.inplace_mask |= 1u << r;
+    return c;
+  }
   if (variant == BICGK_REORDERED_MERGED || variant == BICGK_REORDERED_PLAIN) {
     // Algorithm 6: x, r, r^0, v^ (in V_P) and z; the loop also uses v, s, t, q, t^, r~
     const int live[5] = {V_X, V_R, V_R0, V_P, V_Z}, alt[5] = {V_W, V_Y, V_SH, V_ZH, V_RH};
@@ -583,23 +598,20 @@ KArgs level_args(bicgk_op A, const Workspace &W, int l, cudaGraphConditionalHand
 }
 
 // Arguments of the final kernels and the unpack of a compacted solve: the full layout, x from the
-// final block (V_WH), the final per-column scalars and flags.
+// final block, the final per-column scalars and flags.
 KArgs final_args(bicgk_op A, const Workspace &W, const double *invdiag) {
   KArgs a = make_args(A, W, 0, cudaGraphConditionalHandle{}, nullptr, invdiag);
-  a.v[V_X] = W.d_vec + (int64_t)V_WH * W.vstride;
+  a.v[V_X] = W.d_xf;
   a.sc = W.d_fin_sc;
   a.fl = W.d_fin_fl;
   return a;
 }
 
 // Whether a solve's group of kp columns narrows its layout as its columns stop
-// (BICGK_OPT_COMPACT): classical (Algorithms 1, 2), preconditioned (Algorithm 5) and Reordered
-// (Algorithm 6) BiCGStab, whose live vectors at the top of an iteration are listed above.
+// (BICGK_OPT_COMPACT): every form, with the roles listed above.
 bool compact_columns(bicgk_op A, int variant, int kp) {
-  if (A->opt_compact == 1 || A->profiling || kp < 2) return false;
-  return variant == BICGK_CLASSICAL_MERGED || variant == BICGK_CLASSICAL_PLAIN ||
-         variant == BICGK_PRECOND_MERGED || variant == BICGK_PRECOND_PLAIN ||
-         variant == BICGK_REORDERED_MERGED || variant == BICGK_REORDERED_PLAIN;
+  (void)variant;
+  return A->opt_compact != 1 && !A->profiling && kp >= 2;
 }
 
 // The graph of a compacted solve: set-up; WHILE(level 0); then per level l = 1..L a compaction
@@ -609,6 +621,16 @@ bool compact_columns(bicgk_op A, int variant, int kp) {
 int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, const double *invdiag,
                         int variant) {
   const CompactRoles cr = compact_roles(variant);
+  const int64_t elems = A->n * W.kp;
+  if (W.cbuf_elems != elems) {
+    cudaFree(W.d_xf);
+    cudaFree(W.d_cscratch);
+    W.d_xf = W.d_cscratch = nullptr;
+    W.cbuf_elems = 0;
+    CK(cudaMalloc(&W.d_xf, sizeof(double) * (elems + 2)));
+    CK(cudaMalloc(&W.d_cscratch, sizeof(double) * (elems / 2 + 2)));
+    W.cbuf_elems = elems;
+  }
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   ge->graph = g;
@@ -619,7 +641,7 @@ int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, 
   KArgs lv[kMaxLevels + 1];
   for (int l = 0; l <= L; ++l) lv[l] = level_args(A, W, l, h[l], invdiag, cr);
   const KArgs af = final_args(A, W, invdiag);
-  double *xf = W.d_vec + (int64_t)V_WH * W.vstride;
+  double *xf = W.d_xf;
   cudaStream_t cs = A->cap_stream;
   cudaGraph_t tmp;
   auto fail = [&](cudaError_t e, const char *what) {
@@ -660,6 +682,8 @@ int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, 
     cudaError_t e = launch_compact(lv[l], dst, l + 1, last ? 1 : 0, last ? h[l] : h[l + 1], W.d_fin_sc,
                                    W.d_fin_fl, last ? W.d_act : W.d_cmap + (l + 1) * kMaxKp, W.d_act, xf,
                                    cr.live_mask(), cr.loop_mask, A->nsm * 4, cs);
+    for (int r = 0; e == cudaSuccess && !last && r < V_NVEC; ++r)
+      if ((cr.inplace_mask >> r) & 1u) e = launch_compact_inplace(lv[l], dst, W.d_act, r, W.d_cscratch, A->nsm * 4, cs);
     if (e != cudaSuccess) return fail(e, "capture compaction");
   }
   for (const Step &st : q.fin) {
@@ -1078,7 +1102,10 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     if (cg) {
       int levels = 0;
       while ((W.kp >> levels) > 1) ++levels;
-      launches += 2 * (levels + 1);  // the compaction boundaries' plan and move kernels
+      int inplace = 0;
+      for (unsigned m = compact_roles(variant).inplace_mask; m; m &= m - 1) ++inplace;
+      // the compaction boundaries' plan and move kernels, and the in-place gathers and copies
+      launches += 2 * (levels + 1) + 2 * (int64_t)inplace * levels;
     }
     if (resid_hist)
       CK(cudaMemcpyAsync(W.h_hist, W.d_hist, sizeof(double) * hist_len, cudaMemcpyDeviceToHost, gs));
@@ -1872,7 +1899,7 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
   A.d_col = const_cast<int32_t *>(colidx);
   A.d_val = const_cast<double *>(vals);
   A.stage_cap = 0;  // the k <= 2 SpMM reads CSR entries from global memory (same arithmetic)
-  A.opt_groups = 1;  // one column group, no dot epilogues: bicgk_solve's sequence for k < 16
+  A.opt_groups = 1;  // one column group, no dot epilogues: bicgk_solve's sequence for k < 8
   A.opt_fused = 1;
   Workspace W;
   W.kp = kp;

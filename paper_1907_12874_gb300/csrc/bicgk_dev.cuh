@@ -199,5 +199,10 @@ cudaError_t launch_compact(const KArgs &src, const KArgs &dst, int boundary, int
                            cudaGraphConditionalHandle next, double *fin_sc, int *fin_fl, int *cmap_out,
                            int *act, double *xf, unsigned live_mask, unsigned loop_mask, int grid,
                            cudaStream_t s);
+// In-place compaction of `role` at the same boundary (after launch_compact): the kept columns of
+// src's layout into dst's narrower one in the same vector, through `scratch` (n_rows*dst.kp
+// doubles).  Does nothing unless the boundary narrows.
+cudaError_t launch_compact_inplace(const KArgs &src, const KArgs &dst, const int *act, int role, double *scratch,
+                                   int grid, cudaStream_t s);
 
 }  // namespace bicgk

@@ -1998,7 +1998,42 @@ __global__ void compact_move_kernel(KArgs a, KArgs dst, const int *act, double *
     for (int r = 0; r < V_NVEC; ++r)
       if ((loop_mask >> r) & 1u) dst.v[r][n * kpd] = 0.0;
 }
+
+// In-place compaction of one role (forms whose loops leave no free slot for a second copy):
+// gather the kept columns into a scratch block, then copy it back in the narrower layout (two
+// launches: the gather must read the whole source before the copy overwrites it).
+__global__ void compact_gather_kernel(KArgs a, int kpd, const int *act, int role, double *scratch) {
+  if (a.ctl->mode != 1) return;
+  __shared__ int s_act[kMaxKp];
+  for (int c = threadIdx.x; c < kpd; c += blockDim.x) s_act[c] = act[c];
+  __syncthreads();
+  const int64_t n = a.n;
+  const int shs = __ffs(a.kp) - 1, shd = __ffs(kpd) - 1;
+  const double *src = a.v[role];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * kpd;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = s_act[e & (kpd - 1)];
+    scratch[e] = c >= 0 ? src[((e >> shd) << shs) + c] : 0.0;
+  }
+}
+__global__ void compact_copy_kernel(KArgs dst, int role, const double *scratch) {
+  if (dst.ctl->mode != 1) return;
+  const int64_t m = dst.n * dst.kp;
+  double *d = dst.v[role];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = scratch[e];
+  if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) d[m] = 0.0;  // padding element of an odd length
+}
 }  // namespace
+
+cudaError_t launch_compact_inplace(const KArgs &src, const KArgs &dst, const int *act, int role, double *scratch,
+                                   int grid, cudaStream_t s) {
+  compact_gather_kernel<<<grid, 256, 0, s>>>(src, dst.kp, act, role, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  compact_copy_kernel<<<grid, 256, 0, s>>>(dst, role, scratch);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_compact(const KArgs &src, const KArgs &dst, int boundary, int last,
                            cudaGraphConditionalHandle next, double *fin_sc, int *fin_fl, int *cmap_out,

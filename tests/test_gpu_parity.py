@@ -442,8 +442,24 @@ def test_fused_dots_match_separate_kernels(bk, cuda, variant, k, kind):
     _compare(r, Xf, rof)
 
 
+def _compaction_bars(A, B, X0, tol, maxit, variant, flags, ro):
+    """Bars for comparing two layouts of the same solve: the form's own sensitivity to one
+    rounding unit in b (three draws; Algorithm 3 on the Peclet operator carries it far, the
+    others hardly at all) -- ten times the largest change of the solution (at least 1e-9) and
+    twice the largest change of an iteration count (at least 1)."""
+    sens, spread = 0.0, 0
+    g = np.random.default_rng(31)
+    for _ in range(3):
+        rp = oracle.solve(A, B * (1.0 + 2.0 ** -52 * g.standard_normal(B.shape)), X0=X0, tol=tol,
+                          maxit=maxit, variant=variant, flags=oracle.JACOBI if flags else 0)
+        sens = max(sens, float(_colerr(rp.X, ro.X).max()))
+        spread = max(spread, int(np.abs(rp.iters - ro.iters).max()))
+    return max(1e-9, 10.0 * sens), max(1, 2 * spread)
+
+
 COMPACT_VARIANTS = ["classical_merged", "classical_plain", "precond_merged", "precond_plain",
-                    "reordered_merged", "reordered_plain"]
+                    "reordered_merged", "reordered_plain", "pipelined_merged", "pipelined_plain",
+                    "ppipe_merged", "ppipe_plain", "improved_merged", "improved_plain"]
 
 
 @pytest.mark.parametrize("variant", COMPACT_VARIANTS)
@@ -465,7 +481,7 @@ def test_column_compaction_matches_full_layout(bk, cuda, variant, k):
     Xs = sla.splu(A.to_scipy().tocsc()).solve(B)
     G0 = Xs + 10.0 ** -rng.integers(0, 9, size=k) * rng.standard_normal(B.shape) * np.abs(Xs).max(axis=0)
     G0[:, np.all(B == 0, axis=0)] = 0.0
-    flags = 2 if variant.startswith(("precond", "reordered")) and k % 2 else 0   # Jacobi for some
+    flags = 2 if variant.startswith(("precond", "reordered", "ppipe")) and k % 2 else 0   # Jacobi for some
     Bd = torch.from_numpy(B).cuda()
     G0d = torch.from_numpy(G0).cuda()
     res = {}
@@ -475,23 +491,27 @@ def test_column_compaction_matches_full_layout(bk, cuda, variant, k):
             r = op.solve(Bd, X0=G0d, tol=1e-9, maxit=600, variant=variant, flags=flags)
             res[compact] = (r, r.X.cpu().numpy())
     (r1, X1), (r0, X0) = res[1], res[0]
+    ro = oracle.solve(A, B, X0=G0, tol=1e-9, maxit=600, variant=variant,
+                      flags=oracle.JACOBI if flags else 0)
+    bar, islack = _compaction_bars(A, B, G0, 1e-9, 600, variant, flags, ro)
     assert np.array_equal(r0.status, r1.status)
-    assert np.all(np.abs(r0.iters - r1.iters) <= 1), (r0.iters, r1.iters)
-    assert np.all(_colerr(X0, X1) <= 1e-9), _colerr(X0, X1)
+    assert np.all(np.abs(r0.iters - r1.iters) <= islack), (r0.iters, r1.iters)
+    assert np.all(_colerr(X0, X1) <= bar), _colerr(X0, X1)
     assert np.all(X0[:, np.all(B == 0, axis=0)] == 0.0)
     # histories: every column's entries sit at its own column, NaN after it stopped.  The two
     # layouts sum the dots in different orders, and the difference grows as the residual falls
-    # (2e-6 relative at 1e-8 of the initial residual), so the entries agree to 1e-4.
+    # (2e-6 relative at 1e-8 of the initial residual in the classical form, 8e-4 in the
+    # recurrence-based estimates of the Pipelined forms), so the entries agree to 1e-2; the
+    # columns' histories differ by orders of magnitude (initial errors 1 to 1e-8), so an entry
+    # written at another column's place would not.
     for c in range(k):
         m = int(min(r0.iters[c], r1.iters[c]))
-        np.testing.assert_allclose(r0.hist[: m + 1, c], r1.hist[: m + 1, c], rtol=1e-4)
+        np.testing.assert_allclose(r0.hist[: m + 1, c], r1.hist[: m + 1, c], rtol=1e-2)
         assert np.all(np.isfinite(r0.hist[: r0.iters[c] + 1, c]))
         assert np.all(np.isnan(r0.hist[r0.iters[c] + 1:, c]))
-    ro = oracle.solve(A, B, X0=G0, tol=1e-9, maxit=600, variant=variant,
-                      flags=oracle.JACOBI if flags else 0)
     if k >= 5:
         assert len(set(ro.iters.tolist())) >= 3       # the columns stop at different iterations
-    _compare(r0, X0, ro)
+    _compare(r0, X0, ro, tol_sol=max(SOL_RTOL, bar), iters_slack=islack)
 
 
 @pytest.mark.parametrize("variant", COMPACT_VARIANTS)
@@ -510,10 +530,11 @@ def test_column_compaction_down_to_one_column(bk, cuda, variant):
         rh = op.solve(torch.from_numpy(B).pin_memory(), tol=1e-10, maxit=500, variant=variant)
         bk.set_option(op.handle, bk.OPT_COMPACT, 1)
         rf = op.solve(torch.from_numpy(B).cuda(), tol=1e-10, maxit=500, variant=variant)
-    _compare(r, X, ro)
+    bar, islack = _compaction_bars(A, B, None, 1e-10, 500, variant, 0, ro)
+    _compare(r, X, ro, tol_sol=max(SOL_RTOL, bar), iters_slack=islack)
     assert np.array_equal(rh.X.numpy(), X) and np.array_equal(rh.iters, r.iters)
-    assert np.all(np.abs(rf.iters - r.iters) <= 1)
-    assert np.all(_colerr(rf.X.cpu().numpy(), X) <= 1e-9)
+    assert np.all(np.abs(rf.iters - r.iters) <= islack)
+    assert np.all(_colerr(rf.X.cpu().numpy(), X) <= bar)
     assert np.all(r.iters[[0, 1, 2, 3, 4, 6, 7]] == 0) and r.iters[5] > 10
 
 
