@@ -450,7 +450,7 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
                 torch.cuda.synchronize()
                 s_it = e0.elapsed_time(e1) / 1e3 / nit
                 vecs = TABLE2_VECTORS[base][0 if form == "plain" else 1] + 2 * TABLE2_COPIES[base]
-                # the passes this implementation makes (the SpMM dot epilogues save some at k >= 16)
+                # the passes this implementation makes (the SpMM dot epilogues save some at k >= 8)
                 byts = 2 * (12 * nnz + 4 * (N + 1) + 16 * N * k) + (vecs - fused_passes_saved(v, k)) * 8 * N * k
                 C = nnz / N
                 model = (2 * N * (8 * k * (C + 1) + 4 * (3 * C + 1)) + vecs * 8 * N * k) / (hbm_gbs * 1e9)

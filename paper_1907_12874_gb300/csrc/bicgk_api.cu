@@ -712,9 +712,10 @@ int num_groups(bicgk_op A, int k) {
 // Whether a solve of k columns takes the merged forms' dot kernels into the SpMM epilogues
 // (BICGK_OPT_FUSED_DOTS).  Automatic: when the columns are split into concurrent groups.  There
 // it was measured faster with two groups (fewer kernels per iteration for the groups to share the
-// GPU: 3-4 % at k = 16 and 32) and neutral to 2 % faster with four groups of 8 at k = 32; with one group the
-// fused SpMM's grid-wide reduction costs more than the separate dot kernel (2-8 % slower at
-// k = 1..8).  Profiling mode decides the same way.
+// GPU: 3-4 % at k = 16 and 32; two groups of 4 at k = 8 with it beat one group of 8 without it)
+// and neutral to 2 % faster with four groups of 8 at k = 32; with one group the fused SpMM's
+// grid-wide reduction costs more than the separate dot kernel (2-8 % slower at k = 1..8).
+// Profiling mode decides the same way.
 bool fuse_dots(bicgk_op A, int k) {
   if (A->opt_fused == 1) return false;
   if (A->opt_fused == 2) return true;

@@ -350,7 +350,7 @@ def test_bad_csr_rejected(bk, cuda):
 
 @pytest.mark.parametrize("groups", [0, 3, 4])
 def test_rhs_groups_match_single_group(bk, cuda, groups):
-    """k >= 16 runs as concurrent column groups (two by default at k = 20; three and four forced);
+    """k >= 8 runs as concurrent column groups (two by default at k = 20; three and four forced);
     it must agree with one group (and the oracle), device and host buffers alike."""
     torch = cuda
     A = I.convdiff7(12, peclet=True)
