@@ -88,3 +88,45 @@ def test_mixed_edge_cases(bk, cuda):
         ra = op.solve(torch.from_numpy(B).cuda(), tol=1e-10, maxit=1000)
         rb = op.solve(torch.from_numpy(B).cuda(), tol=1e-10, maxit=1000)
         assert torch.equal(ra.X, rb.X)
+
+
+def test_mixed_column_groups(bk, cuda):
+    """From k = 16 the refinement runs as concurrent column groups (two by default; three and
+    four forced), each with its own FP64 outer and FP32 inner workspaces.  Against one group and
+    the oracle: same status and passes (within one), FP32 iteration totals within the stable
+    operator's spread, every true residual below the tolerance, solutions within the bound the
+    tolerance fixes; host buffers (pageable and page-locked) with X0 give the device call's X."""
+    torch = cuda
+    A = I.convdiff7(12, peclet=True)
+    k, tol = 20, 1e-10
+    B = I.rhs(A.n, k, 7)
+    X0 = 0.1 * I.rhs(A.n, k, 8)
+    Bd, X0d = torch.from_numpy(B).cuda(), torch.from_numpy(X0).cuda()
+    ro = oracle.solve_mixed(A, B, X0=X0, tol=tol, max_outer=20, inner_tol=1e-5, max_inner=2000)
+    inv, lu = _inv_norm(A)
+    Xs = lu.solve(B)
+    res = {}
+    with bk.Operator(A) as op:
+        for groups in (1, 0, 3, 4):
+            bk.set_option(op.handle, bk.OPT_RHS_GROUPS, groups)
+            r = op.solve_mixed(Bd, X0=X0d, tol=tol, max_outer=20, inner_tol=1e-5, max_inner=2000)
+            assert bk.last_stats(op.handle)["groups"] == (groups or 2)
+            res[groups] = (r, r.X.cpu().numpy())
+        bk.set_option(op.handle, bk.OPT_RHS_GROUPS, 0)
+        rh = op.solve_mixed(B, X0=X0, tol=tol, max_outer=20, inner_tol=1e-5, max_inner=2000)
+        rp = op.solve_mixed(torch.from_numpy(B).pin_memory(), X0=torch.from_numpy(X0).pin_memory(), tol=tol,
+                            max_outer=20, inner_tol=1e-5, max_inner=2000)
+    for groups, (r, X) in res.items():
+        assert np.all(r.status == 0) and np.array_equal(r.status, ro.status), groups
+        assert np.all(np.abs(r.outer_iters - ro.outer_iters) <= 1), (groups, r.outer_iters, ro.outer_iters)
+        # FP32 totals where the pass counts agree (a column that needs one more pass near the
+        # tolerance adds a whole inner solve)
+        same = r.outer_iters == ro.outer_iters
+        assert np.all((np.abs(r.inner_iters - ro.inner_iters) <= np.maximum(3, 0.2 * ro.inner_iters))[same]), groups
+        true = np.linalg.norm(B - A.to_scipy() @ X, axis=0) / np.linalg.norm(B, axis=0)
+        assert np.all(true < tol), (groups, true)
+        err = np.linalg.norm(X - Xs, axis=0)
+        assert np.all(err <= 1.5 * inv * true * np.linalg.norm(B, axis=0) + 1e-14), groups
+    X2 = res[0][1]
+    assert np.array_equal(rh.X, X2) and np.array_equal(rh.inner_iters, res[0][0].inner_iters)
+    assert np.array_equal(rp.X.numpy(), X2)
