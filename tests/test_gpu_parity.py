@@ -553,3 +553,21 @@ def test_column_compaction_idle_without_stops(bk, cuda, variant):
             out.append((r.X.cpu().numpy(), r.hist.copy(), r.iters.copy(), r.true_relres.copy()))
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b, equal_nan=True)
+
+
+def test_options_validate_their_values(bk, cuda):
+    """Every execution option takes only its documented values (BICGK_E_INVALID otherwise)."""
+    A = I.convdiff7(6)
+    with bk.Operator(A) as op:
+        for opt, good, bad in ((bk.OPT_RHS_GROUPS, (0, 1, 2, 3, 4), (-1, 5)),
+                               (bk.OPT_FUSED_DOTS, (0, 1, 2), (-1, 3)),
+                               (bk.OPT_THETA_IN_S, (0, 1, 2), (-1, 3)),
+                               (bk.OPT_HOST_ZERO_COPY, (0, 1), (-1, 2)),
+                               (bk.OPT_COMPACT, (0, 1), (-1, 2))):
+            for v in good:
+                bk.set_option(op.handle, opt, v)
+            for v in bad:
+                with pytest.raises(bk.BicgkError):
+                    bk.set_option(op.handle, opt, v)
+        with pytest.raises(bk.BicgkError):
+            bk.set_option(op.handle, 99, 0)
