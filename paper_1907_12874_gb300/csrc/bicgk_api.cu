@@ -18,6 +18,7 @@
 #include <initializer_list>
 #include <map>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -249,6 +250,8 @@ struct bicgk_op_s {
   double *d_invdiag = nullptr;  // Jacobi preconditioner 1/a_ii (made on first use)
   double *d_stage[2] = {nullptr, nullptr};  // caller-layout staging for host-memory calls
   int64_t stage_elems = 0;
+  void *h_bounce = nullptr;  // two page-locked chunks for copies of pageable host blocks
+  cudaEvent_t bounce_ev[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t fork = nullptr;
   // profiling
@@ -458,6 +461,96 @@ const void *mapped_host_ptr(const void *p) {
     return nullptr;
   }
   return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Copies between the device and pageable host blocks.  A cudaMemcpyAsync from or to pageable
+// memory measured about 3 GB/s on these hosts (the driver stages it); instead the block moves
+// through two page-locked chunks of the operator, host threads filling (or draining) one chunk
+// while the DMA engine moves the other.
+constexpr size_t kBounceBytes = size_t(32) << 20;
+
+void parallel_memcpy(void *dst, const void *src, size_t bytes) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const unsigned nt = hw < 8 ? (hw ? hw : 1) : 8;
+  if (nt <= 1 || bytes < (size_t(1) << 20)) {
+    std::memcpy(dst, src, bytes);
+    return;
+  }
+  std::vector<std::thread> th;
+  const size_t part = (bytes + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    const size_t off = t * part;
+    if (off >= bytes) break;
+    const size_t len = part < bytes - off ? part : bytes - off;
+    th.emplace_back([=] { std::memcpy(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, len); });
+  }
+  for (std::thread &x : th) x.join();
+}
+
+int ensure_bounce(bicgk_op A) {
+  if (A->h_bounce) return BICGK_OK;
+  for (int i = 0; i < 2; ++i)
+    if (!A->bounce_ev[i]) CK(cudaEventCreateWithFlags(&A->bounce_ev[i], cudaEventDisableTiming));
+  CK(cudaMallocHost(&A->h_bounce, 2 * kBounceBytes));
+  return BICGK_OK;
+}
+
+// dst (device) <- src (pageable host), queued on s; src may be reused when this returns.
+int copy_in_pageable(bicgk_op A, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  int rc = ensure_bounce(A);
+  if (rc) return rc;
+  for (size_t off = 0, i = 0; off < bytes; off += kBounceBytes, ++i) {
+    const int slot = (int)(i & 1);
+    const size_t len = kBounceBytes < bytes - off ? kBounceBytes : bytes - off;
+    char *b = static_cast<char *>(A->h_bounce) + slot * kBounceBytes;
+    CK(cudaEventSynchronize(A->bounce_ev[slot]));  // the chunk's previous copy has finished
+    parallel_memcpy(b, static_cast<const char *>(src) + off, len);
+    CK(cudaMemcpyAsync(static_cast<char *>(dst) + off, b, len, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(A->bounce_ev[slot], s));
+  }
+  return BICGK_OK;
+}
+
+// dst (pageable host) <- src (device) after the work queued on s; returns when dst is written.
+int copy_out_pageable(bicgk_op A, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  int rc = ensure_bounce(A);
+  if (rc) return rc;
+  const size_t n = (bytes + kBounceBytes - 1) / kBounceBytes;
+  for (size_t i = 0; i < n && i < 2; ++i) {  // two chunks in flight
+    const size_t off = i * kBounceBytes, len = kBounceBytes < bytes - off ? kBounceBytes : bytes - off;
+    CK(cudaMemcpyAsync(static_cast<char *>(A->h_bounce) + (i & 1) * kBounceBytes,
+                       static_cast<const char *>(src) + off, len, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(A->bounce_ev[i & 1], s));
+  }
+  for (size_t i = 0; i < n; ++i) {
+    const int slot = (int)(i & 1);
+    const size_t off = i * kBounceBytes, len = kBounceBytes < bytes - off ? kBounceBytes : bytes - off;
+    CK(cudaEventSynchronize(A->bounce_ev[slot]));
+    parallel_memcpy(static_cast<char *>(dst) + off, static_cast<char *>(A->h_bounce) + slot * kBounceBytes, len);
+    if (i + 2 < n) {  // the drained chunk takes the one after next
+      const size_t o2 = (i + 2) * kBounceBytes, l2 = kBounceBytes < bytes - o2 ? kBounceBytes : bytes - o2;
+      CK(cudaMemcpyAsync(static_cast<char *>(A->h_bounce) + slot * kBounceBytes, static_cast<const char *>(src) + o2,
+                         l2, cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(A->bounce_ev[slot], s));
+    }
+  }
+  return BICGK_OK;
+}
+
+// Host block -> device: a plain copy from page-locked memory, the chunked one from pageable.
+int copy_in_host(bicgk_op A, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (mapped_host_ptr(src)) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+    return BICGK_OK;
+  }
+  return copy_in_pageable(A, dst, src, bytes, s);
+}
+int copy_out_host(bicgk_op A, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (mapped_host_ptr(dst)) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+    return BICGK_OK;
+  }
+  return copy_out_pageable(A, dst, src, bytes, s);
 }
 
 int ensure_stage(bicgk_op A, int64_t elems) {
@@ -905,6 +998,9 @@ int bicgk_op_destroy(bicgk_op A) {
   cudaFree(A->d_val);
   cudaFree(A->d_stage[0]);
   cudaFree(A->d_stage[1]);
+  cudaFreeHost(A->h_bounce);
+  for (cudaEvent_t e : A->bounce_ev)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : A->ev) cudaEventDestroy(e);
   if (A->fork) cudaEventDestroy(A->fork);
   if (A->cap_stream) cudaStreamDestroy(A->cap_stream);
@@ -1030,10 +1126,10 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
   const bool staged = mem == BICGK_MEM_HOST && !zero_copy;
   if (staged) {
     if ((rc = ensure_stage(A, A->n * k))) return rc;
-    CK(cudaMemcpyAsync(A->d_stage[0], B, sizeof(double) * A->n * k, cudaMemcpyHostToDevice, s));
+    if ((rc = copy_in_host(A, A->d_stage[0], B, sizeof(double) * A->n * k, s))) return rc;
     dB = A->d_stage[0];
     if (X0) {
-      CK(cudaMemcpyAsync(A->d_stage[1], X0, sizeof(double) * A->n * k, cudaMemcpyHostToDevice, s));
+      if ((rc = copy_in_host(A, A->d_stage[1], X0, sizeof(double) * A->n * k, s))) return rc;
       dX0 = A->d_stage[1];
     }
     dX = A->d_stage[0];  // X overwrites the staged B after both groups have packed it
@@ -1116,7 +1212,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     }
     launches += 1;  // unpack
   }
-  if (staged) CK(cudaMemcpyAsync(X, dX, sizeof(double) * A->n * k, cudaMemcpyDeviceToHost, s));
+  if (staged && (rc = copy_out_host(A, X, dX, sizeof(double) * A->n * k, s))) return rc;
   CK(cudaStreamSynchronize(s));
   int32_t loop_iters = 0;
   for (int g = 0; g < ngroups; ++g) {
@@ -1178,10 +1274,10 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
   double *dX = X;
   if (mem == BICGK_MEM_HOST) {
     if ((rc = ensure_stage(A, A->n * k))) return rc;
-    CK(cudaMemcpyAsync(A->d_stage[0], B, sizeof(double) * A->n * k, cudaMemcpyHostToDevice, s));
+    if ((rc = copy_in_host(A, A->d_stage[0], B, sizeof(double) * A->n * k, s))) return rc;
     dB = A->d_stage[0];
     if (X0) {
-      CK(cudaMemcpyAsync(A->d_stage[1], X0, sizeof(double) * A->n * k, cudaMemcpyHostToDevice, s));
+      if ((rc = copy_in_host(A, A->d_stage[1], X0, sizeof(double) * A->n * k, s))) return rc;
       dX0 = A->d_stage[1];
     }
     dX = A->d_stage[1];  // X goes to the second staging block: the groups pack B from the first
@@ -1301,7 +1397,7 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
     }
     launches += 1;
   }
-  if (mem == BICGK_MEM_HOST) CK(cudaMemcpyAsync(X, dX, sizeof(double) * A->n * k, cudaMemcpyDeviceToHost, s));
+  if (mem == BICGK_MEM_HOST && (rc = copy_out_host(A, X, dX, sizeof(double) * A->n * k, s))) return rc;
   CK(cudaStreamSynchronize(s));
   int32_t loop_max = 0;
   for (int g = 0; g < ngroups; ++g) {
