@@ -478,12 +478,18 @@ void parallel_memcpy(void *dst, const void *src, size_t bytes) {
   }
   std::vector<std::thread> th;
   const size_t part = (bytes + nt - 1) / nt;
-  for (unsigned t = 0; t < nt; ++t) {
-    const size_t off = t * part;
-    if (off >= bytes) break;
-    const size_t len = part < bytes - off ? part : bytes - off;
-    th.emplace_back([=] { std::memcpy(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, len); });
+  size_t done = 0;  // bytes handed to threads; the rest is copied here (also if a thread cannot start)
+  try {
+    for (unsigned t = 0; t < nt; ++t) {
+      const size_t off = t * part;
+      if (off >= bytes) break;
+      const size_t len = part < bytes - off ? part : bytes - off;
+      th.emplace_back([=] { std::memcpy(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, len); });
+      done = off + len;
+    }
+  } catch (...) {
   }
+  if (done < bytes) std::memcpy(static_cast<char *>(dst) + done, static_cast<const char *>(src) + done, bytes - done);
   for (std::thread &x : th) x.join();
 }
 
