@@ -46,3 +46,24 @@ def test_binding_has_no_cpu_fallback():
     """The binding calls the library for every solve; it has no numpy/torch solver path."""
     src = open(os.path.join(ROOT, "paper_1907_12874_gb300", "bicgk.py")).read()
     assert "oracle" not in src and "np.linalg" not in src and "torch.linalg" not in src
+
+
+def _header_enum(prefix):
+    text = open(os.path.join(ROOT, "include", "bicgk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(" + prefix + r"[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+
+
+def test_binding_constants_match_the_header():
+    """The binding's option, flag, memory-space and form numbers are the header's."""
+    opts = _header_enum("BICGK_OPT_")
+    assert opts, "no options declared"
+    for name, value in opts.items():
+        assert getattr(bicgk, name[len("BICGK_"):]) == value, name
+    assert bicgk.FLAG_NO_STOP_TEST == _header_enum("BICGK_FLAG_")["BICGK_FLAG_NO_STOP_TEST"]
+    assert bicgk.FLAG_JACOBI == _header_enum("BICGK_FLAG_")["BICGK_FLAG_JACOBI"]
+    forms = {k: v for k, v in _header_enum("BICGK_").items()
+             if k.endswith(("_PLAIN", "_MERGED"))}
+    assert len(forms) == 12
+    for name, value in forms.items():
+        assert bicgk.VARIANTS[name[len("BICGK_"):].lower()] == value, name
