@@ -170,7 +170,29 @@ def kernel_algorithmic(name: str, n: int, nnz: int, k: int, variant: str = "clas
     return (r + w) * vec, fl * n * k
 
 
-KERNEL_SOURCES = {"spmm": ("bicgk_dev.cuh", "bicgk_spmm.cu"), "vec": ("bicgk_dev.cuh", "bicgk_vec.cu")}
+def launch_columns(name: str, k: int, groups: int) -> int:
+    """Columns one launch of a kernel processes: the _k<kp> suffix of a product's name, else the
+    padded width of the solve's column groups (the streaming kernels run per group)."""
+    m = re.search(r"_k(\d+)$", name)
+    if m:
+        return int(m.group(1))
+    kg = -(-k // max(1, groups))
+    return 1 << (kg - 1).bit_length()
+
+
+# FP64 FMAs per element and column-iteration of the vector operations of a form (the products add
+# 2 nnz/N): classical, basic and merged: delta 1, s 1, phi/psi/theta 3 (or theta with s), x 2, r 1,
+# rho 1, p 2 (the basic form's (r, r) replaces theta)
+VECTOR_FMA = {"classical_merged": 11, "classical_plain": 11}
+
+
+def solve_fma_per_element(variant: str, A):
+    v = VECTOR_FMA.get(variant)
+    return None if v is None else v + 2.0 * A.nnz / A.n
+
+
+KERNEL_SOURCES = {"spmm": ("bicgk_dev.cuh", "bicgk_spmm.cu"),
+                  "vec": ("bicgk_dev.cuh", "bicgk_rules.cuh", "bicgk_vec.cu")}
 
 
 def kernel_source_kind(name: str) -> str:
@@ -207,13 +229,40 @@ def recorded_traffic():
     return out
 
 
-def cpu_oracle_rate(A, B, variant, cols: int, iters: int):
-    """Oracle RHS-iterations/s on `cols` columns x `iters` fixed iterations of the workload."""
+def cpu_oracle_rate(A, B, variant, cols: int, iters: int, want=False):
+    """Oracle RHS-iterations/s on `cols` columns x `iters` fixed iterations of the workload (and,
+    with `want`, the oracle's result)."""
     import oracle
     t0 = time.perf_counter()
-    oracle.solve(A, B[:, :cols], tol=0.0, maxit=iters, variant=variant, flags=oracle.NO_STOP_TEST)
+    r = oracle.solve(A, B[:, :cols], tol=0.0, maxit=iters, variant=variant, flags=oracle.NO_STOP_TEST)
     dt = time.perf_counter() - t0
-    return cols * iters / dt, dt
+    return (cols * iters / dt, dt, r) if want else (cols * iters / dt, dt)
+
+
+def oracle_columns(A, B, jobs, workers=None):
+    """The oracle on single columns concurrently (columns never interact, so a column solved alone
+    is the column of a k-column solve).  jobs: list of (column, kwargs for oracle.solve or, with
+    kwargs["mixed"], oracle.solve_mixed); returns the results in order."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(job):
+        c, kw = job
+        kw = dict(kw)
+        mixed = kw.pop("mixed", False)
+        x0 = kw.pop("X0", None)
+        oracle.set_threads(1)
+        b = np.ascontiguousarray(B[:, [c]])
+        return (oracle.solve_mixed if mixed else oracle.solve)(A, b, X0=x0, **kw)
+
+    with ThreadPoolExecutor(max(1, min(len(jobs), workers or os.cpu_count() or 1))) as ex:
+        return list(ex.map(one, jobs))
+
+
+def colerr(X, Xo):
+    """Relative 2-norm difference per column."""
+    den = np.linalg.norm(Xo, axis=0)
+    return np.linalg.norm(X - Xo, axis=0) / np.where(den == 0, 1.0, den)
 
 
 def dist_setup(args):
@@ -303,7 +352,8 @@ def mixed_section(args, bicgk, inputs, torch, dev):
     n = args.mixed_grid
     k = 32
     A = inputs.perturbed27(n, seed=7)
-    B = torch.from_numpy(inputs.rhs(A.n, k, 3)).to(dev)
+    Bh = inputs.rhs(A.n, k, 3)
+    B = torch.from_numpy(Bh).to(dev)
     res = {"workload": f"perturbed27 {n}^3 (off-diagonals -U[0.5,1.5], diag = sum|off| + 1), k={k}, "
                        f"rel tol 1e-10", "n_rows": A.n, "nnz": A.nnz}
 
@@ -323,6 +373,8 @@ def mixed_section(args, bicgk, inputs, torch, dev):
         ms64, r64 = timed_solve(lambda: op64.solve(B, X=X, tol=1e-10, maxit=5000, want_hist=False))
         msm, rm = timed_solve(lambda: opm.solve_mixed(B, X=X, tol=1e-10, max_outer=20, inner_tol=1e-5,
                                                       max_inner=5000, want_hist=False))
+        cols = [0, 31]       # one in each of the two column groups
+        Xm = X[:, cols].cpu().numpy()
         # the same comparison at relative residual 1e-8
         ms64b, r64b = timed_solve(lambda: op64.solve(B, X=X, tol=1e-8, maxit=5000, want_hist=False))
         msmb, rmb = timed_solve(lambda: opm.solve_mixed(B, X=X, tol=1e-8, max_outer=20, inner_tol=1e-5,
@@ -341,30 +393,49 @@ def mixed_section(args, bicgk, inputs, torch, dev):
         "mixed_max_true_relres": float(rm.true_relres.max()), "mixed_converged": bool((rm.status == 0).all()),
         "speedup_vs_fp64": ms64 / msm,
     })
+    # error against the oracle's refinement (oracle.solve_mixed) on the sampled columns
+    kw = dict(mixed=True, tol=1e-10, max_outer=20, inner_tol=1e-5, max_inner=5000)
+    ro = oracle_columns(A, Bh, [(c, kw) for c in cols])
+    Xo = np.concatenate([r.X for r in ro], axis=1)
+    res["oracle_err"] = {"value": float(colerr(Xm, Xo).max()),
+                         "max_abs_over_max_abs_x": float(np.abs(Xm - Xo).max() / np.abs(Xo).max()),
+                         "what": f"columns {cols} of the rel. tol 1e-10 mixed solve against oracle.solve_mixed: "
+                                 "max relative 2-norm difference, and the largest elementwise difference "
+                                 "over max |x|"}
     return res
 
 
 def batch_section(args, bicgk, inputs, torch, dev, nsys=64):
     """64 independent 7-point convection-diffusion systems, grids U{16..64}^3, k U{1..8}, rel tol 1e-8.
 
-    Autotuned launch shapes; the batched graph (one launch for all systems) against the
-    per-system launch loop (bicgk_solve per system) with the same shapes; CUDA events.
+    Three ways to run the same batch, CUDA events around each: the persistent mode (one cooperative
+    kernel launch for every system, its rows per CTA tile autotuned), the batched graph (one graph
+    launch, a branch per system) and the per-system launch loop (bicgk_solve per system), the last
+    two with the autotuned per-system launch shapes.
     """
-    u = inputs.uniform01(11, 2 * nsys)
-    grids = [int(16 + np.floor(x * 49)) for x in u[:nsys]]
-    ks = [int(1 + np.floor(x * 8)) for x in u[nsys:]]
+    import oracle
+    grids, ks = inputs.batch_draws(nsys)
     csrs = [inputs.convdiff7(n) for n in grids]
     Bs = [torch.from_numpy(inputs.rhs(c.n, k, 200 + i)).to(dev) for i, (c, k) in enumerate(zip(csrs, ks))]
     Xs = [torch.empty_like(b) for b in Bs]
     res = {"workload": f"{nsys} convdiff7 systems, grids U{{16..64}}^3, k U{{1..8}}, rel tol 1e-8, classical_merged",
            "rows_total": int(sum(c.n for c in csrs)), "rhs_total": int(sum(ks))}
+    sample = sorted({int(np.argmin(grids)), int(np.argmax(grids)), int(np.argmax(ks))})
+    got = {}
     with bicgk.Batch(csrs, ks) as bt:
         t0 = time.perf_counter()
         bt.tune(reps=5)
         torch.cuda.synchronize()
         res["tune_s"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        rows = bt.tune_persistent(reps=3)
+        torch.cuda.synchronize()
+        res["tune_persistent_s"] = time.perf_counter() - t0
+        res["persistent_rows_per_tile"] = sorted({int(r) for r in rows})
+        res["persistent_launch"] = bt.persistent_info()
         out = {}
-        for name, mode in (("graph", bicgk.BATCH_GRAPH), ("loop", bicgk.BATCH_LOOP)):
+        for name, mode in (("persistent", bicgk.BATCH_PERSISTENT), ("graph", bicgk.BATCH_GRAPH),
+                           ("loop", bicgk.BATCH_LOOP)):
             bt.solve(Bs, Xs, tol=1e-8, maxit=5000, mode=mode)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -378,8 +449,26 @@ def batch_section(args, bicgk, inputs, torch, dev, nsys=64):
             out[name] = {"ms": ms, "rhs_iterations_per_s": float(iters.sum()) / (ms / 1e3),
                          "kernel_launches": bt.last_launches(), "converged": bool((status == 0).all()),
                          "max_true_relres": float(trr.max())}
+            if mode == bicgk.BATCH_PERSISTENT:
+                out[name]["loop_iterations"] = bt.last_loop_iters()
+            got[name] = {i: Xs[i].cpu().numpy() for i in sample}
         res.update(out)
         res["graph_speedup_vs_loop"] = out["loop"]["ms"] / out["graph"]["ms"]
+        res["persistent_speedup_vs_loop"] = out["loop"]["ms"] / out["persistent"]["ms"]
+        res["persistent_speedup_vs_graph"] = out["graph"]["ms"] / out["persistent"]["ms"]
+    # error against the oracle's to-tolerance solves of sampled systems: the smallest and the largest
+    # grids, a system with the most right-hand sides
+    errs = {}
+    for i in sample:
+        Bh = Bs[i].cpu().numpy()
+        ro = oracle_columns(csrs[i], Bh, [(c, dict(tol=1e-8, maxit=5000)) for c in range(ks[i])])
+        Xo = np.concatenate([r.X for r in ro], axis=1)
+        for name in got:
+            errs[f"{name}: system {i} ({grids[i]}^3, k={ks[i]})"] = float(colerr(got[name][i], Xo).max())
+    res["oracle_err"] = {"value": max(errs.values()), "systems": errs,
+                         "what": "max relative 2-norm difference per column against the oracle's solve to the "
+                                 "same tolerance (this nearly symmetric operator amplifies rounding: both "
+                                 "stopping iterates sit within the tolerance of the exact solution)"}
     return res
 
 
@@ -431,13 +520,17 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
     12 nnz + 4 (N + 1) + 16 N k bytes (x read once) and 8 N k bytes per vector pass of Table 2
     (M^-1 copies as one read and one write each).  paper_model_ms is the paper's data-transfer
     model T = Sigma / B (Eq. SpMV_mem, x read C + 1 times) with B the measured HBM bandwidth."""
+    import oracle
     N, nnz = A.n, A.nnz
-    res = {"workload": f"{args.grid}^3 benchmark operator, {nit} fixed iterations per form and k",
+    res = {"workload": f"{args.grid}^3 benchmark operator, {nit} fixed iterations per form and k; oracle_err: "
+                       f"column 0 after the {nit} iterations against the oracle's",
            "hbm_gbs": hbm_gbs, "rows": {}}
     with bicgk.Operator(A) as opw:
         for k in (1, 2, 4, 8, 16, 32):
-            Bk = torch.from_numpy(inputs.rhs(N, k, 2)).to(dev)
+            Bh = inputs.rhs(N, k, 2)
+            Bk = torch.from_numpy(Bh).to(dev)
             Xk = torch.empty_like(Bk)
+            col0 = {}
             for v in bicgk.VARIANTS:
                 base, form = v.rsplit("_", 1)
                 opw.solve(Bk, X=Xk, tol=0.0, maxit=3, variant=v, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
@@ -458,6 +551,10 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
                                             "algorithmic_gb_per_iter": byts / 1e9,
                                             "hbm_frac": byts / s_it / (hbm_gbs * 1e9),
                                             "paper_model_ms": model * 1e3}
+                col0[v] = Xk[:, :1].cpu().numpy()
+            jobs = [(0, dict(tol=0.0, maxit=nit, variant=v, flags=oracle.NO_STOP_TEST)) for v in col0]
+            for v, ro in zip(col0, oracle_columns(A, Bh, jobs)):
+                res["rows"][f"{v}/k{k}"]["oracle_err"] = float(colerr(col0[v], ro.X)[0])
     return res
 
 
@@ -474,10 +571,13 @@ def replica_section(args, bicgk, inputs, torch, dev, hbm_gbs):
     res = {"workload": f"7-point Poisson {n}^3 ({N} rows, {A.nnz} nnz), x0 = 0, B U[-1,1] seed 5, "
                        f"{nit} fixed iterations per timing (the paper uses 1000; the time per iteration "
                        f"is steady)", "hbm_gbs": hbm_gbs, "rows": {}}
+    import oracle
     with bicgk.Operator(A) as op:
         for m in (1, 4, 16):
-            B = torch.from_numpy(inputs.rhs(N, m, 5)).to(dev)
+            Bh = inputs.rhs(N, m, 5)
+            B = torch.from_numpy(Bh).to(dev)
             X = torch.empty_like(B)
+            chk = []
             sig_mul = N * (8 * m * (C + 1) + 4 * (3 * C + 1))
             for base in PAPER_TABLE4:
                 row = {}
@@ -496,10 +596,18 @@ def replica_section(args, bicgk, inputs, torch, dev, hbm_gbs):
                     model_ms = (2 * sig_mul + vecs * 8 * N * m) / (hbm_gbs * 1e9) * 1e3
                     row[form] = {"ms_per_iter": ms, "model_ms": model_ms,
                                  "all_columns_ran": bool((r.status == 1).all() and (r.iters == nit).all())}
+                # error against the oracle: column 0 after 5 fixed iterations of each form
+                for form in ("plain", "merged"):
+                    v = f"{base}_{form}"
+                    op.solve(B, X=X, tol=0.0, maxit=5, variant=v, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
+                    chk.append((f"{base}/m{m}", form, v, X[:, :1].cpu().numpy()))
                 p_basic, p_merged = PAPER_TABLE4[base][m]
                 row["merged_gain"] = row["plain"]["ms_per_iter"] / row["merged"]["ms_per_iter"] - 1
                 row["paper_lomonosov2_s"] = {"basic": p_basic, "merged": p_merged, "gain": p_basic / p_merged - 1}
                 res["rows"][f"{base}/m{m}"] = row
+            jobs = [(0, dict(tol=0.0, maxit=5, variant=v, flags=oracle.NO_STOP_TEST)) for _, _, v, _ in chk]
+            for (key, form, _, x), ro in zip(chk, oracle_columns(A, Bh, jobs)):
+                res["rows"][key][form]["oracle_err_5_iterations"] = float(colerr(x, ro.X)[0])
     return res
 
 
@@ -544,9 +652,26 @@ def adjoint_section(args, bicgk, inputs, torch, dev):
         ms_f = e0.elapsed_time(e1) / reps
     S = A.to_scipy()
     adj_res = float(np.linalg.norm(S.T @ gB.cpu().numpy() - W.cpu().numpy()) / np.linalg.norm(W.cpu().numpy()))
+    # error against the dense reference gradients (oracle.adjoint_dense) on the 12^3 instance
+    import oracle
+    A12 = inputs.convdiff7(12)
+    B12 = inputs.rhs(A12.n, 8, 5)
+    W12 = inputs.rhs(A12.n, 8, 6)
+    vals12 = torch.from_numpy(A12.vals.copy()).to(dev).requires_grad_(True)
+    B12t = torch.from_numpy(B12).to(dev).requires_grad_(True)
+    X12 = autograd.solve(vals12, B12t, torch.from_numpy(A12.rowptr).to(dev), torch.from_numpy(A12.colidx).to(dev),
+                         tol=1e-12, maxit=5000)
+    (torch.from_numpy(W12).to(dev) * X12).sum().backward()
+    Xr, dBr, dvr = oracle.adjoint_dense(A12, B12, W12)
+    gb_err = float(np.abs(B12t.grad.cpu().numpy() - dBr).max() / np.abs(dBr).max())
+    gv_err = float(np.abs(vals12.grad.cpu().numpy() - dvr).max() / np.abs(dvr).max())
     return {"workload": "convdiff7 64^3 (262,144 rows, 1,810,432 nnz), k=8, loss = sum(w*X), rel tol 1e-8",
             "forward_backward_ms": ms_fb, "forward_solve_ms": ms_f, "backward_over_forward": ms_fb / ms_f - 1.0,
-            "adjoint_relres": adj_res, "grad_vals_finite": bool(torch.isfinite(gv).all())}
+            "adjoint_relres": adj_res, "grad_vals_finite": bool(torch.isfinite(gv).all()),
+            "oracle_err": {"value": max(gb_err, gv_err), "dL_dB": gb_err, "dL_dA": gv_err,
+                           "what": "12^3 instance (1,728 rows), k = 8, solves to rel. tol 1e-12: largest "
+                                   "elementwise difference of the gradients from oracle.adjoint_dense (dense "
+                                   "LAPACK solves) over the largest gradient entry"}}
 
 
 def main():
@@ -613,6 +738,11 @@ def main():
     # headline: device-resident inputs
     ms, its, launches, results, clocks = timed(args.variant, args.steps, args.warmup, clocks=not args.minimal)
     groups = bicgk.last_stats(op.handle)["groups"]
+    # sampled columns of the timed solve, for the oracle's to-tolerance solves below
+    tol_cols = [c for c in (0, 9, 18, 27) if c < args.k]
+    X_head = Xd[:, tol_cols].cpu().numpy()
+    it_head = results[-1].iters[tol_cols].copy()
+    bg_pool, bg = None, {}
     value = aggregate_rate(float(its), ms, pg, dev)
     ms = max_over_ranks(ms, pg, dev)
     last = results[-1]
@@ -679,15 +809,31 @@ def main():
             out["plain"] = {"variant": plain, "value": vp, "ms_per_step": msp / args.steps,
                             "merged_speedup": value / vp}
 
-    # per-kernel event times of one solve (profiling mode, same stream) -> roofline of the dominant kernel
+    # the oracle's to-tolerance solves of the sampled columns, on four host threads while the GPU
+    # sections below run (columns never interact, so a column solved alone is that column of the solve)
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+
+        def oracle_tol(c):
+            oracle.set_threads(1)
+            return oracle.solve(A, np.ascontiguousarray(B_host[:, [c]]), tol=args.tol, maxit=args.maxit,
+                                variant=args.variant)
+        bg_pool = ThreadPoolExecutor(len(tol_cols))
+        bg = {c: bg_pool.submit(oracle_tol, c) for c in tol_cols}
+
+    # per-kernel event times of one solve (profiling mode: the solve's own column groups and
+    # kernels, the groups one after another on the same stream) -> roofline of the dominant kernel
     bicgk.set_profiling(op.handle, True)
     one(args.variant)
     torch.cuda.synchronize()
     times = bicgk.kernel_times(op.handle)
+    prof_groups = bicgk.last_stats(op.handle)["groups"]
     bicgk.set_profiling(op.handle, args.eager)
     total = sum(t for _, t in times.values())
     dom, (dl, dt) = max(times.items(), key=lambda kv: kv[1][1])
-    byts, flops = kernel_algorithmic(dom, A.n, A.nnz, args.k, args.variant)
+    kl = launch_columns(dom, args.k, prof_groups)
+    byts, flops = kernel_algorithmic(dom, A.n, A.nnz, kl, args.variant)
     avg_s = dt / dl / 1e3
     hbm, hbm_kind = hbm_peak()
     t_mem, t_alu = byts / (hbm * 1e9), flops / (FP64_PEAK_TFLOPS * 1e12)
@@ -704,7 +850,15 @@ def main():
                 "traffic": traffic, "kernel": dom, "peak_kind": f"{hbm_kind} copy bandwidth",
                 "fp64_achieved_tflops": flops / avg_s / 1e12, "fp64_peak_tflops": FP64_PEAK_TFLOPS}
     roof.update({"algorithmic_bytes_per_launch": byts, "flops_per_launch": flops, "launches": dl,
-                 "mean_launch_ms": dt / dl, "share": dt / total if total else None})
+                 "mean_launch_ms": dt / dl, "share": dt / total if total else None,
+                 "columns_per_launch": kl, "profiled_groups": prof_groups})
+    # the whole solve against the FP64 roof: the form's FP64 FMAs per element and column-iteration
+    # (two products of nnz/N FMAs each, the vector operations' FMAs) over the timed solves
+    fma = solve_fma_per_element(args.variant, A)
+    if fma is not None:
+        roof["whole_solve_fp64_tflops"] = 2.0 * fma * A.n * its / (ms / 1e3) / 1e12
+        roof["whole_solve_fp64_frac"] = roof["whole_solve_fp64_tflops"] / FP64_PEAK_TFLOPS
+        roof["whole_solve_fma_per_element"] = fma
     out["roofline"] = roof
     out["kernel_shares"] = {k: {"launches": v[0], "ms": v[1], "share": v[1] / total} for k, v in
                             sorted(times.items(), key=lambda kv: -kv[1][1])}
@@ -737,6 +891,37 @@ def main():
                                "kind": "oracle",
                                "sample": f"{cols} of the {args.k} columns x {iters} fixed iterations "
                                          f"({secs:.1f} s of CPU time)"}
+        # error against the oracle in the benchmark's own launch configuration (all k columns, the
+        # same column groups and kernels): (1) 12 fixed iterations on the 8 columns, beside the
+        # oracle's own change under one rounding unit in b (this operator amplifies rounding
+        # differences: by 60 iterations both are at the percent level); (2) the solve to tolerance
+        # on sampled columns, against the oracle's solves started above
+        m = 12
+        op.solve(Bd, X=Xd, tol=0.0, maxit=m, variant=args.variant, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
+        Xg = Xd[:, :cols].cpu().numpy()
+        kw = dict(tol=0.0, maxit=m, variant=args.variant, flags=oracle.NO_STOP_TEST)
+        ro = oracle_columns(A, B_host, [(c, kw) for c in range(cols)])
+        g = np.random.default_rng(5)
+        Bp = B_host[:, :cols] * (1.0 + 2.0 ** -52 * g.standard_normal((A.n, cols)))
+        rp = oracle_columns(A, Bp, [(c, kw) for c in range(cols)])
+        Xo = np.concatenate([r.X for r in ro], axis=1)
+        err = colerr(Xg, Xo)
+        resp = colerr(np.concatenate([r.X for r in rp], axis=1), Xo)
+        rt = {c: bg[c].result() for c in tol_cols}
+        bg_pool.shutdown()
+        Xt = np.concatenate([rt[c].X for c in tol_cols], axis=1)
+        err_t = colerr(X_head, Xt)
+        out["oracle_err"] = {
+            "value": float(err.max()), "per_column": err.tolist(),
+            "oracle_one_unit_response": float(resp.max()),
+            "what": f"max over columns 0..{cols - 1} of ||x_gpu - x_oracle|| / ||x_oracle|| after {m} fixed "
+                    f"iterations of the k = {args.k} solve in the benchmark's launch configuration; "
+                    "oracle_one_unit_response: the oracle's own change when b moves by one rounding unit",
+            "to_tolerance": {"columns": tol_cols, "max_rel_err": float(err_t.max()), "per_column": err_t.tolist(),
+                             "gpu_iters": it_head.tolist(), "oracle_iters": [int(rt[c].iters[0]) for c in tol_cols],
+                             "what": "the timed solve's solution on these columns against the oracle's solve to "
+                                     "the same tolerance (both stopping iterates lie within the tolerance of the "
+                                     "exact solution; rounding differences decide which iterate stops)"}}
         # the oracle's basic form of the same method (one loop per vector operation), all cores
         plain_v = args.variant.replace("_merged", "_plain")
         if plain_v != args.variant:

@@ -81,7 +81,9 @@ enum bicgk_error {
   BICGK_E_BAD_CSR = -2,  /* row pointers not monotone, column index out of range, ...   */
   BICGK_E_CUDA = -3,     /* a CUDA runtime call failed (bicgk_last_cuda_error() has it) */
   BICGK_E_NOMEM = -4,    /* device or pinned host allocation failed                     */
-  BICGK_E_UNSUPPORTED = -5 /* k above BICGK_MAX_K, or no sm_103 device                  */
+  BICGK_E_UNSUPPORTED = -5, /* k above BICGK_MAX_K, or no sm_103 device                 */
+  BICGK_E_TIMEOUT = -6     /* a grid-barrier wait of the persistent batch kernel passed
+                              its deadline; the solve was abandoned (outputs undefined)  */
 };
 
 #define BICGK_MAX_K 64
@@ -165,9 +167,19 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
 /*
  * Transpose products for the adjoint (differentiation) path.  No counterpart in the paper.
  *
- * bicgk_op_transpose: *AT receives a new operator for A^T (same size and nonzeros, built from
- *   A's device CSR by a stable counting sort on the host: row j of A^T lists the rows i of A
- *   holding column j in ascending order).  Release it with bicgk_op_destroy().
+ * bicgk_op_transpose: *AT receives a new operator for A^T (same size and nonzeros), built on the
+ *   GPU from A's device CSR by a stable radix sort of the entries by column: row j of A^T lists
+ *   the rows i of A holding column j in ascending order (repeated columns of a row in their
+ *   order), the result of a stable counting sort, bitwise.  AT keeps the entry permutation, so
+ *   bicgk_op_transpose_refresh can carry new values of A to it.  Allocates the operator and a
+ *   temporary of about 20 bytes per nonzero.  Release AT with bicgk_op_destroy().
+ * bicgk_op_set_values: new values vals[nnz] (space `mem`) for A's sparsity pattern, copied in
+ *   place: A's captured graphs stay valid, and A's internal transposed copy (bicgk_spmm_t,
+ *   Algorithm 3), FP32 copy and Jacobi diagonal follow.  Returns when the copy is done.
+ * bicgk_op_transpose_refresh: AT (made from A by bicgk_op_transpose) takes A's current values.
+ *   BICGK_E_INVALID if AT was not made that way or the sizes differ.
+ * bicgk_op_get_csr: copies the operator's device CSR to the host arrays rowptr[n_rows+1],
+ *   colidx[nnz], vals[nnz] (each nullable).
  * bicgk_spmm_t: Y = A^T X for device blocks of n_rows*k FP64 (ld = k).
  *   method BICGK_TRANSPOSE_EXPLICIT: the SpMM kernel on a transposed copy that A builds on the
  *   first call and keeps (atomic-free, deterministic); BICGK_TRANSPOSE_ATOMIC: a scatter over the
@@ -178,6 +190,9 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
  */
 enum bicgk_transpose_method { BICGK_TRANSPOSE_EXPLICIT = 0, BICGK_TRANSPOSE_ATOMIC = 1 };
 int bicgk_op_transpose(bicgk_op A, bicgk_op *AT, void *stream);
+int bicgk_op_set_values(bicgk_op A, const double *vals, int mem, void *stream);
+int bicgk_op_transpose_refresh(bicgk_op A, bicgk_op AT, void *stream);
+int bicgk_op_get_csr(bicgk_op A, int32_t *rowptr, int32_t *colidx, double *vals, void *stream);
 int bicgk_spmm_t(bicgk_op A, int32_t k, const double *X, double *Y, int method, void *stream);
 int bicgk_sddmm(bicgk_op A, int32_t k, const double *L, const double *X, double alpha, double *G, void *stream);
 
@@ -216,8 +231,10 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
  * synchronisation of an allocation, and embeddings that run within a fixed
  * device-memory budget.  The caller passes every input and output; the CSR
  * arrays (rowptr[n_rows+1], colidx[nnz], vals[nnz]; layout and meaning as in
- * bicgk_csr_create, not validated here) and B, X0 (nullable), X are DEVICE
- * pointers in the layout of bicgk_solve; iters, status, resid_hist and
+ * bicgk_csr_create) and B, X0 (nullable), X are DEVICE pointers in the layout
+ * of bicgk_solve.  A check kernel validates the CSR before any product reads
+ * it (row pointers from 0, never decreasing, ending at nnz; column indices in
+ * [0, n_rows)) and a malformed one returns BICGK_E_BAD_CSR; iters, status, resid_hist and
  * true_relres are host arrays as there, and every other argument means the
  * same.  Results equal bicgk_solve's with one column group and no column
  * compaction (BICGK_OPT_RHS_GROUPS = 1, BICGK_OPT_COMPACT = 1), within rounding
@@ -237,8 +254,9 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
  * counter, per-column state, padding) is cleared by each call.  Calls whose GPU
  * work overlaps in time race on the array and give wrong results: serialise
  * them.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Returns when all outputs are valid.
+ * (cudaGetSymbolAddress) with that device current, under a lock (first calls
+ * from several host threads are safe); make that first call before any stream
+ * capture.  Returns when all outputs are valid.
  */
 int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
                         const double *vals, int32_t k, const double *B, const double *X0, double rel_tol,
@@ -254,8 +272,8 @@ enum bicgk_option {
   BICGK_OPT_RHS_GROUPS = 3,         /* 0 (default): k >= 8 is solved as two column groups
                                       running concurrently on internal streams, k >= 32 as four
                                       (bicgk_solve_mixed: two from k = 16); 1: one group;
-                                      2..4: that many groups (at most k).  Profiling mode always
-                                      runs one group.                                          */
+                                      2..4: that many groups (at most k).  Profiling mode runs
+                                      the same groups one after another on the caller's stream. */
   BICGK_OPT_FUSED_DOTS = 4,         /* merged forms of Algorithms 2, 5 and 6: take the dot
                                       kernel that follows an SpMM in the listing (delta after
                                       v = A p; group 1 after t = A s, Algorithms 2 and 5) into
@@ -314,10 +332,33 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value);
  *   group without dot epilogues or column compaction (BICGK_OPT_RHS_GROUPS = 1,
  *   BICGK_OPT_FUSED_DOTS = 1, BICGK_OPT_COMPACT = 1) and the same kernel sequence, so their
  *   results are bitwise equal.  Residual histories are not returned.
- * bicgk_batch_last_launches: kernels the last bicgk_batch_solve launched.
+ *   mode BICGK_BATCH_PERSISTENT: the whole batch -- pack, set-up, every iteration of every
+ *   system, true residual, unpack -- in ONE cooperative kernel launch (replayed from a CUDA
+ *   graph), merged classical BiCGStab (Algorithm 2) only, M = identity (other variants and
+ *   BICGK_FLAG_JACOBI: BICGK_E_UNSUPPORTED).  A grid sized to be co-resident walks all systems'
+ *   row tiles phase by phase (Algorithm 2's merged groups), with a grid-wide barrier between
+ *   phases; a system stops costing work once all its columns stopped.  Same scalar rules as the
+ *   other modes; dot products are summed per row tile, so results differ from theirs by
+ *   summation order only (and are bitwise reproducible run to run).  Every barrier wait is
+ *   bounded by the batch's deadline (bicgk_batch_set_deadline; default 1 s): past it the kernel
+ *   returns, the call returns BICGK_E_TIMEOUT, bicgk_last_cuda_error() names the barrier and
+ *   the block, and the next solve starts from a clean state.
+ * bicgk_batch_tune_persistent: autotuner of the persistent mode's rows per CTA tile (1, 2, 4 or
+ *   8 passes of 256 threads: 256..2048 rows at kp <= 2, 64..512 at kp = 8): times `reps`
+ *   persistent solves of 4 fixed iterations with right-hand sides of ones for each and keeps
+ *   the fastest (allocates two temporary blocks).  Writes each system's rows per tile to the
+ *   nullable array [nsys].
+ * bicgk_batch_set_deadline: longest wait of one grid barrier of the persistent kernel, in
+ *   microseconds (0..3.6e9; 0 makes every wait that does not find all blocks arrived fail).
+ * bicgk_batch_last_launches: kernels the last bicgk_batch_solve launched (persistent: 1).
+ * bicgk_batch_last_loop_iters: iterations the persistent kernel's loop ran in the last
+ *   persistent solve (the slowest system's).
+ * bicgk_batch_persistent_info: blocks of the persistent grid (co-resident: SMs x blocks per
+ *   SM) and whether its launch is replayed from a CUDA graph (1) or launched directly (0, a
+ *   runtime that cannot capture cooperative launches); nullable outputs.
  */
 typedef struct bicgk_batch_s *bicgk_batch;
-enum bicgk_batch_mode { BICGK_BATCH_GRAPH = 0, BICGK_BATCH_LOOP = 1 };
+enum bicgk_batch_mode { BICGK_BATCH_GRAPH = 0, BICGK_BATCH_LOOP = 1, BICGK_BATCH_PERSISTENT = 2 };
 int bicgk_batch_create(bicgk_batch *out, int32_t nsys, const int64_t *n_rows, const int64_t *nnz,
                        const int32_t *const *rowptr, const int32_t *const *colidx, const double *const *vals,
                        const int32_t *k, int mem, void *stream);
@@ -326,7 +367,11 @@ int bicgk_batch_tune(bicgk_batch b, int32_t reps, int32_t *vec_grid_out, int32_t
 int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const *X0, double *const *X,
                       double rel_tol, int32_t maxit, int variant, int32_t flags, int mode, int32_t *iters,
                       int32_t *status, double *true_relres, void *stream);
+int bicgk_batch_tune_persistent(bicgk_batch b, int32_t reps, int32_t *rows_per_tile_out, void *stream);
+int bicgk_batch_set_deadline(bicgk_batch b, int64_t microseconds);
 int bicgk_batch_last_launches(bicgk_batch b, int64_t *kernel_launches);
+int bicgk_batch_last_loop_iters(bicgk_batch b, int64_t *iters);
+int bicgk_batch_persistent_info(bicgk_batch b, int32_t *grid_blocks, int32_t *from_graph);
 int bicgk_batch_destroy(bicgk_batch b);
 
 /* Release the operator and all device memory it holds.  NULL is accepted. */
@@ -341,10 +386,14 @@ const char *bicgk_last_cuda_error(void);
 /*
  * Per-kernel timing (profiling aid).  With bicgk_set_profiling(A, 1) the next
  * solves run their iteration loop without the CUDA graph, one launch at a time
- * on the caller's stream, with a CUDA event pair around every launch;
+ * on the caller's stream, with a CUDA event pair around every launch; the
+ * column groups of a solve are the graph mode's, run one after another, so the
+ * kernels timed are the ones the graph mode runs;
  * bicgk_kernel_times() then reports, for kernel class i (0 <= i < *n_out),
- * its name, launch count and summed event time in milliseconds since the last
- * bicgk_set_profiling() call.  Results are identical to the graph mode.
+ * its name (with the group's column count, e.g. "spmm_phi_psi_k8"), launch
+ * count and summed event time in milliseconds since the last
+ * bicgk_set_profiling() call.  Results are identical to the graph mode without
+ * column compaction (BICGK_OPT_COMPACT = 1; the profiling mode does not compact).
  *   names: array of *n_out C strings owned by the library (may be NULL).
  */
 int bicgk_set_profiling(bicgk_op A, int on);

@@ -74,14 +74,24 @@ def _load():
             lib.bicgk_batch_solve.argtypes = [vp, pp, pp, pp, dbl, i32, ctypes.c_int, i32, ctypes.c_int, vp, vp,
                                               vp, vp]
             lib.bicgk_batch_last_launches.argtypes = [vp, ctypes.POINTER(i64)]
+            lib.bicgk_batch_last_loop_iters.argtypes = [vp, ctypes.POINTER(i64)]
+            lib.bicgk_batch_tune_persistent.argtypes = [vp, i32, vp, vp]
+            lib.bicgk_batch_set_deadline.argtypes = [vp, i64]
+            lib.bicgk_batch_persistent_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
             lib.bicgk_batch_destroy.argtypes = [vp]
             for f in ("bicgk_batch_create", "bicgk_batch_tune", "bicgk_batch_solve", "bicgk_batch_last_launches",
+                      "bicgk_batch_last_loop_iters", "bicgk_batch_tune_persistent", "bicgk_batch_set_deadline",
+                      "bicgk_batch_persistent_info",
                       "bicgk_batch_destroy"):
                 getattr(lib, f).restype = ctypes.c_int
             lib.bicgk_op_transpose.argtypes = [vp, ctypes.POINTER(vp), vp]
+            lib.bicgk_op_set_values.argtypes = [vp, vp, ctypes.c_int, vp]
+            lib.bicgk_op_transpose_refresh.argtypes = [vp, vp, vp]
+            lib.bicgk_op_get_csr.argtypes = [vp, vp, vp, vp, vp]
             lib.bicgk_spmm_t.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp]
             lib.bicgk_sddmm.argtypes = [vp, i32, vp, vp, dbl, vp, vp]
-            for f in ("bicgk_op_transpose", "bicgk_spmm_t", "bicgk_sddmm"):
+            for f in ("bicgk_op_transpose", "bicgk_spmm_t", "bicgk_sddmm", "bicgk_op_set_values",
+                      "bicgk_op_transpose_refresh", "bicgk_op_get_csr"):
                 getattr(lib, f).restype = ctypes.c_int
             lib.bicgk_set_profiling.argtypes = [vp, ctypes.c_int]
             lib.bicgk_set_option.argtypes = [vp, ctypes.c_int, i64]
@@ -324,6 +334,30 @@ class Operator:
         t.n, t.nnz, t.handle = self.n, self.nnz, h.value
         return t
 
+    def set_values(self, vals, stream=None) -> None:
+        """New values for the same sparsity pattern (bicgk_op_set_values): host (numpy) or CUDA
+        float64 array of nnz entries.  Captured graphs stay valid; the internal transposed copy
+        and the FP32/Jacobi arrays follow."""
+        mem = MEM_DEVICE if _is_device(vals) else MEM_HOST
+        if not _is_torch(vals):
+            vals = np.ascontiguousarray(vals, dtype=np.float64)
+        _check(_load().bicgk_op_set_values(ctypes.c_void_p(self.handle), _ptr(vals), mem, _stream(stream)),
+               "bicgk_op_set_values")
+
+    def transpose_refresh(self, opT: "Operator", stream=None) -> None:
+        """Carry this operator's current values to opT, made from it by transpose()."""
+        _check(_load().bicgk_op_transpose_refresh(ctypes.c_void_p(self.handle), ctypes.c_void_p(opT.handle),
+                                                  _stream(stream)), "bicgk_op_transpose_refresh")
+
+    def get_csr(self, stream=None):
+        """(rowptr, colidx, vals) of the operator's device copy, as numpy arrays."""
+        rp = np.empty(self.n + 1, np.int32)
+        ci = np.empty(self.nnz, np.int32)
+        va = np.empty(self.nnz, np.float64)
+        _check(_load().bicgk_op_get_csr(ctypes.c_void_p(self.handle), _ptr(rp), _ptr(ci), _ptr(va), _stream(stream)),
+               "bicgk_op_get_csr")
+        return rp, ci, va
+
     def spmm_t(self, X, Y=None, method: int = 0, stream=None):
         """Y = A^T X (method 0: explicit transpose, 1: atomic scatter)."""
         if Y is None:
@@ -376,7 +410,8 @@ class Operator:
             pass
 
 
-BATCH_GRAPH, BATCH_LOOP = 0, 1
+BATCH_GRAPH, BATCH_LOOP, BATCH_PERSISTENT = 0, 1, 2
+E_TIMEOUT = -6
 
 
 def _ptr_array(items):
@@ -414,6 +449,30 @@ class Batch:
         _check(_load().bicgk_batch_tune(ctypes.c_void_p(self.handle), int(reps), _ptr(g), _ptr(sg), _ptr(cpl),
                                         _stream(stream)), "bicgk_batch_tune")
         return {"vec_grid": g, "spmm_grid": sg, "spmm_cols_per_lane": cpl}
+
+    def tune_persistent(self, reps: int = 3, stream=None) -> np.ndarray:
+        """Rows per CTA tile of the persistent mode (bicgk_batch_tune_persistent); per system."""
+        rows = np.zeros(len(self.ks), np.int32)
+        _check(_load().bicgk_batch_tune_persistent(ctypes.c_void_p(self.handle), int(reps), _ptr(rows),
+                                                   _stream(stream)), "bicgk_batch_tune_persistent")
+        return rows
+
+    def set_deadline(self, microseconds: int) -> None:
+        """Longest wait of one grid barrier of the persistent kernel (bicgk_batch_set_deadline)."""
+        _check(_load().bicgk_batch_set_deadline(ctypes.c_void_p(self.handle), int(microseconds)),
+               "bicgk_batch_set_deadline")
+
+    def persistent_info(self) -> dict:
+        g, f = ctypes.c_int32(), ctypes.c_int32()
+        _check(_load().bicgk_batch_persistent_info(ctypes.c_void_p(self.handle), ctypes.byref(g), ctypes.byref(f)),
+               "persistent_info")
+        return {"grid_blocks": g.value, "from_graph": bool(f.value)}
+
+    def last_loop_iters(self) -> int:
+        n = ctypes.c_int64()
+        _check(_load().bicgk_batch_last_loop_iters(ctypes.c_void_p(self.handle), ctypes.byref(n)),
+               "last_loop_iters")
+        return n.value
 
     def solve(self, Bs, Xs=None, X0s=None, tol: float = 1e-8, maxit: int = 1000, variant="classical_merged",
               flags: int = 0, mode: int = BATCH_GRAPH, stream=None):

@@ -17,6 +17,8 @@
 #include <cstring>
 #include <initializer_list>
 #include <map>
+#include <mutex>
+#include <numeric>
 #include <string>
 #include <thread>
 #include <utility>
@@ -24,6 +26,8 @@
 
 #include "../../include/bicgk.h"
 #include "bicgk_dev.cuh"
+#include "bicgk_persist.cuh"
+#include "bicgk_transpose.cuh"
 
 using namespace bicgk;
 
@@ -247,6 +251,8 @@ struct bicgk_op_s {
   Workspace ws[kMaxGroups];
   Workspace ws32[kMaxGroups];  // FP32 inner-solve workspaces of the mixed-precision refinement
   bicgk_op trans = nullptr;  // operator of A^T (atomic-free transpose products; made on first use)
+  int32_t *d_perm = nullptr;  // an operator made by bicgk_op_transpose: the entry of its source
+                              // that each of its entries copies (to carry new values over)
   double *d_invdiag = nullptr;  // Jacobi preconditioner 1/a_ii (made on first use)
   double *d_stage[2] = {nullptr, nullptr};  // caller-layout staging for host-memory calls
   int64_t stage_elems = 0;
@@ -794,8 +800,8 @@ int build_graph_compact(bicgk_op A, Workspace &W, const Seq &q, GraphEntry *ge, 
   return BICGK_OK;
 }
 
-// Column groups of a solve of k columns (BICGK_OPT_RHS_GROUPS; the profiling mode runs them as
-// one group but keeps the kernel sequence this count selects).  Automatic: two from k = 8, four
+// Column groups of a solve of k columns (BICGK_OPT_RHS_GROUPS; the profiling mode runs the same
+// groups one after another).  Automatic: two from k = 8, four
 // from k = 32.  Each group's loop runs until its own slowest column stops, and a group that
 // finishes early leaves the GPU to the others, so smaller groups waste fewer iterations on
 // stopped columns: at 128^3, k = 32 four groups of 8 cost the same per iteration as two of 16
@@ -868,6 +874,36 @@ int check_device(int *dev, int *nsm) {
   return BICGK_OK;
 }
 
+// An operator with device arrays for n rows and nnz entries (contents undefined), its capture
+// stream and fork event.
+int op_alloc(bicgk_op *out, int dev, int nsm, int64_t n, int64_t nnz) {
+  bicgk_op A = new bicgk_op_s();
+  A->device = dev;
+  A->nsm = nsm;
+  A->n = n;
+  A->nnz = nnz;
+  cudaError_t e;
+  // pad by 16 bytes so vectorised reads of the last entries stay inside the allocation
+  if ((e = cudaMalloc(&A->d_rowptr, sizeof(int32_t) * (n + 1) + 16)) != cudaSuccess ||
+      (e = cudaMalloc(&A->d_col, sizeof(int32_t) * nnz + 16)) != cudaSuccess ||
+      (e = cudaMalloc(&A->d_val, sizeof(double) * nnz + 16)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&A->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&A->fork, cudaEventDisableTiming)) != cudaSuccess) {
+    bicgk_op_destroy(A);
+    return cuda_fail(e, "operator allocation");
+  }
+  *out = A;
+  return BICGK_OK;
+}
+
+// Arrays an operator derives from its values (FP32 copy, Jacobi diagonal), recomputed after the
+// values changed.
+int refresh_derived(bicgk_op A, cudaStream_t s) {
+  if (A->d_val32) CK(launch_to_float(A->d_val, A->d_val32, A->nnz, s));
+  if (A->d_invdiag) CK(launch_invdiag(A->d_rowptr, A->d_col, A->d_val, A->d_invdiag, A->n, s));
+  return BICGK_OK;
+}
+
 void prof_record(bicgk_op A, const std::string &name, float ms) {
   ProfEntry &e = A->prof[name];
   e.launches += 1;
@@ -926,6 +962,7 @@ const char *bicgk_strerror(int rc) {
     case BICGK_E_CUDA: return "CUDA runtime error";
     case BICGK_E_NOMEM: return "out of memory";
     case BICGK_E_UNSUPPORTED: return "unsupported configuration";
+    case BICGK_E_TIMEOUT: return "a device-side wait passed its deadline";
     default: return "unknown error";
   }
 }
@@ -966,23 +1003,14 @@ int bicgk_csr_create(bicgk_op *out, int64_t n_rows, int64_t nnz, const int32_t *
     const int64_t t = rp[r1] - rp[r0];
     if (t > maxtile) maxtile = t;
   }
-  bicgk_op A = new bicgk_op_s();
-  A->device = dev;
-  A->nsm = nsm;
-  A->n = n_rows;
-  A->nnz = nnz;
+  bicgk_op A = nullptr;
+  if ((rc = op_alloc(&A, dev, nsm, n_rows, nnz))) return rc;
   A->stage_cap = (int)(maxtile < kSpmmStageMax ? maxtile : kSpmmStageMax);
   const cudaMemcpyKind kind = mem == BICGK_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaError_t e;
-  // pad by 16 bytes so vectorised reads of the last entries stay inside the allocation
-  if ((e = cudaMalloc(&A->d_rowptr, sizeof(int32_t) * (n_rows + 1) + 16)) != cudaSuccess ||
-      (e = cudaMalloc(&A->d_col, sizeof(int32_t) * nnz + 16)) != cudaSuccess ||
-      (e = cudaMalloc(&A->d_val, sizeof(double) * nnz + 16)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(A->d_rowptr, rowptr, sizeof(int32_t) * (n_rows + 1), kind, s)) != cudaSuccess ||
+  if ((e = cudaMemcpyAsync(A->d_rowptr, rowptr, sizeof(int32_t) * (n_rows + 1), kind, s)) != cudaSuccess ||
       (nnz && (e = cudaMemcpyAsync(A->d_col, colidx, sizeof(int32_t) * nnz, kind, s)) != cudaSuccess) ||
       (nnz && (e = cudaMemcpyAsync(A->d_val, vals, sizeof(double) * nnz, kind, s)) != cudaSuccess) ||
-      (e = cudaStreamCreateWithFlags(&A->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&A->fork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     bicgk_op_destroy(A);
     return cuda_fail(e, "bicgk_csr_create");
@@ -999,6 +1027,7 @@ int bicgk_op_destroy(bicgk_op A) {
   for (Workspace &W : A->ws) free_workspace(W);
   for (Workspace &V : A->ws32) free_workspace(V);
   cudaFree(A->d_val32);
+  cudaFree(A->d_perm);
   cudaFree(A->d_rowptr);
   cudaFree(A->d_col);
   cudaFree(A->d_val);
@@ -1101,8 +1130,11 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
   int rc0 = ensure_variant_data(A, variant, jacobi, s);
   if (rc0) return rc0;
   // columns are independent: from k = kSplitMinK they are split into groups solved concurrently,
-  // so that one group's FP64-bound SpMM overlaps another group's bandwidth-bound vector kernels
-  const int ngroups = A->profiling ? 1 : num_groups(A, k);
+  // so that one group's FP64-bound SpMM overlaps another group's bandwidth-bound vector kernels.
+  // The profiling mode keeps the same groups (so it times the kernels the solve runs) but runs
+  // them one after another on the caller's stream.
+  const int ngroups = num_groups(A, k);
+  const bool concurrent = !A->profiling && ngroups >= 2;
   int c0[kMaxGroups + 1];
   for (int g = 0; g <= ngroups; ++g) c0[g] = (int)((int64_t)g * k / ngroups);
   int rc;
@@ -1140,12 +1172,12 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     }
     dX = A->d_stage[0];  // X overwrites the staged B after both groups have packed it
   }
-  if (ngroups > 1) CK(cudaEventRecord(A->fork, s));
+  if (concurrent) CK(cudaEventRecord(A->fork, s));
   int64_t launches = 0;
   for (int g = 0; g < ngroups; ++g) {
     Workspace &W = A->ws[g];
-    cudaStream_t gs = ngroups > 1 ? W.stream : s;
-    if (ngroups > 1) CK(cudaStreamWaitEvent(gs, A->fork, 0));
+    cudaStream_t gs = concurrent ? W.stream : s;
+    if (concurrent) CK(cudaStreamWaitEvent(gs, A->fork, 0));
     const int kg = c0[g + 1] - c0[g];
     const int64_t hist_len = (int64_t)(maxit + 1) * W.kp;
     Ctl *hc = W.h_ctl;
@@ -1182,15 +1214,15 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
       }
       CK(cudaGraphLaunch(it->second.exec, gs));
     }
-    if (ngroups > 1 && staged) {
+    if (concurrent && staged) {
       // the staged B is overwritten by X only after every group has packed its columns
       CK(cudaEventRecord(W.done, gs));
     }
   }
   for (int g = 0; g < ngroups; ++g) {
     Workspace &W = A->ws[g];
-    cudaStream_t gs = ngroups > 1 ? W.stream : s;
-    if (ngroups > 1 && staged)
+    cudaStream_t gs = concurrent ? W.stream : s;
+    if (concurrent && staged)
       for (int h = 0; h < ngroups; ++h)
         if (h != g) CK(cudaStreamWaitEvent(gs, A->ws[h].done, 0));
     const int kg = c0[g + 1] - c0[g];
@@ -1212,7 +1244,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
     }
     if (resid_hist)
       CK(cudaMemcpyAsync(W.h_hist, W.d_hist, sizeof(double) * hist_len, cudaMemcpyDeviceToHost, gs));
-    if (ngroups > 1) {
+    if (concurrent) {
       CK(cudaEventRecord(W.done, gs));
       CK(cudaStreamWaitEvent(s, W.done, 0));
     }
@@ -1257,8 +1289,9 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
   // FP32 inner workspaces; the refinement passes of the groups advance together.  Automatic: two
   // groups from k = 16 (27-point operator, 128^3, k = 32: 98.9 ms against 101.0 for one group and
   // 110.6 for four of 8, whose FP32 products are less efficient)
-  const int ngroups =
-      A->profiling ? 1 : A->opt_groups == 0 ? (k >= kMixedSplitMinK ? 2 : 1) : num_groups(A, k);
+  // (the profiling mode runs the same groups one after another on the caller's stream)
+  const int ngroups = A->opt_groups == 0 ? (k >= kMixedSplitMinK ? 2 : 1) : num_groups(A, k);
+  const bool concurrent = !A->profiling && ngroups >= 2;
   int c0[kMaxGroups + 1];
   for (int g = 0; g <= ngroups; ++g) c0[g] = (int)((int64_t)g * k / ngroups);
   int rc;
@@ -1288,7 +1321,7 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
     }
     dX = A->d_stage[1];  // X goes to the second staging block: the groups pack B from the first
   }
-  if (ngroups > 1) CK(cudaEventRecord(A->fork, s));
+  if (concurrent) CK(cudaEventRecord(A->fork, s));
   const Seq qi = make_inner32_seq();
   const Step res = resid(V_X, V_R, V_B);
   int64_t launches = 0;
@@ -1297,8 +1330,8 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
   for (int g = 0; g < ngroups; ++g) {
     Workspace &W = A->ws[g];
     Workspace &V = A->ws32[g];
-    cudaStream_t gs = ngroups > 1 ? W.stream : s;
-    if (ngroups > 1) CK(cudaStreamWaitEvent(gs, A->fork, 0));
+    cudaStream_t gs = concurrent ? W.stream : s;
+    if (concurrent) CK(cudaStreamWaitEvent(gs, A->fork, 0));
     const int kg = c0[g + 1] - c0[g];
     // outer (FP64) state
     Ctl *hc = W.h_ctl;
@@ -1332,7 +1365,7 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
       if (!live[g]) continue;
       Workspace &W = A->ws[g];
       Workspace &V = A->ws32[g];
-      cudaStream_t gs = ngroups > 1 ? W.stream : s;
+      cudaStream_t gs = concurrent ? W.stream : s;
       const KArgs ao = make_args(A, W, 0, cudaGraphConditionalHandle{});
       KArgs air = ao;  // outer steps that touch the FP32 blocks: b32 in V_Q, d in V_Y
       const KArgs ai0 = make_args(A, V, 0, cudaGraphConditionalHandle{});
@@ -1348,7 +1381,7 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
       if (!live[g]) continue;
       Workspace &W = A->ws[g];
       Workspace &V = A->ws32[g];
-      CK(cudaStreamSynchronize(ngroups > 1 ? W.stream : s));
+      CK(cudaStreamSynchronize(concurrent ? W.stream : s));
       if (pass > 0)
         for (int c = 0; c < c0[g + 1] - c0[g]; ++c) inner_total[c0[g] + c] += V.h_fl[F_ITERS * kMaxKp + c];
       live[g] = W.h_ctl->any_active != 0;
@@ -1360,7 +1393,7 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
       if (!live[g]) continue;
       Workspace &W = A->ws[g];
       Workspace &V = A->ws32[g];
-      cudaStream_t gs = ngroups > 1 ? W.stream : s;
+      cudaStream_t gs = concurrent ? W.stream : s;
       const KArgs ao = make_args(A, W, 0, cudaGraphConditionalHandle{});
       KArgs air = ao;
       const KArgs ai0 = make_args(A, V, 0, cudaGraphConditionalHandle{});
@@ -1389,7 +1422,7 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
   }
   for (int g = 0; g < ngroups; ++g) {
     Workspace &W = A->ws[g];
-    cudaStream_t gs = ngroups > 1 ? W.stream : s;
+    cudaStream_t gs = concurrent ? W.stream : s;
     const KArgs ao = make_args(A, W, 0, cudaGraphConditionalHandle{});
     CK(launch_unpack_role(dX + c0[g], k, c0[g + 1] - c0[g], ao, V_X, 1, gs));
     CK(cudaMemcpyAsync(W.h_fl, W.d_fl, sizeof(int) * F_NFLAG * kMaxKp, cudaMemcpyDeviceToHost, gs));
@@ -1397,7 +1430,7 @@ int bicgk_solve_mixed(bicgk_op A, int32_t k, const double *B, const double *X0, 
     if (resid_hist)
       CK(cudaMemcpyAsync(W.h_hist, W.d_hist, sizeof(double) * (max_outer + 1) * W.kp, cudaMemcpyDeviceToHost,
                          gs));
-    if (ngroups > 1) {
+    if (concurrent) {
       CK(cudaEventRecord(W.done, gs));
       CK(cudaStreamWaitEvent(s, W.done, 0));
     }
@@ -1433,25 +1466,66 @@ int bicgk_op_transpose(bicgk_op A, bicgk_op *AT, void *stream) {
   *AT = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = A->n, nnz = A->nnz;
-  std::vector<int32_t> rp(n + 1), ci(nnz), rpt(n + 2, 0), cit(nnz);
-  std::vector<double> va(nnz), vat(nnz);
-  CK(cudaMemcpyAsync(rp.data(), A->d_rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
-  if (nnz) {
-    CK(cudaMemcpyAsync(ci.data(), A->d_col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(va.data(), A->d_val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s));
+  bicgk_op T = nullptr;
+  int rc = op_alloc(&T, A->device, A->nsm, n, nnz);
+  if (rc) return rc;
+  void *scratch = nullptr;
+  int *d_max = nullptr;
+  int maxtile = 0;
+  cudaError_t e;
+  if ((e = cudaMalloc(&T->d_perm, sizeof(int32_t) * nnz + 16)) != cudaSuccess ||
+      (e = cudaMalloc(&scratch, transpose_scratch_bytes(n, nnz))) != cudaSuccess ||
+      (e = cudaMalloc(&d_max, sizeof(int))) != cudaSuccess ||
+      (e = launch_transpose(A->d_rowptr, A->d_col, A->d_val, n, nnz, T->d_rowptr, T->d_col, T->d_val, T->d_perm, d_max,
+                            scratch, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&maxtile, d_max, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    cudaFree(scratch);
+    cudaFree(d_max);
+    bicgk_op_destroy(T);
+    return cuda_fail(e, "bicgk_op_transpose");
+  }
+  cudaFree(scratch);
+  cudaFree(d_max);
+  T->stage_cap = maxtile < kSpmmStageMax ? maxtile : kSpmmStageMax;
+  *AT = T;
+  return BICGK_OK;
+}
+
+int bicgk_op_set_values(bicgk_op A, const double *vals, int mem, void *stream) {
+  if (!A || (A->nnz > 0 && !vals) || (mem != BICGK_MEM_HOST && mem != BICGK_MEM_DEVICE)) return BICGK_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (A->nnz > 0)
+    CK(cudaMemcpyAsync(A->d_val, vals, sizeof(double) * A->nnz,
+                       mem == BICGK_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  int rc = refresh_derived(A, s);
+  if (rc) return rc;
+  if (A->trans) {
+    CK(launch_permute_values(A->trans->d_perm, A->d_val, A->nnz, A->trans->d_val, s));
+    if ((rc = refresh_derived(A->trans, s))) return rc;
   }
   CK(cudaStreamSynchronize(s));
-  // counting sort by column, stable in the row index: row j of A^T lists the rows i of A
-  // that hold column j, ascending
-  for (int64_t e = 0; e < nnz; ++e) rpt[ci[e] + 2]++;
-  for (int64_t j = 0; j < n; ++j) rpt[j + 2] += rpt[j + 1];
-  for (int64_t i = 0; i < n; ++i)
-    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
-      const int32_t pos = rpt[ci[e] + 1]++;
-      cit[pos] = (int32_t)i;
-      vat[pos] = va[e];
-    }
-  return bicgk_csr_create(AT, n, nnz, rpt.data(), cit.data(), vat.data(), BICGK_MEM_HOST, stream);
+  return BICGK_OK;
+}
+
+int bicgk_op_transpose_refresh(bicgk_op A, bicgk_op AT, void *stream) {
+  if (!A || !AT || !AT->d_perm || AT->n != A->n || AT->nnz != A->nnz) return BICGK_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_permute_values(AT->d_perm, A->d_val, A->nnz, AT->d_val, s));
+  int rc = refresh_derived(AT, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  return BICGK_OK;
+}
+
+int bicgk_op_get_csr(bicgk_op A, int32_t *rowptr, int32_t *colidx, double *vals, void *stream) {
+  if (!A) return BICGK_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (rowptr) CK(cudaMemcpyAsync(rowptr, A->d_rowptr, sizeof(int32_t) * (A->n + 1), cudaMemcpyDeviceToHost, s));
+  if (colidx && A->nnz) CK(cudaMemcpyAsync(colidx, A->d_col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, s));
+  if (vals && A->nnz) CK(cudaMemcpyAsync(vals, A->d_val, sizeof(double) * A->nnz, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return BICGK_OK;
 }
 
 int bicgk_spmm_t(bicgk_op A, int32_t k, const double *X, double *Y, int method, void *stream) {
@@ -1576,6 +1650,21 @@ struct bicgk_batch_s {
   int64_t hist_iters = 0;     // history capacity of every system, in iterations + 1
   std::map<int, GraphEntry> graphs;
   int64_t last_launches = 0;
+  // persistent mode: one cooperative launch over every system's row tiles
+  PersistSys *d_psys = nullptr, *h_psys = nullptr;
+  unsigned *d_tickets = nullptr;
+  int *d_live = nullptr;
+  PersistCtl *d_pc = nullptr, *h_pc = nullptr;
+  double *d_ppart = nullptr;
+  size_t ppart_cap = 0;       // doubles
+  int64_t p_ntiles = 0;
+  int p_grid = 0;
+  int p_sub = 1;              // 256-thread passes per tile (rows per CTA tile; bicgk_batch_tune)
+  int64_t deadline_us = 1000000;  // longest wait at one grid barrier
+  GraphEntry pgraph;          // clear the control block, the cooperative kernel
+  bool pgraph_ok = false;
+  bool p_direct = false;      // the runtime could not capture the cooperative launch
+  int64_t p_loop_iters = 0;
 };
 
 namespace {
@@ -1673,6 +1762,115 @@ int batch_build_graph(bicgk_batch b, int variant, bool jacobi, GraphEntry *ge) {
   return BICGK_OK;
 }
 
+void persist_drop_graph(bicgk_batch b) {
+  if (b->pgraph.exec) cudaGraphExecDestroy(b->pgraph.exec);
+  if (b->pgraph.graph) cudaGraphDestroy(b->pgraph.graph);
+  b->pgraph = GraphEntry{};
+  b->pgraph_ok = false;
+}
+
+// Tiles, descriptors and buffers of the persistent mode for the batch's current workspaces (after
+// batch_ensure).  Caller blocks and history length are filled per solve.
+int persist_prepare(bicgk_batch b) {
+  const int n = b->nsys;
+  if (!b->d_psys) {
+    CK(cudaMalloc(&b->d_psys, sizeof(PersistSys) * n));
+    CK(cudaMallocHost(&b->h_psys, sizeof(PersistSys) * n));
+    CK(cudaMalloc(&b->d_tickets, sizeof(unsigned) * n));
+    CK(cudaMalloc(&b->d_live, sizeof(int) * n));
+    CK(cudaMalloc(&b->d_pc, sizeof(PersistCtl)));
+    CK(cudaMallocHost(&b->h_pc, sizeof(PersistCtl)));
+    memset(b->h_psys, 0, sizeof(PersistSys) * n);
+  }
+  int64_t tiles = 0;
+  size_t part = 0;
+  for (int i = 0; i < n; ++i) {
+    bicgk_op A = b->ops[i];
+    Workspace &W = b->ws[i];
+    const int64_t rows = (int64_t)persist_rows_per_pass(W.kp) * b->p_sub;
+    PersistSys &S = b->h_psys[i];
+    S.rowptr = A->d_rowptr;
+    S.colidx = A->d_col;
+    S.vals = A->d_val;
+    const int roles[P_NROLE] = {V_X, V_R, V_R0, V_P, V_V, V_S, V_T, V_B};
+    for (int r = 0; r < P_NROLE; ++r) S.vec[r] = W.d_vec + (size_t)roles[r] * W.vstride;
+    S.sc = W.d_sc;
+    S.fl = W.d_fl;
+    S.ctl = W.d_ctl;
+    S.n = A->n;
+    S.k = b->k[i];
+    S.kp = W.kp;
+    S.sub = b->p_sub;
+    S.ntiles = (int)((A->n + rows - 1) / rows);
+    S.tile0 = tiles;
+    tiles += S.ntiles;
+    part += (size_t)S.ntiles * 3 * W.kp;
+  }
+  if (part > b->ppart_cap) {
+    cudaFree(b->d_ppart);
+    b->d_ppart = nullptr;
+    CK(cudaMalloc(&b->d_ppart, sizeof(double) * part));
+    b->ppart_cap = part;
+    persist_drop_graph(b);
+  }
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    b->h_psys[i].part = b->d_ppart + off;
+    off += (size_t)b->h_psys[i].ntiles * 3 * b->h_psys[i].kp;
+  }
+  if (tiles != b->p_ntiles) persist_drop_graph(b);
+  b->p_ntiles = tiles;
+  if (!b->p_grid) {
+    const int nb = persist_blocks_per_sm();
+    if (nb < 1) return cuda_fail(cudaGetLastError(), "persistent kernel occupancy");
+    b->p_grid = b->ops[0]->nsm * (nb < kPersistMaxBlocksPerSm ? nb : kPersistMaxBlocksPerSm);
+  }
+  return BICGK_OK;
+}
+
+// One persistent solve on stream s (descriptors and control blocks already uploaded): a graph of
+// the control-block reset and the cooperative kernel, captured once per shape.
+int persist_launch(bicgk_batch b, cudaStream_t s) {
+  PersistArgs pa;
+  pa.sys = b->d_psys;
+  pa.tickets = b->d_tickets;
+  pa.live = b->d_live;
+  pa.pc = b->d_pc;
+  pa.ntiles = b->p_ntiles;
+  pa.nsys = b->nsys;
+  pa.pad = 0;
+  pa.deadline_ns = (unsigned long long)b->deadline_us * 1000ull;
+  if (!b->pgraph_ok && !b->p_direct) {
+    cudaStream_t cs = b->ops[0]->cap_stream;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(b->d_pc, 0, sizeof(PersistCtl), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_tickets, 0, sizeof(unsigned) * b->nsys, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_live, 0, sizeof(int) * b->nsys, cs);
+    if (e == cudaSuccess) e = launch_persist(pa, b->p_grid, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess) e2 = cudaGraphInstantiate(&b->pgraph.exec, g, 0);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      // a runtime that cannot capture a cooperative launch: launch it directly from now on
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      b->p_direct = true;
+    } else {
+      b->pgraph.graph = g;
+      b->pgraph_ok = true;
+    }
+  }
+  if (b->p_direct) {
+    CK(cudaMemsetAsync(b->d_pc, 0, sizeof(PersistCtl), s));
+    CK(cudaMemsetAsync(b->d_tickets, 0, sizeof(unsigned) * b->nsys, s));
+    CK(cudaMemsetAsync(b->d_live, 0, sizeof(int) * b->nsys, s));
+    CK(launch_persist(pa, b->p_grid, s));
+    return BICGK_OK;
+  }
+  CK(cudaGraphLaunch(b->pgraph.exec, s));
+  return BICGK_OK;
+}
+
 // Mean time of `reps` launches of one kernel configuration (CUDA events on stream s).
 template <class F>
 int time_launches(F launch, int reps, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
@@ -1747,6 +1945,14 @@ int bicgk_batch_destroy(bicgk_batch b) {
   if (!b) return BICGK_OK;
   cudaDeviceSynchronize();
   batch_drop_graphs(b);
+  persist_drop_graph(b);
+  cudaFree(b->d_psys);
+  cudaFreeHost(b->h_psys);
+  cudaFree(b->d_tickets);
+  cudaFree(b->d_live);
+  cudaFree(b->d_pc);
+  cudaFreeHost(b->h_pc);
+  cudaFree(b->d_ppart);
   for (Workspace &W : b->ws) {
     cudaFree(W.d_vec);
     cudaFree(W.d_part);
@@ -1849,9 +2055,14 @@ int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const
                       double rel_tol, int32_t maxit, int variant, int32_t flags, int mode, int32_t *iters,
                       int32_t *status, double *true_relres, void *stream) {
   if (!b || !B || !X || !iters || !status || !(rel_tol >= 0.0) || maxit < 0 || maxit > 10000000 || variant < 0 ||
-      variant > 11 || (flags & ~3) || (mode != BICGK_BATCH_GRAPH && mode != BICGK_BATCH_LOOP))
+      variant > 11 || (flags & ~3) ||
+      (mode != BICGK_BATCH_GRAPH && mode != BICGK_BATCH_LOOP && mode != BICGK_BATCH_PERSISTENT))
     return BICGK_E_INVALID;
   const bool jacobi = (flags & BICGK_FLAG_JACOBI) != 0;
+  if (mode == BICGK_BATCH_PERSISTENT && (variant != BICGK_CLASSICAL_MERGED || jacobi)) {
+    g_cuda_err = "persistent batch mode runs merged classical BiCGStab (Algorithm 2) without preconditioner";
+    return BICGK_E_UNSUPPORTED;
+  }
   const int gkey = variant + 100 * (jacobi ? 1 : 0);
   for (int i = 0; i < b->nsys; ++i)
     if (!B[i] || !X[i]) return BICGK_E_INVALID;
@@ -1871,6 +2082,50 @@ int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const
     return BICGK_OK;
   }
   if ((rc = batch_ensure(b, maxit))) return rc;
+  if (mode == BICGK_BATCH_PERSISTENT) {  // one cooperative launch for every system
+    if ((rc = persist_prepare(b))) return rc;
+    for (int i = 0; i < b->nsys; ++i) {
+      Ctl *hc = b->h_ctl + i;
+      memset(hc, 0, sizeof(Ctl));
+      hc->tol = rel_tol;
+      hc->hist = b->ws[i].d_hist;
+      hc->maxit = maxit;
+      hc->k = b->k[i];
+      hc->kp = b->ws[i].kp;
+      hc->flags = flags;
+      PersistSys &S = b->h_psys[i];
+      S.B = B[i];
+      S.X0 = X0 ? X0[i] : nullptr;
+      S.X = X[i];
+      S.hist_len = (int64_t)(maxit + 1) * b->ws[i].kp;
+    }
+    CK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(Ctl) * b->nsys, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->d_psys, b->h_psys, sizeof(PersistSys) * b->nsys, cudaMemcpyHostToDevice, s));
+    if ((rc = persist_launch(b, s))) return rc;
+    CK(cudaMemcpyAsync(b->h_fl, b->d_fl, sizeof(int) * F_NFLAG * kMaxKp * b->nsys, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(b->h_sc, b->d_sc, sizeof(double) * S_NSLOT * kMaxKp * b->nsys, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(b->h_pc, b->d_pc, sizeof(PersistCtl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (b->h_pc->err) {
+      g_cuda_err = "persistent batch solve: grid barrier " + std::to_string(b->h_pc->err_barrier) +
+                   " of block " + std::to_string(b->h_pc->err_block) + " waited longer than the deadline (" +
+                   std::to_string(b->deadline_us) + " us); the solve was abandoned";
+      return BICGK_E_TIMEOUT;
+    }
+    for (int i = 0; i < b->nsys; ++i) {
+      const int *fl = b->h_fl + (size_t)i * F_NFLAG * kMaxKp;
+      const double *sc = b->h_sc + (size_t)i * S_NSLOT * kMaxKp;
+      for (int c = 0; c < b->k[i]; ++c) {
+        iters[off + c] = fl[F_ITERS * kMaxKp + c];
+        status[off + c] = fl[F_STATUS * kMaxKp + c];
+        if (true_relres) true_relres[off + c] = sc[S_TRUE * kMaxKp + c];
+      }
+      off += b->k[i];
+    }
+    b->p_loop_iters = b->h_pc->iters;
+    b->last_launches = 1;
+    return BICGK_OK;
+  }
   for (int i = 0; i < b->nsys; ++i)
     if ((rc = ensure_variant_data(b->ops[i], variant, jacobi, s))) return rc;
   for (int i = 0; i < b->nsys; ++i) {
@@ -1919,6 +2174,84 @@ int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const
   return BICGK_OK;
 }
 
+int bicgk_batch_tune_persistent(bicgk_batch b, int32_t reps, int32_t *rows_per_tile_out, void *stream) {
+  if (!b || reps < 1 || reps > 1000) return BICGK_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  // right-hand sides of ones and a scratch solution for every system (one buffer each, shared)
+  size_t most = 0;
+  for (int i = 0; i < b->nsys; ++i) {
+    const size_t e = (size_t)b->ops[i]->n * b->k[i];
+    if (e > most) most = e;
+  }
+  double *d_one = nullptr, *d_x = nullptr;
+  CK(cudaMalloc(&d_one, sizeof(double) * most));
+  cudaError_t e = cudaMalloc(&d_x, sizeof(double) * most);
+  if (e != cudaSuccess) {
+    cudaFree(d_one);
+    return cuda_fail(e, "bicgk_batch_tune_persistent");
+  }
+  std::vector<double> ones(most, 1.0);
+  std::vector<const double *> Bv(b->nsys, d_one);
+  std::vector<double *> Xv(b->nsys, d_x);
+  std::vector<int32_t> it(1 + std::accumulate(b->k.begin(), b->k.end(), 0)), st(it.size());
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = BICGK_OK;
+  if ((e = cudaMemcpy(d_one, ones.data(), sizeof(double) * most, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
+    rc = cuda_fail(e, "bicgk_batch_tune_persistent");
+  // rows per CTA tile: 1, 2, 4, 8 passes of 256 threads; 4 fixed iterations of every system
+  int best_sub = b->p_sub;
+  float best = 1e30f;
+  for (int sub = 1; sub <= 8 && rc == BICGK_OK; sub *= 2) {
+    b->p_sub = sub;
+    float total = 0.f;
+    for (int r = 0; r <= reps && rc == BICGK_OK; ++r) {
+      cudaEventRecord(e0, s);
+      rc = bicgk_batch_solve(b, Bv.data(), nullptr, Xv.data(), 0.0, 4, BICGK_CLASSICAL_MERGED,
+                             BICGK_FLAG_NO_STOP_TEST, BICGK_BATCH_PERSISTENT, it.data(), st.data(), nullptr, stream);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) total += ms;  // the first solve of a shape captures its graph
+    }
+    if (rc == BICGK_OK && total < best * 0.98f) {
+      best = total;
+      best_sub = sub;
+    }
+  }
+  b->p_sub = best_sub;
+  persist_drop_graph(b);
+  if (rc == BICGK_OK) rc = persist_prepare(b);
+  if (rc == BICGK_OK && rows_per_tile_out)
+    for (int i = 0; i < b->nsys; ++i) rows_per_tile_out[i] = persist_rows_per_pass(b->ws[i].kp) * best_sub;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d_one);
+  cudaFree(d_x);
+  return rc;
+}
+
+int bicgk_batch_set_deadline(bicgk_batch b, int64_t microseconds) {
+  if (!b || microseconds < 0 || microseconds > (int64_t)3600 * 1000000) return BICGK_E_INVALID;
+  if (b->deadline_us != microseconds) persist_drop_graph(b);  // the deadline is a kernel argument
+  b->deadline_us = microseconds;
+  return BICGK_OK;
+}
+
+int bicgk_batch_last_loop_iters(bicgk_batch b, int64_t *iters) {
+  if (!b || !iters) return BICGK_E_INVALID;
+  *iters = b->p_loop_iters;
+  return BICGK_OK;
+}
+
+int bicgk_batch_persistent_info(bicgk_batch b, int32_t *grid_blocks, int32_t *from_graph) {
+  if (!b) return BICGK_E_INVALID;
+  if (grid_blocks) *grid_blocks = b->p_grid;
+  if (from_graph) *from_graph = b->pgraph_ok ? 1 : 0;
+  return BICGK_OK;
+}
+
 int bicgk_batch_last_launches(bicgk_batch b, int64_t *kernel_launches) {
   if (!b || !kernel_launches) return BICGK_E_INVALID;
   *kernel_launches = b->last_launches;
@@ -1944,8 +2277,28 @@ __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
 void *g_static_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_static_scratch_mu;  // the per-device address is looked up once, by one thread
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// The caller's CSR is checked on the device before any product reads it: row pointers start at 0,
+// never decrease and end at nnz; every column index lies in [0, n).  Any violation sets *bad.
+__global__ void noalloc_csr_check(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                  int64_t n, int64_t nnz, int *bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool ok = true;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+    const int32_t a = rowptr[i];
+    if (i == 0 && a != 0) ok = false;
+    if (i == n && a != nnz) ok = false;
+    if (i < n && rowptr[i + 1] < a) ok = false;
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const int32_t c = colidx[e];
+    if (c < 0 || c >= n) ok = false;
+  }
+  if (!ok) atomicOr(bad, 1);
+}
 
 }  // namespace
 
@@ -1979,19 +2332,37 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
   const size_t b_part = round256(sizeof(double) * ((size_t)nsm * kPartBlocksPerSm + kMaxRedGroups) * kMaxDots * kMaxKp);
   const size_t b_ctl = round256(sizeof(Ctl));
   const size_t b_hist = round256(sizeof(double) * (size_t)hist_len);
-  const size_t need = b_vec + b_sc + b_fl + b_part + b_ctl + b_hist;
+  const size_t b_chk = 256;  // the CSR check's flag
+  const size_t need = b_vec + b_sc + b_fl + b_part + b_ctl + b_hist + b_chk;
   if (need > kStaticScratchBytes) {
     g_cuda_err = "bicgk_solve_noalloc: this problem needs " + std::to_string(need) +
                  " bytes of scratch; the static scratch holds " + std::to_string(kStaticScratchBytes);
     return BICGK_E_UNSUPPORTED;
   }
-  // first call on this device: host code needs the array's device address
-  if (!g_static_scratch_addr[dev]) {
-    void *p = nullptr;
-    CK(cudaGetSymbolAddress(&p, g_static_scratch));
-    g_static_scratch_addr[dev] = p;
+  // first call on this device: host code needs the array's device address (looked up under a
+  // lock, so first calls from several host threads at once are safe)
+  unsigned char *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_scratch_mu);
+    if (!g_static_scratch_addr[dev]) {
+      void *p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_static_scratch));
+      g_static_scratch_addr[dev] = p;
+    }
+    base = static_cast<unsigned char *>(g_static_scratch_addr[dev]);
   }
-  unsigned char *base = static_cast<unsigned char *>(g_static_scratch_addr[dev]);
+  // the CSR check, before anything reads the arrays
+  int *d_bad = reinterpret_cast<int *>(base + b_vec + b_sc + b_fl + b_part + b_ctl + b_hist);
+  int h_bad = 0;
+  CK(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+  noalloc_csr_check<<<nsm * 4, 256, 0, s>>>(rowptr, colidx, n_rows, nnz, d_bad);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h_bad) {
+    g_cuda_err = "bicgk_solve_noalloc: malformed CSR (row pointers or column indices)";
+    return BICGK_E_BAD_CSR;
+  }
   // an operator view of the caller's CSR and the static scratch (owns nothing)
   bicgk_op_s A;
   A.device = dev;

@@ -159,3 +159,15 @@ def perturbed27(n: int, seed: int, margin: float = 1.0) -> CSR:
     vals_a[:, 13] = -vals_a.sum(axis=1) + margin  # sum |off| + margin (all off-diagonals negative)
     vals = [vals_a[:, s] for s in range(27)]
     return _assemble(N, cols, vals, valid, f"perturbed27_{n}^3")
+
+
+def batch_draws(nsys: int = 64, seed: int = 11, lo: int = 16, hi: int = 64, kmax: int = 8):
+    """Grid edges and RHS counts of a batch of independent systems: system i has an n_i^3 grid,
+    n_i uniform on {lo..hi}, and k_i right-hand sides uniform on {1..kmax}, drawn from one
+    splitmix64 stream (the first nsys draws give the grids, the next nsys the RHS counts).  The
+    right-hand sides of system i are ``rhs(n_i^3, k_i, 200 + i)``.  The defaults are the batched
+    workload: 64 systems, grids 16^3..64^3, 1..8 right-hand sides."""
+    u = uniform01(seed, 2 * nsys)
+    grids = [int(lo + np.floor(x * (hi - lo + 1))) for x in u[:nsys]]
+    ks = [int(1 + np.floor(x * kmax)) for x in u[nsys:]]
+    return grids, ks

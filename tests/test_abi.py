@@ -62,6 +62,10 @@ def test_binding_constants_match_the_header():
         assert getattr(bicgk, name[len("BICGK_"):]) == value, name
     assert bicgk.FLAG_NO_STOP_TEST == _header_enum("BICGK_FLAG_")["BICGK_FLAG_NO_STOP_TEST"]
     assert bicgk.FLAG_JACOBI == _header_enum("BICGK_FLAG_")["BICGK_FLAG_JACOBI"]
+    for name, value in _header_enum("BICGK_BATCH_").items():
+        assert getattr(bicgk, name[len("BICGK_"):]) == value, name
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "bicgk.h")).read(), flags=re.S)
+    assert bicgk.E_TIMEOUT == int(re.search(r"BICGK_E_TIMEOUT\s*=\s*(-\d+)", text).group(1))
     forms = {k: v for k, v in _header_enum("BICGK_").items()
              if k.endswith(("_PLAIN", "_MERGED"))}
     assert len(forms) == 12

@@ -6,26 +6,33 @@ BiCGStab (Algorithm 2), solved as the benchmark solves it: graph mode with the d
 four concurrent column groups of 8 that narrow their layout as their columns stop, default
 launch shapes.
 
-What the oracle can check at this size:
-  * the SpMM output, every element (the oracle's product is cheap);
-  * trajectories of sampled columns: columns never interact (pinned bitwise on the oracle), so
-    the oracle solves a sample of columns on its own and x_m must agree after m fixed iterations;
-  * the full solve through properties that hold at any size: every column converged, its true
-    relative residual (recomputed here with the oracle's product) below the tolerance, and the
-    iteration counts of sampled columns inside the spread that the oracle's own equivalent forms
-    show on this nearly symmetric operator (rounding differences grow there, so the stopping
-    iterate is not unique; see the module doc of test_gpu_parity).
+What the oracle can check at this size (columns never interact -- pinned bitwise on the oracle --
+so it runs single columns concurrently, tests/oracle_bars.py):
+  * the SpMM output, every element;
+  * trajectories of all 32 columns: x_m after m = 1, 4, 8, 16 fixed iterations within 1e-12
+    relative, or ten times the oracle's own change of x_m under one rounding unit in b where that
+    is larger (rounding differences grow on this nearly symmetric operator; the bar is printed),
+    and the residual histories within 1e-10 (or ten times the oracle's own change);
+  * the full solve to tolerance on eight sampled columns (two or more in each group): solution
+    within ten times the oracle's own one-unit response, iteration counts within twice its
+    one-unit spread (at least +-1), and on every column the true relative residual (recomputed
+    with the oracle's product) below the tolerance;
+  * the same to-tolerance comparison at k = 1 and k = 4 (the one-lane-per-row SpMM and the group
+    SpMM at kp = 4): their columns are the first columns of the same block, so the oracle runs of
+    the sampled columns serve them too.
 """
 import numpy as np
 import pytest
 
 import oracle
+from oracle_bars import colerr, derived_bars, solve_columns, trajectory_bars
 from paper_1907_12874_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-N_GRID, K, SEED, TOL = 128, 32, 2, 1e-8
-SAMPLE = [0, 9, 18, 31]               # columns the oracle follows (one in each of the four groups)
+N_GRID, K, SEED, TOL, MAXIT = 128, 32, 2, 1e-8, 5000
+SAMPLE = [0, 1, 2, 3, 9, 18, 27, 31]      # groups of 8: columns 0-3 in the first, one or two in each other
+KW = dict(tol=TOL, maxit=MAXIT, variant="classical_merged")
 
 
 @pytest.fixture(scope="module")
@@ -33,6 +40,17 @@ def system():
     A = I.convdiff7(N_GRID)
     B = I.rhs(A.n, K, SEED)
     return A, B
+
+
+@pytest.fixture(scope="module")
+def oracle_sample(system):
+    """The oracle's to-tolerance solves of the sampled columns and the bars from its rounding
+    response (six draws per column)."""
+    A, B = system
+    ro = solve_columns(A, B, cols=SAMPLE, **KW)
+    assert np.all(ro.status == 0)
+    sol_bar, it_bar = derived_bars(A, B, ro, cols=SAMPLE, label="128^3 k=32 sampled columns", **KW)
+    return ro, sol_bar, it_bar
 
 
 @pytest.fixture(scope="module")
@@ -52,26 +70,30 @@ def test_full_size_spmm(bk, cuda, system):
     assert np.all(np.abs(Y - Yo) <= bound + 1e-300)
 
 
-def test_full_size_trajectory_sampled_columns(bk, cuda, system):
+def test_full_size_trajectory_all_columns(bk, cuda, system):
     torch = cuda
     A, B = system
-    Bs = np.ascontiguousarray(B[:, SAMPLE])
     with bk.Operator(A) as op:
         Bd = torch.from_numpy(B).cuda()
-        for m in (1, 3):
+        for m in (1, 4, 8, 16):
             r = op.solve(Bd, tol=0.0, maxit=m, flags=bk.FLAG_NO_STOP_TEST, want_hist=True)
-            X = r.X.cpu().numpy()[:, SAMPLE]
-            ro = oracle.solve(A, Bs, tol=0.0, maxit=m, variant="classical_merged", flags=oracle.NO_STOP_TEST)
-            err = np.linalg.norm(X - ro.X, axis=0) / np.linalg.norm(ro.X, axis=0)
-            assert np.all(err <= 1e-12), (m, err)
-            np.testing.assert_allclose(r.hist[: m + 1, SAMPLE], ro.hist[: m + 1], rtol=1e-10)
+            X = r.X.cpu().numpy()
+            bar, ro, sens, hbar = trajectory_bars(A, B, m)
+            err = colerr(X, ro.X)
+            herr = np.max(np.abs(r.hist[: m + 1] - ro.hist[: m + 1]) / np.abs(ro.hist[: m + 1]), axis=0)
+            print(f"[trajectory 128^3 k=32 m={m}] max GPU-oracle {err.max():.2e}, oracle one-unit response "
+                  f"max {sens.max():.2e}, bar max {bar.max():.2e}; history max {herr.max():.2e}, bar max "
+                  f"{hbar.max():.2e}")
+            assert np.all(err <= bar), (m, err, bar)
+            assert np.all(herr <= hbar), (m, herr, hbar)
 
 
-def test_full_size_solve(bk, cuda, system):
+def test_full_size_solve(bk, cuda, system, oracle_sample):
     torch = cuda
     A, B = system
+    ro, sol_bar, it_bar = oracle_sample
     with bk.Operator(A) as op:
-        r = op.solve(torch.from_numpy(B).cuda(), tol=TOL, maxit=5000, want_hist=False)
+        r = op.solve(torch.from_numpy(B).cuda(), tol=TOL, maxit=MAXIT, want_hist=False)
         X = r.X.cpu().numpy()
     assert np.all(r.status == 0), r.status
     R = B - oracle.spmm(A, X)
@@ -81,26 +103,82 @@ def test_full_size_solve(bk, cuda, system):
     # the library's own true residual: the residual is ~1e-8 ||b|| while recomputing b - Ax rounds
     # at u ||A|| ||x|| ~ 5e-12 ||b|| here, so two independent evaluations agree to ~1e-3 relative
     np.testing.assert_allclose(r.true_relres, relres, rtol=1e-2)
-    ro = oracle.solve(A, np.ascontiguousarray(B[:, SAMPLE]), tol=TOL, maxit=5000, variant="classical_merged")
-    assert np.all(ro.status == 0)
-    spread = np.maximum(2, 0.15 * ro.iters)
-    assert np.all(np.abs(r.iters[SAMPLE] - ro.iters) <= spread), (r.iters[SAMPLE], ro.iters)
+    err = colerr(X[:, SAMPLE], ro.X)
+    print(f"[solve 128^3 k=32] GPU-oracle {np.array2string(err, precision=2)}, iterations GPU "
+          f"{r.iters[SAMPLE].tolist()} oracle {ro.iters.tolist()}")
+    assert np.all(np.abs(r.iters[SAMPLE] - ro.iters) <= it_bar), (r.iters[SAMPLE], ro.iters, it_bar)
+    assert np.all(err <= sol_bar), (err, sol_bar)
 
 
 @pytest.mark.parametrize("k", [1, 4])
-def test_full_size_solve_small_k(bk, cuda, system, k):
-    """k = 1 and k = 4 at full size (the one-lane-per-row SpMM and the group SpMM at kp = 4): every
-    column converged, true residuals recomputed by the oracle below the tolerance, iteration counts
-    within the oracle's spread on this nearly symmetric operator."""
+def test_full_size_solve_small_k(bk, cuda, system, oracle_sample, k):
+    """k = 1 and k = 4 at full size: every column converged, true residuals recomputed by the
+    oracle below the tolerance, and each column against the oracle's solve of it with the bars of
+    the sampled columns (columns 0..3 of the benchmark block)."""
     torch = cuda
     A, Bfull = system
+    ro, sol_bar, it_bar = oracle_sample
     B = np.ascontiguousarray(Bfull[:, :k])
     with bk.Operator(A) as op:
-        r = op.solve(torch.from_numpy(B).cuda(), tol=TOL, maxit=5000, want_hist=False)
+        r = op.solve(torch.from_numpy(B).cuda(), tol=TOL, maxit=MAXIT, want_hist=False)
         X = r.X.cpu().numpy()
     assert np.all(r.status == 0), r.status
     relres = np.linalg.norm(B - oracle.spmm(A, X), axis=0) / np.linalg.norm(B, axis=0)
     assert np.all(relres < 2 * TOL), relres
-    ro = oracle.solve(A, B, tol=TOL, maxit=5000, variant="classical_merged")
+    err = colerr(X, ro.X[:, :k])
+    print(f"[solve 128^3 k={k}] GPU-oracle {np.array2string(err, precision=2)}, iterations GPU "
+          f"{r.iters.tolist()} oracle {ro.iters[:k].tolist()}")
+    assert np.all(np.abs(r.iters - ro.iters[:k]) <= it_bar[:k]), (r.iters, ro.iters[:k], it_bar[:k])
+    assert np.all(err <= sol_bar[:k]), (err, sol_bar[:k])
+
+
+# ------------------------------------------------------------------ mixed precision at full size
+
+MIXED_SAMPLE = [0, 13, 18, 31]          # two in each of the two column groups of the mixed solve
+MIXED_KW = dict(tol=1e-10, max_outer=20, inner_tol=1e-5, max_inner=5000)
+
+
+def test_full_size_mixed_matches_oracle(bk, cuda):
+    """The mixed-precision configuration at full size, as the benchmark runs it: perturbed 27-point
+    stencil on 128^3 (2,097,152 rows, 55,742,968 nonzeros), k = 32 (seed 3), FP32 inner solves in
+    FP64 refinement to relative residual 1e-10, two concurrent column groups.  Sampled columns
+    against oracle.solve_mixed element by element.
+
+    Bars from the oracle's own response to one FP32 rounding unit in its inner solves' input: a
+    one-unit change of b (2^-52) does not survive the rounding of the residual to FP32, so the
+    oracle instead starts from x0 = 2^-24 xi * x (xi standard normal, three draws), which moves the
+    FP32 right-hand side of the first inner solve by about one FP32 unit and leaves the problem
+    itself unchanged.  Per column: |x - x_oracle| <= 10 x the largest max-norm change of the
+    oracle's solution (at least 1e-10 max|x|), element by element; refinement passes within one; FP32 iteration totals
+    within twice the draws' spread (at least 2); true residual below the tolerance on every
+    column."""
+    torch = cuda
+    A = I.perturbed27(N_GRID, seed=7)
+    B = I.rhs(A.n, K, 3)
+    with bk.Operator(A) as op:
+        r = op.solve_mixed(torch.from_numpy(B).cuda(), want_hist=False, **MIXED_KW)
+        X = r.X.cpu().numpy()
+    assert np.all(r.status == 0), r.status
+    relres = np.linalg.norm(B - oracle.spmm(A, X), axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(relres < MIXED_KW["tol"]), relres
+    ro = solve_columns(A, B, cols=MIXED_SAMPLE, mixed=True, **MIXED_KW)
     assert np.all(ro.status == 0)
-    assert np.all(np.abs(r.iters - ro.iters) <= np.maximum(2, 0.15 * ro.iters)), (r.iters, ro.iters)
+    rng = np.random.default_rng(23)
+    resp = np.zeros(len(MIXED_SAMPLE))
+    inner = []
+    Bs = np.ascontiguousarray(B[:, MIXED_SAMPLE])
+    for _ in range(3):
+        X0 = 2.0 ** -24 * rng.standard_normal(ro.X.shape) * ro.X
+        rp = solve_columns(A, Bs, X0=X0, mixed=True, **MIXED_KW)
+        resp = np.maximum(resp, np.abs(rp.X - ro.X).max(axis=0))
+        inner.append(rp.inner_iters)
+    spread = np.abs(np.array(inner) - ro.inner_iters[None, :]).max(axis=0)
+    bar = np.maximum(10.0 * resp, 1e-10 * np.abs(ro.X).max(axis=0))
+    dev = np.abs(X[:, MIXED_SAMPLE] - ro.X).max(axis=0)
+    print(f"[mixed 128^3 k=32] max |x - x_oracle| {np.array2string(dev, precision=2)}, bar "
+          f"{np.array2string(bar, precision=2)} (max |x| {np.abs(ro.X).max():.2f}); passes GPU "
+          f"{r.outer_iters[MIXED_SAMPLE].tolist()} oracle {ro.outer_iters.tolist()}; FP32 iterations GPU "
+          f"{r.inner_iters[MIXED_SAMPLE].tolist()} oracle {ro.inner_iters.tolist()} spread {spread.tolist()}")
+    assert np.all(np.abs(X[:, MIXED_SAMPLE] - ro.X) <= bar[None, :]), (dev, bar)
+    assert np.all(np.abs(r.outer_iters[MIXED_SAMPLE] - ro.outer_iters) <= 1)
+    assert np.all(np.abs(r.inner_iters[MIXED_SAMPLE] - ro.inner_iters) <= np.maximum(2, 2 * spread))

@@ -4,9 +4,10 @@ The inner FP32 solves amplify rounding differences like any BiCGStab run, so
 the comparison is at the level the method fixes: both reach the FP64
 tolerance (true residual, recomputed in FP64), the refinement passes agree
 within one, the FP32 iteration totals within 20 % (40 % on the rounding-
-chaotic nearly symmetric operator), and the GPU solution is
-as close to the exact solution x* (sparse LU) as its residual allows:
-||x - x*|| <= ||A^-1|| ||b - A x||.
+chaotic nearly symmetric operator), the GPU solution is as close to the exact
+solution x* (sparse LU) as its residual allows: ||x - x*|| <= ||A^-1|| ||b - A x||,
+and element by element within ten times the oracle's own response to one FP32
+rounding unit in its inner solves' input (see oracle_response_fp32).
 """
 import numpy as np
 import pytest
@@ -21,6 +22,20 @@ pytestmark = pytest.mark.gpu
 def bk(cuda):
     from paper_1907_12874_gb300 import bicgk
     return bicgk
+
+
+def oracle_response_fp32(A, B, ro, draws=3, seed=23, X0=None, **kw):
+    """Per column, the largest max-norm change of oracle.solve_mixed's solution when its first FP32
+    inner solve sees a right-hand side moved by about one FP32 rounding unit.  A one-unit change of
+    b (2^-52) would not survive the rounding of the residual to FP32, so the oracle starts from
+    x0 + 2^-24 xi * x (xi standard normal) instead, which leaves the problem unchanged."""
+    rng = np.random.default_rng(seed)
+    resp = np.zeros(B.shape[1])
+    for _ in range(draws):
+        Xp = 2.0 ** -24 * rng.standard_normal(ro.X.shape) * ro.X
+        rp = oracle.solve_mixed(A, B, X0=Xp if X0 is None else X0 + Xp, **kw)
+        resp = np.maximum(resp, np.abs(rp.X - ro.X).max(axis=0))
+    return np.maximum(10.0 * resp, 1e-10 * np.abs(ro.X).max(axis=0))
 
 
 def _inv_norm(A):
@@ -64,6 +79,11 @@ def test_mixed_matches_oracle_and_exact(bk, cuda, case):
     # the FP64 solve to the same tolerance lands within the same bound
     err64 = np.linalg.norm(X - X64, axis=0) / np.linalg.norm(X64, axis=0)
     assert np.all(err64 <= 3 * inv * tol * np.linalg.norm(B, axis=0) / np.linalg.norm(X64, axis=0))
+    # element by element against the oracle's refinement
+    bar = oracle_response_fp32(A, B, ro, tol=tol, max_outer=20, inner_tol=1e-5, max_inner=2000)
+    dev = np.abs(X - ro.X).max(axis=0)
+    print(f"[mixed {case}] max |x - x_oracle| {np.array2string(dev, precision=2)}, bar {np.array2string(bar, precision=2)}")
+    assert np.all(np.abs(X - ro.X) <= bar[None, :]), (dev, bar)
     # the history is the FP64 true residual before each pass and contracts by ~inner_tol
     for c in range(k):
         h = r.hist[: r.outer_iters[c] + 1, c]
@@ -103,6 +123,7 @@ def test_mixed_column_groups(bk, cuda):
     X0 = 0.1 * I.rhs(A.n, k, 8)
     Bd, X0d = torch.from_numpy(B).cuda(), torch.from_numpy(X0).cuda()
     ro = oracle.solve_mixed(A, B, X0=X0, tol=tol, max_outer=20, inner_tol=1e-5, max_inner=2000)
+    bar = oracle_response_fp32(A, B, ro, X0=X0, tol=tol, max_outer=20, inner_tol=1e-5, max_inner=2000)
     inv, lu = _inv_norm(A)
     Xs = lu.solve(B)
     res = {}
@@ -127,6 +148,7 @@ def test_mixed_column_groups(bk, cuda):
         assert np.all(true < tol), (groups, true)
         err = np.linalg.norm(X - Xs, axis=0)
         assert np.all(err <= 1.5 * inv * true * np.linalg.norm(B, axis=0) + 1e-14), groups
+        assert np.all(np.abs(X - ro.X) <= bar[None, :]), (groups, np.abs(X - ro.X).max(axis=0), bar)
     X2 = res[0][1]
     assert np.array_equal(rh.X, X2) and np.array_equal(rh.inner_iters, res[0][0].inner_iters)
     assert np.array_equal(rp.X.numpy(), X2)

@@ -12,11 +12,13 @@ Three kinds of comparison:
   * full solve, nearly symmetric operators (the h-scaled convection-diffusion
     of the 16^3 configuration, Poisson): there BiCGStab amplifies rounding
     differences by about 10^3 every 8 iterations, so the stopping iterate is
-    not unique.  What is unique is the exact solution x* = A^-1 b (sparse LU):
-    the GPU iterate must be as close to x* as the oracle's (both are bounded by
-    ||A^-1|| times their residual), both true residuals below the tolerance,
-    and the iteration counts inside the spread the oracle's own equivalent
-    forms show (15%).
+    not unique: one rounding unit in b moves the oracle's own solution by up
+    to ~1e-7 and its iteration counts by up to 9.  The bars are measured on
+    the oracle per case (tests/oracle_bars.py): solution within ten times the
+    oracle's largest one-unit response (at least 1e-10), iterations within
+    twice its largest one-unit change (at least +-1), same status; besides,
+    both true residuals below the tolerance and the GPU iterate as close to
+    the exact solution x* = A^-1 b (sparse LU) as its residual allows.
 Inputs are the seeded synthetic stencils of the paper's workloads (Sec. 2.3:
 7-point Poisson; the upwind convection-diffusion and 27-point operators of the
 benchmark configurations).
@@ -26,6 +28,7 @@ import pytest
 
 import oracle
 from paper_1907_12874_gb300 import inputs as I
+from oracle_bars import derived_bars
 
 pytestmark = pytest.mark.gpu
 
@@ -148,16 +151,21 @@ def test_spmm_unaligned_caller_arrays(bk, cuda, k):
         assert torch.equal(Ya32, Yu32)
 
 
-def _compare_chaotic(r, X, ro, A, B, tol):
-    """Nearly symmetric operators: compare with the unique exact solution (see module doc)."""
+def _compare_chaotic(r, X, ro, A, B, tol, variant="classical_merged", maxit=1000):
+    """Nearly symmetric operators: bars from the oracle's own rounding response (module doc), and
+    the bound that ties the iterate to the unique exact solution x*."""
     import scipy.sparse.linalg as sla
+    sol_bar, it_bar = derived_bars(A, B, ro, tol=tol, maxit=maxit, variant=variant, label=f"{A.name} {variant}")
+    assert np.array_equal(r.status, ro.status), (r.status, ro.status)
+    assert np.all(np.abs(r.iters - ro.iters) <= it_bar), (r.iters, ro.iters, it_bar)
+    err = _colerr(X, ro.X)
+    assert np.all(err <= sol_bar), (err, sol_bar)
+    assert np.all(r.status == 0) and np.all(r.true_relres < 2 * tol) and np.all(ro.true_relres < 2 * tol)
     lu = sla.splu(A.to_scipy().tocsc())
     Xs = lu.solve(B)
-    assert np.all(r.status == 0) and np.all(ro.status == 0)
-    assert np.all(r.true_relres < 2 * tol) and np.all(ro.true_relres < 2 * tol)
     eg = np.linalg.norm(X - Xs, axis=0)
-    eo = np.linalg.norm(ro.X - Xs, axis=0)
-    # ||x - x*|| <= ||A^-1|| ||b - A x||: estimate ||A^-1|| by power iteration with the LU factors
+    # ||x - x*|| <= ||A^-1|| ||b - A x||: ||A^-1|| by power iteration with the LU factors (1.5 covers
+    # the estimate's shortfall)
     v = I.rhs(A.n, 1, 99)[:, 0]
     for _ in range(30):
         w = lu.solve(v)
@@ -166,8 +174,7 @@ def _compare_chaotic(r, X, ro, A, B, tol):
     inv_norm = np.sqrt(np.linalg.norm(lu.solve(lu.solve(v), trans="T")))
     bound = inv_norm * r.true_relres * np.linalg.norm(B, axis=0)
     assert np.all(eg <= 1.5 * bound + 1e-14), (eg, bound)
-    assert np.all(eg <= 20 * eo + 1e-12 * np.linalg.norm(Xs, axis=0)), (eg, eo)
-    assert np.all(np.abs(r.iters - ro.iters) <= np.maximum(2, 0.15 * ro.iters)), (r.iters, ro.iters)
+    return err
 
 
 def _trajectory(bk, torch, A, B, variant, ms=(1, 2, 4, 8), tol_traj=1e-12):
@@ -192,7 +199,7 @@ def test_config1_16cubed_k4(bk, cuda, variant):
     _trajectory(bk, cuda, A, B, variant)
     ro = oracle.solve(A, B, tol=1e-8, maxit=1000, variant=variant)
     r, X = _gpu_solve(bk, cuda, A, B, tol=1e-8, maxit=1000, variant=variant)
-    _compare_chaotic(r, X, ro, A, B, 1e-8)
+    _compare_chaotic(r, X, ro, A, B, 1e-8, variant=variant)
 
 
 def _oracle_rounding_sensitivity(A, B, variant, ro, reps=3, seed=11):
@@ -247,7 +254,7 @@ def test_k64_and_poisson(bk, cuda):
     _trajectory(bk, cuda, A, B, "classical_merged", ms=(1, 4, 8))
     ro = oracle.solve(A, B, tol=1e-9, maxit=1000, variant="classical_merged")
     r, X = _gpu_solve(bk, cuda, A, B, tol=1e-9, maxit=1000, variant="classical_merged")
-    _compare_chaotic(r, X, ro, A, B, 1e-9)
+    _compare_chaotic(r, X, ro, A, B, 1e-9, variant="classical_merged")
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -338,6 +345,28 @@ def test_profiling_mode_matches_graph_mode(bk, cuda):
         bk.set_profiling(op.handle, False)
     assert torch.equal(rg.X, rp.X)
     assert "merged_pszqy_3dots" in times and times["merged_pszqy_3dots"][0] == int(rp.iters.max())
+
+
+@pytest.mark.parametrize("k", [8, 20, 32])
+def test_profiling_mode_keeps_the_column_groups(bk, cuda, k):
+    """The profiling mode runs the graph mode's column groups one after another: the same kernels
+    (names carry the group's column count), bitwise the graph mode's results without compaction."""
+    torch = cuda
+    A = I.convdiff7(12, peclet=True)
+    B = torch.from_numpy(I.rhs(A.n, k, 13)).cuda()
+    with bk.Operator(A) as op:
+        bk.set_option(op.handle, bk.OPT_COMPACT, 1)
+        rg = op.solve(B, tol=1e-8, maxit=500)
+        groups = bk.last_stats(op.handle)["groups"]
+        bk.set_profiling(op.handle, True)
+        rp = op.solve(B, tol=1e-8, maxit=500)
+        assert bk.last_stats(op.handle)["groups"] == groups
+        times = bk.kernel_times(op.handle)
+        bk.set_profiling(op.handle, False)
+    assert groups == (4 if k >= 32 else 2)
+    assert torch.equal(rg.X, rp.X) and np.array_equal(rg.iters, rp.iters)
+    kg = 1 << (k // groups - 1).bit_length()
+    assert any(name.endswith(f"_k{kg}") for name in times), times.keys()
 
 
 def test_bad_csr_rejected(bk, cuda):
