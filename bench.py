@@ -67,6 +67,9 @@ def parse():
                    help="skip the differentiable solve (64^3, k = 8: forward + adjoint backward)")
     p.add_argument("--profile-mixed", action="store_true",
                    help="only the mixed-precision solve at --mixed-grid, in the host-loop mode (profiler captures)")
+    p.add_argument("--profile-batch", action="store_true",
+                   help="only the batched workload in the persistent mode, 10 fixed iterations, twice "
+                        "(profiler captures of the persistent kernel)")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batching comparison (64 systems, grids 16^3..64^3, 1..8 RHS)")
     p.add_argument("--eager", action="store_true",
@@ -696,6 +699,22 @@ def main():
             times = bicgk.kernel_times(opm.handle)
         print(json.dumps({"profile_mixed": True, "grid": args.mixed_grid, "outer": int(r.outer_iters.max()),
                           "inner": float(r.inner_iters.mean()), "kernel_ms": times}), flush=True)
+        return
+
+    if args.profile_batch:
+        grids, ks = inputs.batch_draws()
+        csrs = [inputs.convdiff7(n) for n in grids]
+        Bs = [torch.from_numpy(inputs.rhs(c.n, k, 200 + i)).to(dev) for i, (c, k) in enumerate(zip(csrs, ks))]
+        with bicgk.Batch(csrs, ks) as bt:
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                _, iters, _, _ = bt.solve(Bs, tol=0.0, maxit=10, flags=bicgk.FLAG_NO_STOP_TEST,
+                                          mode=bicgk.BATCH_PERSISTENT)
+                e1.record()
+                torch.cuda.synchronize()
+            print(json.dumps({"profile_batch": True, "ms_10_iterations": e0.elapsed_time(e1),
+                              "persistent": bt.persistent_info(), "column_iterations": int(iters.sum())}), flush=True)
         return
 
     A = inputs.convdiff7(args.grid)

@@ -354,8 +354,9 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value);
  * bicgk_batch_last_loop_iters: iterations the persistent kernel's loop ran in the last
  *   persistent solve (the slowest system's).
  * bicgk_batch_persistent_info: blocks of the persistent grid (co-resident: SMs x blocks per
- *   SM) and whether its launch is replayed from a CUDA graph (1) or launched directly (0, a
- *   runtime that cannot capture cooperative launches); nullable outputs.
+ *   SM) and whether its launch is replayed from a CUDA graph (1: a graph of three memset nodes
+ *   and one cooperative kernel node) or launched directly (0: the runtime refused the graph;
+ *   graph_error is the cudaError_t it gave); nullable outputs.
  */
 typedef struct bicgk_batch_s *bicgk_batch;
 enum bicgk_batch_mode { BICGK_BATCH_GRAPH = 0, BICGK_BATCH_LOOP = 1, BICGK_BATCH_PERSISTENT = 2 };
@@ -371,7 +372,7 @@ int bicgk_batch_tune_persistent(bicgk_batch b, int32_t reps, int32_t *rows_per_t
 int bicgk_batch_set_deadline(bicgk_batch b, int64_t microseconds);
 int bicgk_batch_last_launches(bicgk_batch b, int64_t *kernel_launches);
 int bicgk_batch_last_loop_iters(bicgk_batch b, int64_t *iters);
-int bicgk_batch_persistent_info(bicgk_batch b, int32_t *grid_blocks, int32_t *from_graph);
+int bicgk_batch_persistent_info(bicgk_batch b, int32_t *grid_blocks, int32_t *from_graph, int32_t *graph_error);
 int bicgk_batch_destroy(bicgk_batch b);
 
 /* Release the operator and all device memory it holds.  NULL is accepted. */

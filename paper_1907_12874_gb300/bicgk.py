@@ -77,7 +77,8 @@ def _load():
             lib.bicgk_batch_last_loop_iters.argtypes = [vp, ctypes.POINTER(i64)]
             lib.bicgk_batch_tune_persistent.argtypes = [vp, i32, vp, vp]
             lib.bicgk_batch_set_deadline.argtypes = [vp, i64]
-            lib.bicgk_batch_persistent_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+            lib.bicgk_batch_persistent_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                                        ctypes.POINTER(i32)]
             lib.bicgk_batch_destroy.argtypes = [vp]
             for f in ("bicgk_batch_create", "bicgk_batch_tune", "bicgk_batch_solve", "bicgk_batch_last_launches",
                       "bicgk_batch_last_loop_iters", "bicgk_batch_tune_persistent", "bicgk_batch_set_deadline",
@@ -463,10 +464,10 @@ class Batch:
                "bicgk_batch_set_deadline")
 
     def persistent_info(self) -> dict:
-        g, f = ctypes.c_int32(), ctypes.c_int32()
-        _check(_load().bicgk_batch_persistent_info(ctypes.c_void_p(self.handle), ctypes.byref(g), ctypes.byref(f)),
-               "persistent_info")
-        return {"grid_blocks": g.value, "from_graph": bool(f.value)}
+        g, f, e = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_load().bicgk_batch_persistent_info(ctypes.c_void_p(self.handle), ctypes.byref(g), ctypes.byref(f),
+                                                   ctypes.byref(e)), "persistent_info")
+        return {"grid_blocks": g.value, "from_graph": bool(f.value), "graph_error": e.value}
 
     def last_loop_iters(self) -> int:
         n = ctypes.c_int64()

@@ -1663,7 +1663,8 @@ struct bicgk_batch_s {
   int64_t deadline_us = 1000000;  // longest wait at one grid barrier
   GraphEntry pgraph;          // clear the control block, the cooperative kernel
   bool pgraph_ok = false;
-  bool p_direct = false;      // the runtime could not capture the cooperative launch
+  bool p_direct = false;      // the runtime could not put the cooperative launch in a graph
+  int p_capture_err = 0;      // the cudaError_t it gave
   int64_t p_loop_iters = 0;
 };
 
@@ -1841,22 +1842,37 @@ int persist_launch(bicgk_batch b, cudaStream_t s) {
   pa.pad = 0;
   pa.deadline_ns = (unsigned long long)b->deadline_us * 1000ull;
   if (!b->pgraph_ok && !b->p_direct) {
-    cudaStream_t cs = b->ops[0]->cap_stream;
+    // graph: clear the control block, tickets and liveness; then the cooperative kernel node
     cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(b->d_pc, 0, sizeof(PersistCtl), cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_tickets, 0, sizeof(unsigned) * b->nsys, cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_live, 0, sizeof(int) * b->nsys, cs);
-    if (e == cudaSuccess) e = launch_persist(pa, b->p_grid, cs);
-    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-    if (e == cudaSuccess && e2 == cudaSuccess) e2 = cudaGraphInstantiate(&b->pgraph.exec, g, 0);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      // a runtime that cannot capture a cooperative launch: launch it directly from now on
+    cudaGraphExec_t ge = nullptr;
+    cudaGraphNode_t m[3], kn;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    const struct {
+      void *p;
+      size_t bytes;
+    } clr[3] = {{b->d_pc, sizeof(PersistCtl)}, {b->d_tickets, sizeof(unsigned) * b->nsys},
+                {b->d_live, sizeof(int) * b->nsys}};
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+      cudaMemsetParams mp = {};
+      mp.dst = clr[i].p;
+      mp.value = 0;
+      mp.elementSize = 4;
+      mp.width = clr[i].bytes / 4;
+      mp.height = 1;
+      mp.pitch = clr[i].bytes;
+      e = cudaGraphAddMemsetNode(&m[i], g, nullptr, 0, &mp);
+    }
+    if (e == cudaSuccess) e = add_persist_node(g, m, 3, pa, b->p_grid, &kn);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e != cudaSuccess) {
+      // a runtime that cannot put a cooperative launch in a graph: launch it directly from now on
       if (g) cudaGraphDestroy(g);
+      b->p_capture_err = (int)e;
       cudaGetLastError();
       b->p_direct = true;
     } else {
       b->pgraph.graph = g;
+      b->pgraph.exec = ge;
       b->pgraph_ok = true;
     }
   }
@@ -2245,10 +2261,11 @@ int bicgk_batch_last_loop_iters(bicgk_batch b, int64_t *iters) {
   return BICGK_OK;
 }
 
-int bicgk_batch_persistent_info(bicgk_batch b, int32_t *grid_blocks, int32_t *from_graph) {
+int bicgk_batch_persistent_info(bicgk_batch b, int32_t *grid_blocks, int32_t *from_graph, int32_t *graph_error) {
   if (!b) return BICGK_E_INVALID;
   if (grid_blocks) *grid_blocks = b->p_grid;
   if (from_graph) *from_graph = b->pgraph_ok ? 1 : 0;
+  if (graph_error) *graph_error = b->p_capture_err;
   return BICGK_OK;
 }
 

@@ -23,11 +23,13 @@
 // Set-up: pack B, X0 (barrier); r = b - A x, r0 = p = r, (b, b), (r, r) -> eps, rho (barrier).
 // Final: true residual ||b - A x|| and X out.
 //
-// Dot products: a lane's row products -> warp butterfly over the lanes of a column -> warps in
-// order -> one partial per tile and dot -> the block that finishes a system's LAST tile of the
-// phase (atomic ticket, no wait) sums that system's tile partials in tile order and runs the
-// listing's scalar rule for every column (bicgk_rules.cuh).  The order is fixed by the tiling, so
-// results are bitwise reproducible.
+// Dot products: a lane's row products, summed over the block's tiles of the system in tile order
+// (a system's tiles are contiguous, so a block meets its tiles of one system one after another)
+// -> warp butterfly over the lanes of a column -> warps in order -> one partial per block and
+// system -> the last of the system's min(G, tiles) blocks to arrive (atomic ticket, no wait) sums
+// the partials in block-slot order and runs the listing's scalar rule for every column
+// (bicgk_rules.cuh).  The order is fixed by the tiling and the grid, so results are bitwise
+// reproducible.
 //
 // Grid barrier: arrival counter (64-bit, monotone within a launch, cleared by the host before
 // every launch) and a spin of thread 0 of each block on an acquire load.  Every wait is bounded:
@@ -65,47 +67,43 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
 }
 
 // Grid-wide barrier with a deadline.  Returns false if this launch was aborted (by this block's
-// own timeout or another's).
-struct GridBarrier {
-  unsigned long long *count;
-  PersistCtl *pc;
-  unsigned long long target;
-  unsigned long long deadline_ns;
-  unsigned long long max_spins;
-  int index;
-
-  __device__ bool sync(int *s_ok) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      target += gridDim.x;
-      index += 1;
-      __threadfence();
-      atomicAdd(count, 1ULL);
-      int ok = 1;
-      const unsigned long long t0 = gtimer();
-      for (unsigned long long spin = 0;; ++spin) {
-        if (ld_acquire_u64(count) >= target) break;
-        if (ld_relaxed_i32(&pc->err)) {
-          ok = 0;
-          break;
-        }
-        if (gtimer() - t0 > deadline_ns || spin >= max_spins) {
-          if (atomicCAS(&pc->err, 0, 1) == 0) {
-            pc->err_barrier = index;
-            pc->err_block = blockIdx.x;
-          }
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+// own timeout or another's).  Only thread 0 of a block waits; its arrival target and barrier
+// count live in shared memory (no registers held across the phases).
+__device__ bool grid_sync(const PersistArgs &pa, unsigned long long *s_target, int *s_index, int *s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long target = *s_target + gridDim.x;
+    const int index = *s_index + 1;
+    *s_target = target;
+    *s_index = index;
+    PersistCtl *pc = pa.pc;
+    const unsigned long long max_spins = pa.deadline_ns / 16 + 1000000ull;
+    __threadfence();
+    atomicAdd(&pc->bar, 1ULL);
+    int ok = 1;
+    const unsigned long long t0 = gtimer();
+    for (unsigned long long spin = 0;; ++spin) {
+      if (ld_acquire_u64(&pc->bar) >= target) break;
+      if (ld_relaxed_i32(&pc->err)) {
+        ok = 0;
+        break;
       }
-      __threadfence();
-      *s_ok = ok;
+      if (gtimer() - t0 > pa.deadline_ns || spin >= max_spins) {
+        if (atomicCAS(&pc->err, 0, 1) == 0) {
+          pc->err_barrier = index;
+          pc->err_block = blockIdx.x;
+        }
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
     }
-    __syncthreads();
-    return *s_ok != 0;
+    __threadfence();
+    *s_ok = ok;
   }
-};
+  __syncthreads();
+  return *s_ok != 0;
+}
 
 // Lanes per row, rows per 256-thread pass, columns per lane.
 template <int KP>
@@ -154,6 +152,8 @@ struct Smem {
   double red[kPT / 32][3][kMaxKp];  // per-warp dot sums of a tile
   double tmp[kPT];                  // system reduction: per-thread sums
   double res[3 * kMaxKp];           // system reduction: the dots, [d * kp + c]
+  unsigned long long bar_target;  // grid barrier: arrivals that complete the next barrier
+  int bar_index;                  // grid barrier: barriers passed
   int ok;
   int last;
   double sval[kPersistStage];       // staged CSR entries of a tile (kp <= 2)
@@ -198,7 +198,7 @@ __device__ __forceinline__ double2 row_product(const PersistSys &S, const double
   return acc;
 }
 
-// Sum the lanes' dot accumulators of one tile and store the tile's partial [tile][d][c].
+// Sum the lanes' dot accumulators over the block and store the block's partial [slot][d][c].
 template <int KP, int ND>
 __device__ void tile_partials(const PersistSys &S, int tl, double2 (&acc)[3], Smem &sm) {
   constexpr int L = Geo<KP>::L;
@@ -230,21 +230,21 @@ __device__ void tile_partials(const PersistSys &S, int tl, double2 (&acc)[3], Sm
   }
 }
 
-// The block that completes a system's last tile of a phase: true if it is this block.
-__device__ bool arrive(const PersistSys &S, unsigned *ticket, Smem &sm) {
+// Whether this block is the last of the `parts` blocks that contribute to a system in a phase.
+__device__ bool arrive(unsigned *ticket, int parts, Smem &sm) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned prev = atomicAdd(ticket, 1u);
-    sm.last = prev == (unsigned)(S.ntiles - 1);
+    sm.last = prev == (unsigned)(parts - 1);
   }
   __syncthreads();
   if (sm.last) __threadfence();
   return sm.last != 0;
 }
 
-// Sum of the system's tile partials in tile order (fixed split over threads), into sm.res.
+// Sum of the system's `parts` block partials in slot order (fixed split over threads), into sm.res.
 template <int KP, int ND>
-__device__ void sys_sum(const PersistSys &S, Smem &sm) {
+__device__ void sys_sum(const PersistSys &S, int parts, Smem &sm) {
   constexpr int P = ND * KP;
   constexpr int T = kPT / P;  // threads per (dot, column)
   const int t = threadIdx.x;
@@ -252,7 +252,7 @@ __device__ void sys_sum(const PersistSys &S, Smem &sm) {
     const int p = t / T, u = t % T;
     const int d = p / KP, c = p % KP;
     double s = 0.0;
-    for (int tl = u; tl < S.ntiles; tl += T) s += __ldcg(S.part + ((int64_t)tl * 3 + d) * KP + c);
+    for (int tl = u; tl < parts; tl += T) s += __ldcg(S.part + ((int64_t)tl * 3 + d) * KP + c);
     sm.tmp[t] = s;
   }
   __syncthreads();
@@ -279,28 +279,51 @@ __device__ KArgs rule_args(const PersistSys &S, int kp) {
 
 enum Phase : int { PH_PACK = 0, PH_SETUP, PH_P1, PH_P2, PH_P3, PH_P4, PH_P5, PH_FINAL };
 
-// One tile of one phase for a system with kp = KP.
+// Dot products a phase takes, and whether it multiplies by A.
+template <int PH>
+struct PhaseInfo {
+  static constexpr int ND = PH == PH_SETUP ? 2 : PH == PH_P1 ? 1 : PH == PH_P3 ? 3 : PH == PH_P4 ? 1 : PH == PH_FINAL ? 1 : 0;
+  static constexpr bool SPMM = PH == PH_SETUP || PH == PH_P1 || PH == PH_P3 || PH == PH_FINAL;
+};
+
+// The lane's per-column scalars a phase uses (alpha, omega, beta, the x-update flags), loaded once
+// per block and system when the block reaches its first tile of the system.
+struct LaneSc {
+  double2 al, om, be;
+  bool u0, u1;
+};
 template <int KP, int PH>
-__device__ void run_tile(const PersistArgs &pa, int si, const PersistSys &S, int tl, Smem &sm) {
+__device__ LaneSc lane_scalars(const PersistSys &S) {
+  const int q = threadIdx.x % Geo<KP>::L;
+  LaneSc ls;
+  ls.al = ls.om = ls.be = make_double2(0.0, 0.0);
+  ls.u0 = ls.u1 = false;
+  if constexpr (PH == PH_P2 || PH == PH_P4) ls.al = sc2<KP>(S, S_ALPHA, q);
+  if constexpr (PH == PH_P4 || PH == PH_P5) ls.om = sc2<KP>(S, S_OMEGA, q);
+  if constexpr (PH == PH_P5) ls.be = sc2<KP>(S, S_BETA, q);
+  if constexpr (PH == PH_P4) {
+    ls.u0 = __ldcg(S.fl + F_XUPD * kMaxKp + 2 * q) != 0;
+    ls.u1 = KP > 1 && __ldcg(S.fl + F_XUPD * kMaxKp + 2 * q + 1) != 0;
+  }
+  return ls;
+}
+
+// One tile of one phase for a system with kp = KP; the lane's dot products are added to acc.
+// Not inlined: each (KP, phase) routine gets the block's whole register budget (inlined into the
+// one kernel, the union of their live values spilled inside the row loops); the call costs a few
+// local-memory moves per tile.
+template <int KP, int PH>
+__device__ __noinline__ void run_tile(const PersistSys &S, int tl, Smem &sm, double2 (&acc)[3], const LaneSc &ls) {
   constexpr int L = Geo<KP>::L, RPP = Geo<KP>::RPP;
-  constexpr int ND = PH == PH_SETUP ? 2 : PH == PH_P1 ? 1 : PH == PH_P3 ? 3 : PH == PH_P4 ? 1 : PH == PH_FINAL ? 1 : 0;
-  constexpr bool SPMM = PH == PH_SETUP || PH == PH_P1 || PH == PH_P3 || PH == PH_FINAL;
+  constexpr bool SPMM = PhaseInfo<PH>::SPMM;
   const int q = threadIdx.x % L;
   const int rr = threadIdx.x / L;
   const int64_t rows = (int64_t)RPP * S.sub;
   const int64_t r0 = (int64_t)tl * rows;
   const int64_t r1 = r0 + rows < S.n ? r0 + rows : S.n;
   double *const *V = S.vec;
-  double2 acc[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-  double2 al = make_double2(0.0, 0.0), om = al, be = al;
-  bool u0 = false, u1 = false;
-  if constexpr (PH == PH_P2 || PH == PH_P4 || PH == PH_P5) al = sc2<KP>(S, S_ALPHA, q);
-  if constexpr (PH == PH_P4 || PH == PH_P5) om = sc2<KP>(S, S_OMEGA, q);
-  if constexpr (PH == PH_P5) be = sc2<KP>(S, S_BETA, q);
-  if constexpr (PH == PH_P4) {
-    u0 = __ldcg(S.fl + F_XUPD * kMaxKp + 2 * q) != 0;
-    u1 = KP > 1 && __ldcg(S.fl + F_XUPD * kMaxKp + 2 * q + 1) != 0;
-  }
+  const double2 al = ls.al, om = ls.om, be = ls.be;
+  const bool u0 = ls.u0, u1 = ls.u1;
   for (int64_t p0 = r0; p0 < r1; p0 += RPP) {
     const int64_t pe = p0 + RPP < r1 ? p0 + RPP : r1;
     int te0 = 0;
@@ -392,48 +415,57 @@ __device__ void run_tile(const PersistArgs &pa, int si, const PersistSys &S, int
       for (int t = threadIdx.x; t < F_NFLAG * kMaxKp; t += kPT) S.fl[t] = 0;
     }
   }
-  if constexpr (ND > 0) {
-    tile_partials<KP, ND>(S, tl, acc, sm);
-    if (!arrive(S, pa.tickets + si, sm)) return;
-    sys_sum<KP, ND>(S, sm);
-    const KArgs a = rule_args(S, KP);
-    const int c = threadIdx.x;
-    if constexpr (PH == PH_SETUP) {
-      if (c < KP) fin_col<FIN_SETUP>(a, c, sm.res, KP);
-    } else if constexpr (PH == PH_P1) {
-      if (c < KP) fin_col<FIN_DELTA>(a, c, sm.res, KP);
-    } else if constexpr (PH == PH_P3) {
-      if (c < KP) fin_col<FIN_G1>(a, c, sm.res, KP);
-    } else if constexpr (PH == PH_P4) {
-      if (c < KP) fin_col<FIN_RHO>(a, c, sm.res, KP);
-    } else if constexpr (PH == PH_FINAL) {
-      if (c < KP) fin_col<FIN_TRUE>(a, c, sm.res, KP);
+}
+
+// The block's dot sums for system si in this phase (its tiles of si are consecutive in its tile
+// order): one partial per block at `slot` (the offset of the block's first tile of si), then the
+// system's last arriving block sums the min(G, ntiles) partials in slot order and runs the
+// listing's scalar rule.
+template <int KP, int PH>
+__device__ void flush(const PersistArgs &pa, int si, int slot, double2 (&acc)[3], Smem &sm) {
+  constexpr int ND = PhaseInfo<PH>::ND;
+  const PersistSys &S = pa.sys[si];
+  const int parts = S.ntiles < (int)gridDim.x ? S.ntiles : (int)gridDim.x;
+  tile_partials<KP, ND>(S, slot, acc, sm);
+  if (!arrive(pa.tickets + si, parts, sm)) return;
+  sys_sum<KP, ND>(S, parts, sm);
+  const KArgs a = rule_args(S, KP);
+  const int c = threadIdx.x;
+  if constexpr (PH == PH_SETUP) {
+    if (c < KP) fin_col<FIN_SETUP>(a, c, sm.res, KP);
+  } else if constexpr (PH == PH_P1) {
+    if (c < KP) fin_col<FIN_DELTA>(a, c, sm.res, KP);
+  } else if constexpr (PH == PH_P3) {
+    if (c < KP) fin_col<FIN_G1>(a, c, sm.res, KP);
+  } else if constexpr (PH == PH_P4) {
+    if (c < KP) fin_col<FIN_RHO>(a, c, sm.res, KP);
+  } else if constexpr (PH == PH_FINAL) {
+    if (c < KP) fin_col<FIN_TRUE>(a, c, sm.res, KP);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pa.tickets[si] = 0u;  // the next phase's arrivals come after a grid barrier
+    if constexpr (PH == PH_SETUP || PH == PH_P4) {
+      // loop control of this system (the last reducing step of the set-up / of an iteration)
+      Ctl *ctl = S.ctl;
+      int any = 0;
+      for (int cc = 0; cc < KP; ++cc) any |= S.fl[F_ACT * kMaxKp + cc];
+      ctl->any_active = any;
+      int go;
+      if constexpr (PH == PH_SETUP) {
+        go = any && ctl->maxit > 0;
+        if (go) atomicAdd(&pa.pc->running, 1);
+      } else {
+        const int j = ctl->iter + 1;
+        ctl->iter = j;
+        ctl->loop_iters = j;
+        go = any && j < ctl->maxit;
+        if (!go) atomicSub(&pa.pc->running, 1);
+      }
+      pa.live[si] = go;
     }
     __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      pa.tickets[si] = 0u;  // the next phase's arrivals come after a grid barrier
-      if constexpr (PH == PH_SETUP || PH == PH_P4) {
-        // loop control of this system (the last reducing step of the set-up / of an iteration)
-        Ctl *ctl = S.ctl;
-        int any = 0;
-        for (int cc = 0; cc < KP; ++cc) any |= S.fl[F_ACT * kMaxKp + cc];
-        ctl->any_active = any;
-        int go;
-        if constexpr (PH == PH_SETUP) {
-          go = any && ctl->maxit > 0;
-          if (go) atomicAdd(&pa.pc->running, 1);
-        } else {
-          const int j = ctl->iter + 1;
-          ctl->iter = j;
-          ctl->loop_iters = j;
-          go = any && j < ctl->maxit;
-          if (!go) atomicSub(&pa.pc->running, 1);
-        }
-        pa.live[si] = go;
-      }
-      __threadfence();
-    }
   }
 }
 
@@ -449,51 +481,114 @@ __device__ int find_sys(const PersistArgs &pa, int64_t t) {
 }
 
 template <int PH>
+__device__ void flush_kp(const PersistArgs &pa, int si, int slot, double2 (&acc)[3], Smem &sm) {
+  switch (pa.sys[si].kp) {
+    case 1: flush<1, PH>(pa, si, slot, acc, sm); break;
+    case 2: flush<2, PH>(pa, si, slot, acc, sm); break;
+    case 4: flush<4, PH>(pa, si, slot, acc, sm); break;
+    case 8: flush<8, PH>(pa, si, slot, acc, sm); break;
+    case 16: flush<16, PH>(pa, si, slot, acc, sm); break;
+    case 32: flush<32, PH>(pa, si, slot, acc, sm); break;
+    default: flush<64, PH>(pa, si, slot, acc, sm); break;
+  }
+}
+
+// Block b takes tiles b, b + G, ...; a system's tiles are contiguous, so the block meets its tiles
+// of one system one after another and sums their dot products before one flush per system.
+template <int PH>
 __device__ void run_phase(const PersistArgs &pa, Smem &sm, bool live_only) {
+  constexpr int ND = PhaseInfo<PH>::ND;
+  int cur = -1, slot = 0;
+  double2 acc[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  LaneSc ls;
   for (int64_t t = blockIdx.x; t < pa.ntiles; t += gridDim.x) {
     const int si = find_sys(pa, t);
-    const PersistSys &S = pa.sys[si];
     if (live_only && !__ldcg(pa.live + si)) continue;
+    const PersistSys &S = pa.sys[si];
     const int tl = (int)(t - S.tile0);
-    switch (S.kp) {
-      case 1: run_tile<1, PH>(pa, si, S, tl, sm); break;
-      case 2: run_tile<2, PH>(pa, si, S, tl, sm); break;
-      case 4: run_tile<4, PH>(pa, si, S, tl, sm); break;
-      case 8: run_tile<8, PH>(pa, si, S, tl, sm); break;
-      case 16: run_tile<16, PH>(pa, si, S, tl, sm); break;
-      case 32: run_tile<32, PH>(pa, si, S, tl, sm); break;
-      default: run_tile<64, PH>(pa, si, S, tl, sm); break;
+    if (si != cur) {
+      if constexpr (ND > 0) {
+        if (cur >= 0) flush_kp<PH>(pa, cur, slot, acc, sm);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[d] = make_double2(0.0, 0.0);
+      }
+      cur = si;
+      slot = tl;
+      switch (S.kp) {
+        case 1: ls = lane_scalars<1, PH>(S); break;
+        case 2: ls = lane_scalars<2, PH>(S); break;
+        case 4: ls = lane_scalars<4, PH>(S); break;
+        case 8: ls = lane_scalars<8, PH>(S); break;
+        case 16: ls = lane_scalars<16, PH>(S); break;
+        case 32: ls = lane_scalars<32, PH>(S); break;
+        default: ls = lane_scalars<64, PH>(S); break;
+      }
     }
+    switch (S.kp) {
+      case 1: run_tile<1, PH>(S, tl, sm, acc, ls); break;
+      case 2: run_tile<2, PH>(S, tl, sm, acc, ls); break;
+      case 4: run_tile<4, PH>(S, tl, sm, acc, ls); break;
+      case 8: run_tile<8, PH>(S, tl, sm, acc, ls); break;
+      case 16: run_tile<16, PH>(S, tl, sm, acc, ls); break;
+      case 32: run_tile<32, PH>(S, tl, sm, acc, ls); break;
+      default: run_tile<64, PH>(S, tl, sm, acc, ls); break;
+    }
+  }
+  if constexpr (ND > 0) {
+    if (cur >= 0) flush_kp<PH>(pa, cur, slot, acc, sm);
   }
 }
 
 __global__ void __launch_bounds__(kPT, kPersistMaxBlocksPerSm) persist_kernel(const PersistArgs pa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-  GridBarrier bar{&pa.pc->bar, pa.pc, 0ull, pa.deadline_ns, pa.deadline_ns / 16 + 1000000ull, 0};
+  if (threadIdx.x == 0) {
+    sm.bar_target = 0ull;
+    sm.bar_index = 0;
+  }
   run_phase<PH_PACK>(pa, sm, false);
-  if (!bar.sync(&sm.ok)) return;
+  if (!grid_sync(pa, &sm.bar_target, &sm.bar_index, &sm.ok)) return;
   run_phase<PH_SETUP>(pa, sm, false);
-  if (!bar.sync(&sm.ok)) return;
+  if (!grid_sync(pa, &sm.bar_target, &sm.bar_index, &sm.ok)) return;
   for (int j = 0;; ++j) {
     if (ld_relaxed_i32(&pa.pc->running) == 0) break;
     run_phase<PH_P1>(pa, sm, true);
-    if (!bar.sync(&sm.ok)) return;
+    if (!grid_sync(pa, &sm.bar_target, &sm.bar_index, &sm.ok)) return;
     run_phase<PH_P2>(pa, sm, true);
-    if (!bar.sync(&sm.ok)) return;
+    if (!grid_sync(pa, &sm.bar_target, &sm.bar_index, &sm.ok)) return;
     run_phase<PH_P3>(pa, sm, true);
-    if (!bar.sync(&sm.ok)) return;
+    if (!grid_sync(pa, &sm.bar_target, &sm.bar_index, &sm.ok)) return;
     run_phase<PH_P4>(pa, sm, true);
-    if (!bar.sync(&sm.ok)) return;
+    if (!grid_sync(pa, &sm.bar_target, &sm.bar_index, &sm.ok)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) pa.pc->iters = j + 1;
     if (ld_relaxed_i32(&pa.pc->running) == 0) break;
     run_phase<PH_P5>(pa, sm, true);
-    if (!bar.sync(&sm.ok)) return;
+    if (!grid_sync(pa, &sm.bar_target, &sm.bar_index, &sm.ok)) return;
   }
   run_phase<PH_FINAL>(pa, sm, false);
 }
 
 }  // namespace
+
+cudaError_t add_persist_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const PersistArgs &pa,
+                             int grid, cudaGraphNode_t *node) {
+  const size_t smem = sizeof(Smem);
+  cudaError_t e = cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  PersistArgs arg = pa;
+  void *params[1] = {&arg};
+  cudaKernelNodeParams kp = {};
+  kp.func = reinterpret_cast<void *>(persist_kernel);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(kPT);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = params;
+  kp.extra = nullptr;
+  if ((e = cudaGraphAddKernelNode(node, g, deps, ndeps, &kp)) != cudaSuccess) return e;
+  cudaLaunchAttributeValue v = {};
+  v.cooperative = 1;
+  return cudaGraphKernelNodeSetAttribute(*node, cudaLaunchAttributeCooperative, &v);
+}
 
 int persist_blocks_per_sm() {
   int nb = 0;

@@ -67,5 +67,8 @@ inline int persist_rows_per_pass(int kp) { return kPersistThreads / (kp >= 4 ? k
 int persist_blocks_per_sm();
 // Cooperative launch of `grid` blocks (grid must not exceed the co-resident count).
 cudaError_t launch_persist(const PersistArgs &pa, int grid, cudaStream_t s);
+// The same launch as a cooperative kernel node of graph g after `deps`.
+cudaError_t add_persist_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const PersistArgs &pa,
+                             int grid, cudaGraphNode_t *node);
 
 }  // namespace bicgk

@@ -89,8 +89,10 @@ class CSR:
         return d
 
     def to_scipy(self):
+        """scipy CSR of copies of the arrays: scipy may sort or merge the entries of its own arrays in
+        place (repeated column indices), which must not change this matrix."""
         import scipy.sparse as sp
-        return sp.csr_matrix((self.vals, self.colidx, self.rowptr), shape=(self.n, self.n))
+        return sp.csr_matrix((self.vals.copy(), self.colidx.copy(), self.rowptr.copy()), shape=(self.n, self.n))
 
 
 def _assemble(n_rows: int, cols: list, vals: list, valid: list, name: str) -> CSR:
