@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--profile-batch", action="store_true",
                    help="only the batched workload in the persistent mode, 10 fixed iterations, twice "
                         "(profiler captures of the persistent kernel)")
+    p.add_argument("--no-small-k", action="store_true",
+                   help="skip the small-problem comparison of the graph path and the persistent kernel")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batching comparison (64 systems, grids 16^3..64^3, 1..8 RHS)")
     p.add_argument("--eager", action="store_true",
@@ -435,7 +437,6 @@ def batch_section(args, bicgk, inputs, torch, dev, nsys=64):
         torch.cuda.synchronize()
         res["tune_persistent_s"] = time.perf_counter() - t0
         res["persistent_rows_per_tile"] = sorted({int(r) for r in rows})
-        res["persistent_launch"] = bt.persistent_info()
         out = {}
         for name, mode in (("persistent", bicgk.BATCH_PERSISTENT), ("graph", bicgk.BATCH_GRAPH),
                            ("loop", bicgk.BATCH_LOOP)):
@@ -454,6 +455,7 @@ def batch_section(args, bicgk, inputs, torch, dev, nsys=64):
                          "max_true_relres": float(trr.max())}
             if mode == bicgk.BATCH_PERSISTENT:
                 out[name]["loop_iterations"] = bt.last_loop_iters()
+                out[name]["launch"] = bt.persistent_info()
             got[name] = {i: Xs[i].cpu().numpy() for i in sample}
         res.update(out)
         res["graph_speedup_vs_loop"] = out["loop"]["ms"] / out["graph"]["ms"]
@@ -558,6 +560,69 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
             jobs = [(0, dict(tol=0.0, maxit=nit, variant=v, flags=oracle.NO_STOP_TEST)) for v in col0]
             for v, ro in zip(col0, oracle_columns(A, Bh, jobs)):
                 res["rows"][f"{v}/k{k}"]["oracle_err"] = float(colerr(col0[v], ro.X)[0])
+    return res
+
+
+def small_k_section(args, bicgk, inputs, torch, dev, A128):
+    """Small problems, where a kernel's data phase lasts a few microseconds and launch, ramp and
+    reduction tails set the pace: the graph path against the persistent kernel (bicgk_solve with
+    BICGK_OPT_PERSISTENT = 2, one cooperative launch per solve).
+      * the 16^3 configuration (4,096 rows, k = 4, h-scaled convection-diffusion, rel. tol 1e-8):
+        time per solve (CUDA events, mean of 20), against the oracle's solve;
+      * the 128^3 benchmark operator at k = 1, 2, 4: time per iteration over 40 fixed iterations,
+        x after 12 fixed iterations against the oracle's."""
+    import oracle
+    res = {}
+    A16 = inputs.convdiff7(16)
+    B16h = inputs.rhs(A16.n, 4, 1)
+    B16 = torch.from_numpy(B16h).to(dev)
+    X16 = torch.empty_like(B16)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ro = oracle.solve(A16, B16h, tol=1e-8, maxit=1000)
+    row = {"workload": "convdiff7 16^3 (4,096 rows), k=4, rel tol 1e-8, classical_merged"}
+    with bicgk.Operator(A16) as op:
+        for name, opt in (("graph", 0), ("persistent", 2)):
+            bicgk.set_option(op.handle, bicgk.OPT_PERSISTENT, opt)
+            r = op.solve(B16, X=X16, tol=1e-8, maxit=1000, want_hist=False)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(20):
+                r = op.solve(B16, X=X16, tol=1e-8, maxit=1000, want_hist=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 20
+            row[name] = {"ms_per_solve": ms, "rhs_iterations_per_s": float(r.iters.sum()) / (ms / 1e3),
+                         "iters": r.iters.tolist(), "kernel_launches": bicgk.last_stats(op.handle)["kernel_launches"],
+                         "oracle_err": float(colerr(X16.cpu().numpy(), ro.X).max()),
+                         "max_true_relres": float(r.true_relres.max())}
+    row["oracle_iters"] = ro.iters.tolist()
+    row["persistent_speedup"] = row["graph"]["ms_per_solve"] / row["persistent"]["ms_per_solve"]
+    res["config_16cubed_k4"] = row
+    nit = 40
+    rows128 = {}
+    with bicgk.Operator(A128) as op:
+        for k in (1, 2, 4):
+            Bh = inputs.rhs(A128.n, k, 2)
+            Bk = torch.from_numpy(Bh).to(dev)
+            Xk = torch.empty_like(Bk)
+            ro12 = oracle_columns(A128, Bh, [(0, dict(tol=0.0, maxit=12, flags=oracle.NO_STOP_TEST))])[0]
+            row = {}
+            for name, opt in (("graph", 0), ("persistent", 2)):
+                bicgk.set_option(op.handle, bicgk.OPT_PERSISTENT, opt)
+                op.solve(Bk, X=Xk, tol=0.0, maxit=3, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
+                torch.cuda.synchronize()
+                e0.record()
+                op.solve(Bk, X=Xk, tol=0.0, maxit=nit, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False, want_true=False)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / nit
+                op.solve(Bk, X=Xk, tol=0.0, maxit=12, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
+                row[name] = {"us_per_iter": ms * 1e3, "rhs_iterations_per_s": k / (ms / 1e3),
+                             "oracle_err_12_iterations": float(colerr(Xk[:, :1].cpu().numpy(), ro12.X)[0])}
+            row["persistent_speedup"] = row["graph"]["us_per_iter"] / row["persistent"]["us_per_iter"]
+            rows128[f"k{k}"] = row
+    res["benchmark_operator_128cubed"] = {"workload": f"{A128.name}, {nit} fixed iterations, classical_merged",
+                                          "rows": rows128}
     return res
 
 
@@ -884,6 +949,10 @@ def main():
 
     if args.sweep and rank == 0:
         out["sweep"] = sweep_section(args, bicgk, inputs, torch, dev, A, hbm_peak()[0])
+
+    # small problems: the graph path against the persistent kernel
+    if not args.no_small_k and rank == 0:
+        out["small_k"] = small_k_section(args, bicgk, inputs, torch, dev, A)
 
     # the paper's own iteration benchmark (Poisson 200^3, every form, m = 1, 4, 16)
     if args.replica and rank == 0:

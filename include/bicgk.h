@@ -292,12 +292,19 @@ enum bicgk_option {
                                       in place through their mapped device addresses, group by
                                       group, overlapping the transfer with the solve; 1: copy
                                       through a device staging block as for pageable memory.   */
-  BICGK_OPT_COMPACT = 7             /* every form.  0 (default): when at most half of a
+  BICGK_OPT_COMPACT = 7,            /* every form.  0 (default): when at most half of a
                                       column group's columns are still iterating, the group
                                       continues in a layout of half the width (down to one
                                       column), so stopped columns stop costing arithmetic;
                                       1: never.  The iterates are those of the full layout up
                                       to summation order.                                      */
+  BICGK_OPT_PERSISTENT = 8          /* merged classical BiCGStab (Algorithm 2) without
+                                      preconditioner on device blocks: 2 runs the solve as ONE
+                                      cooperative launch of the persistent batch kernel (a
+                                      one-system batch over this operator, kept for the next
+                                      solve of the same k; see BICGK_BATCH_PERSISTENT), with its
+                                      scalar rules and a residual history; 0 (default) and 1:
+                                      the graph path.  Not in profiling mode.                 */
 };
 
 /*
@@ -334,20 +341,22 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value);
  *   results are bitwise equal.  Residual histories are not returned.
  *   mode BICGK_BATCH_PERSISTENT: the whole batch -- pack, set-up, every iteration of every
  *   system, true residual, unpack -- in ONE cooperative kernel launch (replayed from a CUDA
- *   graph), merged classical BiCGStab (Algorithm 2) only, M = identity (other variants and
- *   BICGK_FLAG_JACOBI: BICGK_E_UNSUPPORTED).  A grid sized to be co-resident walks all systems'
- *   row tiles phase by phase (Algorithm 2's merged groups), with a grid-wide barrier between
+ *   graph), merged classical BiCGStab (Algorithm 2) only, M = identity, at most 1024 systems
+ *   (other variants, BICGK_FLAG_JACOBI, more systems: BICGK_E_UNSUPPORTED).  A grid sized to be
+ *   co-resident walks the row tiles of the systems still iterating phase by phase (Algorithm
+ *   2's merged groups), each block a contiguous share of them, with a grid-wide barrier between
  *   phases; a system stops costing work once all its columns stopped.  Same scalar rules as the
  *   other modes; dot products are summed per row tile, so results differ from theirs by
  *   summation order only (and are bitwise reproducible run to run).  Every barrier wait is
  *   bounded by the batch's deadline (bicgk_batch_set_deadline; default 1 s): past it the kernel
  *   returns, the call returns BICGK_E_TIMEOUT, bicgk_last_cuda_error() names the barrier and
  *   the block, and the next solve starts from a clean state.
- * bicgk_batch_tune_persistent: autotuner of the persistent mode's rows per CTA tile (1, 2, 4 or
- *   8 passes of 256 threads: 256..2048 rows at kp <= 2, 64..512 at kp = 8): times `reps`
- *   persistent solves of 4 fixed iterations with right-hand sides of ones for each and keeps
- *   the fastest (allocates two temporary blocks).  Writes each system's rows per tile to the
- *   nullable array [nsys].
+ * bicgk_batch_tune_persistent: autotuner of the persistent mode: rows per CTA tile (1, 2, 4 or
+ *   8 passes of 256 threads: 256..2048 rows at kp <= 2, 64..512 at kp = 8) x blocks per SM (the
+ *   kernel compiled for 4 blocks of up to 64 registers a thread, or 6 of up to 40); times `reps`
+ *   persistent solves of 4 fixed iterations with right-hand sides of ones for each of the 8
+ *   shapes and keeps the fastest (allocates two temporary blocks).  Writes each system's rows
+ *   per tile to the nullable array [nsys]; bicgk_batch_persistent_info gives the grid.
  * bicgk_batch_set_deadline: longest wait of one grid barrier of the persistent kernel, in
  *   microseconds (0..3.6e9; 0 makes every wait that does not find all blocks arrived fail).
  * bicgk_batch_last_launches: kernels the last bicgk_batch_solve launched (persistent: 1).

@@ -273,6 +273,9 @@ struct bicgk_op_s {
   int opt_theta = 0;  // BICGK_OPT_THETA_IN_S
   int opt_zero_copy = 0;  // BICGK_OPT_HOST_ZERO_COPY
   int opt_compact = 0;    // BICGK_OPT_COMPACT
+  int opt_persistent = 0; // BICGK_OPT_PERSISTENT
+  bicgk_batch pbatch = nullptr;  // one-system batch over this operator for the persistent kernel
+  int pbatch_k = 0;
   // launch shapes chosen by the batch autotuner (0 = the per-SM rule above)
   int grid_vec_abs = 0;
   int grid_spmm_abs = 0;
@@ -844,6 +847,17 @@ int seq_opts(bicgk_op A, int k, int variant) {
   return (fuse_dots(A, k) ? SEQ_FUSE : 0) | (theta_in_s(A, k, variant) ? SEQ_THETA_S : 0);
 }
 
+// Whether bicgk_solve runs this solve in the persistent kernel (BICGK_OPT_PERSISTENT): merged
+// classical BiCGStab without preconditioner, device blocks, not in profiling mode; automatic: never
+// (see the option's description).
+bool use_persistent(bicgk_op A, int k, int variant, bool jacobi, int mem) {
+  if (A->opt_persistent == 1 || A->profiling || variant != BICGK_CLASSICAL_MERGED || jacobi ||
+      mem != BICGK_MEM_DEVICE)
+    return false;
+  (void)k;
+  return A->opt_persistent == 2;
+}
+
 int build_graph(bicgk_op A, Workspace &W, int variant, bool jacobi, int opts, GraphEntry *ge) {
   return build_graph_seq(A, W, make_seq(variant, jacobi, opts), nullptr, ge, jacobi ? A->d_invdiag : nullptr);
 }
@@ -950,6 +964,11 @@ int run_profiled(bicgk_op A, Workspace &W, int variant, bool jacobi, int opts, c
 
 }  // namespace
 
+// Defined with the batches below.
+int persist_single(bicgk_op A, int32_t k, const double *B, const double *X0, double rel_tol, int32_t maxit,
+                   int32_t flags, double *X, int32_t *iters, int32_t *status, double *resid_hist,
+                   double *true_relres, cudaStream_t s);
+
 extern "C" {
 
 const char *bicgk_version(void) { return "bicgk 0.2 sm_103a"; }
@@ -1022,6 +1041,7 @@ int bicgk_csr_create(bicgk_op *out, int64_t n_rows, int64_t nnz, const int32_t *
 int bicgk_op_destroy(bicgk_op A) {
   if (!A) return BICGK_OK;
   cudaDeviceSynchronize();
+  if (A->pbatch) bicgk_batch_destroy(A->pbatch);  // borrows A: leaves it alone
   if (A->trans) bicgk_op_destroy(A->trans);
   cudaFree(A->d_invdiag);
   for (Workspace &W : A->ws) free_workspace(W);
@@ -1125,6 +1145,8 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
   if (k > BICGK_MAX_K) return BICGK_E_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   const bool jacobi = (flags & BICGK_FLAG_JACOBI) != 0;
+  if (use_persistent(A, k, variant, jacobi, mem))
+    return persist_single(A, k, B, X0, rel_tol, maxit, flags, X, iters, status, resid_hist, true_relres, s);
   const int opts = seq_opts(A, k, variant);
   const int gkey = variant + 100 * (jacobi ? 1 : 0) + 1000 * opts;
   int rc0 = ensure_variant_data(A, variant, jacobi, s);
@@ -1580,6 +1602,10 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value) {
       if (value < 0 || value > 1) return BICGK_E_INVALID;
       A->opt_compact = (int)value;
       break;
+    case BICGK_OPT_PERSISTENT:
+      if (value < 0 || value > 2) return BICGK_E_INVALID;
+      A->opt_persistent = (int)value;
+      break;
     default:
       return BICGK_E_INVALID;
   }
@@ -1640,6 +1666,7 @@ int bicgk_last_groups(bicgk_op A, int32_t *groups) {
 // no edges between them, so the GPU overlaps the systems' kernels.
 struct bicgk_batch_s {
   int nsys = 0;
+  bool borrowed = false;      // the operators belong to the caller (a one-system batch of bicgk_solve)
   std::vector<bicgk_op> ops;
   std::vector<int> k;
   std::vector<Workspace> ws;  // batch workspaces (shared state)
@@ -1659,7 +1686,8 @@ struct bicgk_batch_s {
   size_t ppart_cap = 0;       // doubles
   int64_t p_ntiles = 0;
   int p_grid = 0;
-  int p_sub = 1;              // 256-thread passes per tile (rows per CTA tile; bicgk_batch_tune)
+  int p_sub = 1;              // 256-thread passes per tile (rows per CTA tile; bicgk_batch_tune_persistent)
+  int p_minb = 4;             // blocks per SM of the kernel variant (4 or 6; bicgk_batch_tune_persistent)
   int64_t deadline_us = 1000000;  // longest wait at one grid barrier
   GraphEntry pgraph;          // clear the control block, the cooperative kernel
   bool pgraph_ok = false;
@@ -1822,9 +1850,9 @@ int persist_prepare(bicgk_batch b) {
   if (tiles != b->p_ntiles) persist_drop_graph(b);
   b->p_ntiles = tiles;
   if (!b->p_grid) {
-    const int nb = persist_blocks_per_sm();
+    const int nb = persist_blocks_per_sm(b->p_minb);
     if (nb < 1) return cuda_fail(cudaGetLastError(), "persistent kernel occupancy");
-    b->p_grid = b->ops[0]->nsm * (nb < kPersistMaxBlocksPerSm ? nb : kPersistMaxBlocksPerSm);
+    b->p_grid = b->ops[0]->nsm * (nb < b->p_minb ? nb : b->p_minb);
   }
   return BICGK_OK;
 }
@@ -1862,7 +1890,7 @@ int persist_launch(bicgk_batch b, cudaStream_t s) {
       mp.pitch = clr[i].bytes;
       e = cudaGraphAddMemsetNode(&m[i], g, nullptr, 0, &mp);
     }
-    if (e == cudaSuccess) e = add_persist_node(g, m, 3, pa, b->p_grid, &kn);
+    if (e == cudaSuccess) e = add_persist_node(g, m, 3, pa, b->p_grid, b->p_minb, &kn);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
     if (e != cudaSuccess) {
       // a runtime that cannot put a cooperative launch in a graph: launch it directly from now on
@@ -1880,7 +1908,7 @@ int persist_launch(bicgk_batch b, cudaStream_t s) {
     CK(cudaMemsetAsync(b->d_pc, 0, sizeof(PersistCtl), s));
     CK(cudaMemsetAsync(b->d_tickets, 0, sizeof(unsigned) * b->nsys, s));
     CK(cudaMemsetAsync(b->d_live, 0, sizeof(int) * b->nsys, s));
-    CK(launch_persist(pa, b->p_grid, s));
+    CK(launch_persist(pa, b->p_grid, b->p_minb, s));
     return BICGK_OK;
   }
   CK(cudaGraphLaunch(b->pgraph.exec, s));
@@ -1901,6 +1929,84 @@ int time_launches(F launch, int reps, cudaStream_t s, cudaEvent_t e0, cudaEvent_
 }
 
 }  // namespace
+
+namespace {
+
+// Control blocks, flags, scalars and caller-pointer table of a batch, and the workspaces' views
+// of them.
+int batch_alloc_state(bicgk_batch b) {
+  const int nsys = b->nsys;
+  cudaError_t e = cudaSuccess;
+  {
+    if ((e = cudaMalloc(&b->d_ctl, sizeof(Ctl) * nsys)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_fl, sizeof(int) * F_NFLAG * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_sc, sizeof(double) * S_NSLOT * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_io, sizeof(BatchIO) * nsys)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_ctl, sizeof(Ctl) * nsys)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_fl, sizeof(int) * F_NFLAG * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_sc, sizeof(double) * S_NSLOT * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_io, sizeof(BatchIO) * nsys)) != cudaSuccess ||
+        (e = cudaMemset(b->d_ctl, 0, sizeof(Ctl) * nsys)) != cudaSuccess ||
+        (e = cudaMemset(b->d_fl, 0, sizeof(int) * F_NFLAG * kMaxKp * nsys)) != cudaSuccess ||
+        (e = cudaMemset(b->d_sc, 0, sizeof(double) * S_NSLOT * kMaxKp * nsys)) != cudaSuccess)
+      return cuda_fail(e, "batch state");
+  }
+  for (int i = 0; i < nsys; ++i) {
+    Workspace &W = b->ws[i];
+    W.shared_state = true;
+    W.d_ctl = b->d_ctl + i;
+    W.d_fl = b->d_fl + (size_t)i * F_NFLAG * kMaxKp;
+    W.d_sc = b->d_sc + (size_t)i * S_NSLOT * kMaxKp;
+  }
+  return BICGK_OK;
+}
+
+}  // namespace
+
+// One solve of the operator's own system by the persistent kernel (bicgk_solve with
+// BICGK_OPT_PERSISTENT): a one-system batch that borrows the operator, kept for the next solve of
+// the same width.  Device blocks only.
+int persist_single(bicgk_op A, int32_t k, const double *B, const double *X0, double rel_tol, int32_t maxit,
+                   int32_t flags, double *X, int32_t *iters, int32_t *status, double *resid_hist,
+                   double *true_relres, cudaStream_t s) {
+  if (A->pbatch && A->pbatch_k != k) {
+    bicgk_batch_destroy(A->pbatch);
+    A->pbatch = nullptr;
+  }
+  if (!A->pbatch) {
+    bicgk_batch b = new bicgk_batch_s();
+    b->nsys = 1;
+    b->borrowed = true;
+    b->k.assign(1, k);
+    b->ops.assign(1, A);
+    b->ws.resize(1);
+    int rc = batch_alloc_state(b);
+    if (rc) {
+      bicgk_batch_destroy(b);
+      return rc;
+    }
+    A->pbatch = b;
+    A->pbatch_k = k;
+  }
+  bicgk_batch b = A->pbatch;
+  const double *Bv[1] = {B};
+  const double *X0v[1] = {X0};
+  double *Xv[1] = {X};
+  int rc = bicgk_batch_solve(b, Bv, X0 ? X0v : nullptr, Xv, rel_tol, maxit, BICGK_CLASSICAL_MERGED, flags,
+                             BICGK_BATCH_PERSISTENT, iters, status, true_relres, s);
+  if (rc) return rc;
+  if (resid_hist) {
+    const Workspace &W = b->ws[0];
+    CK(cudaMemcpy2DAsync(resid_hist, sizeof(double) * k, W.d_hist, sizeof(double) * W.kp, sizeof(double) * k,
+                         (size_t)maxit + 1, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  A->last_loop_iters = (int32_t)b->p_loop_iters;
+  A->last_launches = 1;
+  A->last_kernels_per_iter = 0;
+  A->last_groups = 1;
+  return BICGK_OK;
+}
 
 extern "C" {
 
@@ -1927,35 +2033,15 @@ int bicgk_batch_create(bicgk_batch *out, int32_t nsys, const int64_t *n_rows, co
     b->ops[i]->opt_fused = 1;
     b->ops[i]->opt_compact = 1;
   }
-  cudaError_t e = cudaSuccess;
-  if (rc == BICGK_OK) {
-    if ((e = cudaMalloc(&b->d_ctl, sizeof(Ctl) * nsys)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_fl, sizeof(int) * F_NFLAG * kMaxKp * nsys)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_sc, sizeof(double) * S_NSLOT * kMaxKp * nsys)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_io, sizeof(BatchIO) * nsys)) != cudaSuccess ||
-        (e = cudaMallocHost(&b->h_ctl, sizeof(Ctl) * nsys)) != cudaSuccess ||
-        (e = cudaMallocHost(&b->h_fl, sizeof(int) * F_NFLAG * kMaxKp * nsys)) != cudaSuccess ||
-        (e = cudaMallocHost(&b->h_sc, sizeof(double) * S_NSLOT * kMaxKp * nsys)) != cudaSuccess ||
-        (e = cudaMallocHost(&b->h_io, sizeof(BatchIO) * nsys)) != cudaSuccess ||
-        (e = cudaMemset(b->d_ctl, 0, sizeof(Ctl) * nsys)) != cudaSuccess ||
-        (e = cudaMemset(b->d_fl, 0, sizeof(int) * F_NFLAG * kMaxKp * nsys)) != cudaSuccess ||
-        (e = cudaMemset(b->d_sc, 0, sizeof(double) * S_NSLOT * kMaxKp * nsys)) != cudaSuccess)
-      rc = cuda_fail(e, "bicgk_batch_create");
-  }
+  if (rc == BICGK_OK) rc = batch_alloc_state(b);
   if (rc != BICGK_OK) {
     bicgk_batch_destroy(b);
     return rc;
   }
-  for (int i = 0; i < nsys; ++i) {
-    Workspace &W = b->ws[i];
-    W.shared_state = true;
-    W.d_ctl = b->d_ctl + i;
-    W.d_fl = b->d_fl + (size_t)i * F_NFLAG * kMaxKp;
-    W.d_sc = b->d_sc + (size_t)i * S_NSLOT * kMaxKp;
-  }
   *out = b;
   return BICGK_OK;
 }
+
 
 int bicgk_batch_destroy(bicgk_batch b) {
   if (!b) return BICGK_OK;
@@ -1974,7 +2060,8 @@ int bicgk_batch_destroy(bicgk_batch b) {
     cudaFree(W.d_part);
     cudaFree(W.d_hist);
   }
-  for (bicgk_op A : b->ops) bicgk_op_destroy(A);
+  if (!b->borrowed)
+    for (bicgk_op A : b->ops) bicgk_op_destroy(A);
   cudaFree(b->d_ctl);
   cudaFree(b->d_fl);
   cudaFree(b->d_sc);
@@ -2075,8 +2162,9 @@ int bicgk_batch_solve(bicgk_batch b, const double *const *B, const double *const
       (mode != BICGK_BATCH_GRAPH && mode != BICGK_BATCH_LOOP && mode != BICGK_BATCH_PERSISTENT))
     return BICGK_E_INVALID;
   const bool jacobi = (flags & BICGK_FLAG_JACOBI) != 0;
-  if (mode == BICGK_BATCH_PERSISTENT && (variant != BICGK_CLASSICAL_MERGED || jacobi)) {
-    g_cuda_err = "persistent batch mode runs merged classical BiCGStab (Algorithm 2) without preconditioner";
+  if (mode == BICGK_BATCH_PERSISTENT && (variant != BICGK_CLASSICAL_MERGED || jacobi || b->nsys > kPersistMaxSys)) {
+    g_cuda_err = "persistent batch mode runs merged classical BiCGStab (Algorithm 2) without preconditioner, "
+                 "for at most " + std::to_string(kPersistMaxSys) + " systems";
     return BICGK_E_UNSUPPORTED;
   }
   const int gkey = variant + 100 * (jacobi ? 1 : 0);
@@ -2215,10 +2303,17 @@ int bicgk_batch_tune_persistent(bicgk_batch b, int32_t reps, int32_t *rows_per_t
   if ((e = cudaMemcpy(d_one, ones.data(), sizeof(double) * most, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
     rc = cuda_fail(e, "bicgk_batch_tune_persistent");
-  // rows per CTA tile: 1, 2, 4, 8 passes of 256 threads; 4 fixed iterations of every system
-  int best_sub = b->p_sub;
+  // blocks per SM (the kernel variant for 4 or 6) x rows per CTA tile (1, 2, 4, 8 passes of 256
+  // threads); 4 fixed iterations of every system
+  int best_sub = b->p_sub, best_minb = b->p_minb;
   float best = 1e30f;
-  for (int sub = 1; sub <= 8 && rc == BICGK_OK; sub *= 2) {
+  for (int cfg = 0; cfg < 8 && rc == BICGK_OK; ++cfg) {
+    const int sub = 1 << (cfg & 3), minb = cfg < 4 ? 4 : 6;
+    if (minb != b->p_minb) {
+      b->p_minb = minb;
+      b->p_grid = 0;  // re-derived from the variant's occupancy
+      persist_drop_graph(b);
+    }
     b->p_sub = sub;
     float total = 0.f;
     for (int r = 0; r <= reps && rc == BICGK_OK; ++r) {
@@ -2234,9 +2329,12 @@ int bicgk_batch_tune_persistent(bicgk_batch b, int32_t reps, int32_t *rows_per_t
     if (rc == BICGK_OK && total < best * 0.98f) {
       best = total;
       best_sub = sub;
+      best_minb = minb;
     }
   }
   b->p_sub = best_sub;
+  if (b->p_minb != best_minb) b->p_grid = 0;
+  b->p_minb = best_minb;
   persist_drop_graph(b);
   if (rc == BICGK_OK) rc = persist_prepare(b);
   if (rc == BICGK_OK && rows_per_tile_out)

@@ -147,17 +147,26 @@ __device__ __forceinline__ double2 sc2(const PersistSys &S, int slot, int q) {
   }
 }
 
-// Shared memory of a block.
+// Shared memory of a block.  The dot-product scratch and the CSR staging buffer share storage:
+// a block stages entries only inside a tile's row passes and reduces only between tiles.
 struct Smem {
-  double red[kPT / 32][3][kMaxKp];  // per-warp dot sums of a tile
-  double tmp[kPT];                  // system reduction: per-thread sums
-  double res[3 * kMaxKp];           // system reduction: the dots, [d * kp + c]
+  union {
+    struct {
+      double red[kPT / 32][3][kMaxKp];  // per-warp dot sums of the block's tiles of a system
+      double tmp[kPT];                  // system reduction: per-thread sums
+      double res[3 * kMaxKp];           // system reduction: the dots, [d * kp + c]
+    } r;
+    struct {
+      double sval[kPersistStage];       // staged CSR entries of a 256-row pass (kp <= 2)
+      int32_t scol[kPersistStage];
+    } st;
+  } u;
   unsigned long long bar_target;  // grid barrier: arrivals that complete the next barrier
   int bar_index;                  // grid barrier: barriers passed
   int ok;
   int last;
-  double sval[kPersistStage];       // staged CSR entries of a tile (kp <= 2)
-  int32_t scol[kPersistStage];
+  int pref[kPersistMaxSys + 1];   // tiles of the systems a phase runs, exclusive prefix
+  int scan_warp[kPT / 32];
 };
 
 // y = A x (or b - A x) for the lane's row i and column pair q.  KP <= 2 may read the tile's
@@ -170,8 +179,8 @@ __device__ __forceinline__ double2 row_product(const PersistSys &S, const double
   if constexpr (KP <= 2) {
     if (staged) {
       for (int e = e0; e < e1; ++e) {
-        const double av = sm.sval[e - te0];
-        const double2 u = vld<KP>(x, sm.scol[e - te0], 0);
+        const double av = sm.u.st.sval[e - te0];
+        const double2 u = vld<KP>(x, sm.u.st.scol[e - te0], 0);
         acc.x = fma(av, u.x, acc.x);
         acc.y = fma(av, u.y, acc.y);
       }
@@ -203,6 +212,7 @@ template <int KP, int ND>
 __device__ void tile_partials(const PersistSys &S, int tl, double2 (&acc)[3], Smem &sm) {
   constexpr int L = Geo<KP>::L;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // the reduction scratch shares storage with the staged CSR entries of the last pass
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
 #pragma unroll
@@ -212,10 +222,10 @@ __device__ void tile_partials(const PersistSys &S, int tl, double2 (&acc)[3], Sm
     }
     if (lane < L) {
       if constexpr (KP == 1) {
-        sm.red[w][d][0] = acc[d].x;
+        sm.u.r.red[w][d][0] = acc[d].x;
       } else {
-        sm.red[w][d][2 * lane] = acc[d].x;
-        sm.red[w][d][2 * lane + 1] = acc[d].y;
+        sm.u.r.red[w][d][2 * lane] = acc[d].x;
+        sm.u.r.red[w][d][2 * lane + 1] = acc[d].y;
       }
     }
   }
@@ -224,7 +234,7 @@ __device__ void tile_partials(const PersistSys &S, int tl, double2 (&acc)[3], Sm
     const int d = threadIdx.x / KP, c = threadIdx.x % KP;
     double s = 0.0;
 #pragma unroll
-    for (int ww = 0; ww < kPT / 32; ++ww) s += sm.red[ww][d][c];
+    for (int ww = 0; ww < kPT / 32; ++ww) s += sm.u.r.red[ww][d][c];
     S.part[((int64_t)tl * 3 + d) * KP + c] = s;
     __threadfence();
   }
@@ -253,13 +263,13 @@ __device__ void sys_sum(const PersistSys &S, int parts, Smem &sm) {
     const int d = p / KP, c = p % KP;
     double s = 0.0;
     for (int tl = u; tl < parts; tl += T) s += __ldcg(S.part + ((int64_t)tl * 3 + d) * KP + c);
-    sm.tmp[t] = s;
+    sm.u.r.tmp[t] = s;
   }
   __syncthreads();
   if (t < P) {
     double s = 0.0;
-    for (int u = 0; u < T; ++u) s += sm.tmp[t * T + u];
-    sm.res[t] = s;  // t = d * KP + c
+    for (int u = 0; u < T; ++u) s += sm.u.r.tmp[t * T + u];
+    sm.u.r.res[t] = s;  // t = d * KP + c
   }
   __syncthreads();
 }
@@ -324,6 +334,56 @@ __device__ __noinline__ void run_tile(const PersistSys &S, int tl, Smem &sm, dou
   double *const *V = S.vec;
   const double2 al = ls.al, om = ls.om, be = ls.be;
   const bool u0 = ls.u0, u1 = ls.u1;
+  if constexpr (PH == PH_P2 || PH == PH_P4 || PH == PH_P5) {
+    // streaming phases; s and p updates keep two rows per thread in flight (both rows' loads before
+    // either's store), the five-vector x/r update one row
+    if constexpr (PH == PH_P2) {  // s = r - alpha v
+      for (int64_t p0 = r0; p0 < r1; p0 += 2 * RPP) {
+        const int64_t i0 = p0 + rr, i1 = p0 + RPP + rr;
+        double2 ra = make_double2(0.0, 0.0), va = ra, rb = ra, vb = ra;
+        if (i0 < r1) {
+          ra = vld<KP>(V[P_R], i0, q);
+          va = vld<KP>(V[P_V], i0, q);
+        }
+        if (i1 < r1) {
+          rb = vld<KP>(V[P_R], i1, q);
+          vb = vld<KP>(V[P_V], i1, q);
+        }
+        if (i0 < r1) vst<KP>(V[P_S], i0, q, fma2(neg2(al), va, ra));
+        if (i1 < r1) vst<KP>(V[P_S], i1, q, fma2(neg2(al), vb, rb));
+      }
+    } else if constexpr (PH == PH_P5) {  // p = r + beta (p - omega v)
+      for (int64_t p0 = r0; p0 < r1; p0 += 2 * RPP) {
+        const int64_t i0 = p0 + rr, i1 = p0 + RPP + rr;
+        double2 ra = make_double2(0.0, 0.0), pa_ = ra, va = ra, rb = ra, pb = ra, vb = ra;
+        if (i0 < r1) {
+          ra = vld<KP>(V[P_R], i0, q);
+          pa_ = vld<KP>(V[P_P], i0, q);
+          va = vld<KP>(V[P_V], i0, q);
+        }
+        if (i1 < r1) {
+          rb = vld<KP>(V[P_R], i1, q);
+          pb = vld<KP>(V[P_P], i1, q);
+          vb = vld<KP>(V[P_V], i1, q);
+        }
+        if (i0 < r1) vst<KP>(V[P_P], i0, q, fma2(be, fma2(neg2(om), va, pa_), ra));
+        if (i1 < r1) vst<KP>(V[P_P], i1, q, fma2(be, fma2(neg2(om), vb, pb), rb));
+      }
+    } else {  // x += alpha p + omega s (columns that formed x_{j+1}); r = s - omega t; rho = (r, r0)
+      for (int64_t i = r0 + rr; i < r1; i += RPP) {
+        const double2 x = vld<KP>(V[P_X], i, q), p = vld<KP>(V[P_P], i, q), sv = vld<KP>(V[P_S], i, q);
+        const double2 t = vld<KP>(V[P_T], i, q);
+        if (u0 | u1) {
+          const double2 xn = fma2(om, sv, fma2(al, p, x));
+          vst<KP>(V[P_X], i, q, make_double2(u0 ? xn.x : x.x, u1 ? xn.y : x.y));
+        }
+        const double2 r = fma2(neg2(om), t, sv);
+        vst<KP>(V[P_R], i, q, r);
+        dacc(acc[0], r, vld<KP>(V[P_R0], i, q));
+      }
+    }
+    return;
+  }
   for (int64_t p0 = r0; p0 < r1; p0 += RPP) {
     const int64_t pe = p0 + RPP < r1 ? p0 + RPP : r1;
     int te0 = 0;
@@ -336,8 +396,8 @@ __device__ __noinline__ void run_tile(const PersistSys &S, int tl, Smem &sm, dou
       __syncthreads();
       if (staged)
         for (int e = te0 + threadIdx.x; e < te1; e += kPT) {
-          sm.sval[e - te0] = __ldg(S.vals + e);
-          sm.scol[e - te0] = __ldg(S.colidx + e);
+          sm.u.st.sval[e - te0] = __ldg(S.vals + e);
+          sm.u.st.scol[e - te0] = __ldg(S.colidx + e);
         }
       __syncthreads();
     }
@@ -371,8 +431,6 @@ __device__ __noinline__ void run_tile(const PersistSys &S, int tl, Smem &sm, dou
         const double2 v = row_product<KP>(S, V[P_P], i, q, sm, te0, staged);
         vst<KP>(V[P_V], i, q, v);
         dacc(acc[0], v, vld<KP>(V[P_R0], i, q));
-      } else if constexpr (PH == PH_P2) {
-        vst<KP>(V[P_S], i, q, fma2(neg2(al), vld<KP>(V[P_V], i, q), vld<KP>(V[P_R], i, q)));
       } else if constexpr (PH == PH_P3) {
         const double2 t = row_product<KP>(S, V[P_S], i, q, sm, te0, staged);
         vst<KP>(V[P_T], i, q, t);
@@ -380,19 +438,6 @@ __device__ __noinline__ void run_tile(const PersistSys &S, int tl, Smem &sm, dou
         dacc(acc[0], t, s);
         dacc(acc[1], t, t);
         dacc(acc[2], s, s);
-      } else if constexpr (PH == PH_P4) {
-        const double2 x = vld<KP>(V[P_X], i, q), p = vld<KP>(V[P_P], i, q);
-        const double2 s = vld<KP>(V[P_S], i, q), t = vld<KP>(V[P_T], i, q);
-        if (u0 | u1) {
-          const double2 xn = fma2(om, s, fma2(al, p, x));
-          vst<KP>(V[P_X], i, q, make_double2(u0 ? xn.x : x.x, u1 ? xn.y : x.y));
-        }
-        const double2 r = fma2(neg2(om), t, s);
-        vst<KP>(V[P_R], i, q, r);
-        dacc(acc[0], r, vld<KP>(V[P_R0], i, q));
-      } else if constexpr (PH == PH_P5) {
-        const double2 r = vld<KP>(V[P_R], i, q), p = vld<KP>(V[P_P], i, q), v = vld<KP>(V[P_V], i, q);
-        vst<KP>(V[P_P], i, q, fma2(be, fma2(neg2(om), v, p), r));
       } else if constexpr (PH == PH_FINAL) {
         // ||b - A x||^2 of the final iterate; X out (ld = k; b = 0 columns give x = 0)
         const double2 ax = row_product<KP>(S, V[P_X], i, q, sm, te0, staged);
@@ -417,30 +462,28 @@ __device__ __noinline__ void run_tile(const PersistSys &S, int tl, Smem &sm, dou
   }
 }
 
-// The block's dot sums for system si in this phase (its tiles of si are consecutive in its tile
-// order): one partial per block at `slot` (the offset of the block's first tile of si), then the
-// system's last arriving block sums the min(G, ntiles) partials in slot order and runs the
-// listing's scalar rule.
+// The block's dot sums for system si in this phase: one partial per block at `slot` (0 <= slot <
+// parts, the blocks that run tiles of si), then the system's last arriving block sums the parts
+// partials in slot order and runs the listing's scalar rule.
 template <int KP, int PH>
-__device__ void flush(const PersistArgs &pa, int si, int slot, double2 (&acc)[3], Smem &sm) {
+__device__ void flush(const PersistArgs &pa, int si, int slot, int parts, double2 (&acc)[3], Smem &sm) {
   constexpr int ND = PhaseInfo<PH>::ND;
   const PersistSys &S = pa.sys[si];
-  const int parts = S.ntiles < (int)gridDim.x ? S.ntiles : (int)gridDim.x;
   tile_partials<KP, ND>(S, slot, acc, sm);
   if (!arrive(pa.tickets + si, parts, sm)) return;
   sys_sum<KP, ND>(S, parts, sm);
   const KArgs a = rule_args(S, KP);
   const int c = threadIdx.x;
   if constexpr (PH == PH_SETUP) {
-    if (c < KP) fin_col<FIN_SETUP>(a, c, sm.res, KP);
+    if (c < KP) fin_col<FIN_SETUP>(a, c, sm.u.r.res, KP);
   } else if constexpr (PH == PH_P1) {
-    if (c < KP) fin_col<FIN_DELTA>(a, c, sm.res, KP);
+    if (c < KP) fin_col<FIN_DELTA>(a, c, sm.u.r.res, KP);
   } else if constexpr (PH == PH_P3) {
-    if (c < KP) fin_col<FIN_G1>(a, c, sm.res, KP);
+    if (c < KP) fin_col<FIN_G1>(a, c, sm.u.r.res, KP);
   } else if constexpr (PH == PH_P4) {
-    if (c < KP) fin_col<FIN_RHO>(a, c, sm.res, KP);
+    if (c < KP) fin_col<FIN_RHO>(a, c, sm.u.r.res, KP);
   } else if constexpr (PH == PH_FINAL) {
-    if (c < KP) fin_col<FIN_TRUE>(a, c, sm.res, KP);
+    if (c < KP) fin_col<FIN_TRUE>(a, c, sm.u.r.res, KP);
   }
   __threadfence();
   __syncthreads();
@@ -469,51 +512,103 @@ __device__ void flush(const PersistArgs &pa, int si, int slot, double2 (&acc)[3]
   }
 }
 
-// The system that owns global tile t (tile0 ascending).
-__device__ int find_sys(const PersistArgs &pa, int64_t t) {
-  int lo = 0, hi = pa.nsys - 1;
+// Exclusive prefix over the systems of the tiles this phase runs (a system's tiles if it is live,
+// or every system's), in shared memory; returns the total.  Every block computes the same.
+__device__ int64_t phase_prefix(const PersistArgs &pa, Smem &sm, bool live_only) {
+  int carry = 0;
+  for (int base = 0; base < pa.nsys; base += kPT) {
+    const int si = base + threadIdx.x;
+    int v = 0;
+    if (si < pa.nsys) v = (!live_only || __ldcg(pa.live + si)) ? pa.sys[si].ntiles : 0;
+    // block-wide exclusive scan of v
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sm.scan_warp[w] = x;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int ww = 0; ww < kPT / 32; ++ww) {
+      const int t = sm.scan_warp[ww];
+      if (ww < w) before += t;
+      total += t;
+    }
+    if (si < pa.nsys) sm.pref[si] = carry + before + x - v;
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sm.pref[pa.nsys] = carry;
+  __syncthreads();
+  return carry;
+}
+
+// The system of phase tile t: the last system whose prefix is <= t (systems without tiles in the
+// phase have equal consecutive prefixes and are passed over).
+__device__ int find_sys(const Smem &sm, int nsys, int64_t t) {
+  int lo = 0, hi = nsys - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (pa.sys[mid].tile0 <= t) lo = mid;
+    if (sm.pref[mid] <= t) lo = mid;
     else hi = mid - 1;
   }
   return lo;
 }
 
 template <int PH>
-__device__ void flush_kp(const PersistArgs &pa, int si, int slot, double2 (&acc)[3], Smem &sm) {
+__device__ void flush_kp(const PersistArgs &pa, int si, int slot, int parts, double2 (&acc)[3], Smem &sm) {
   switch (pa.sys[si].kp) {
-    case 1: flush<1, PH>(pa, si, slot, acc, sm); break;
-    case 2: flush<2, PH>(pa, si, slot, acc, sm); break;
-    case 4: flush<4, PH>(pa, si, slot, acc, sm); break;
-    case 8: flush<8, PH>(pa, si, slot, acc, sm); break;
-    case 16: flush<16, PH>(pa, si, slot, acc, sm); break;
-    case 32: flush<32, PH>(pa, si, slot, acc, sm); break;
-    default: flush<64, PH>(pa, si, slot, acc, sm); break;
+    case 1: flush<1, PH>(pa, si, slot, parts, acc, sm); break;
+    case 2: flush<2, PH>(pa, si, slot, parts, acc, sm); break;
+    case 4: flush<4, PH>(pa, si, slot, parts, acc, sm); break;
+    case 8: flush<8, PH>(pa, si, slot, parts, acc, sm); break;
+    case 16: flush<16, PH>(pa, si, slot, parts, acc, sm); break;
+    case 32: flush<32, PH>(pa, si, slot, parts, acc, sm); break;
+    default: flush<64, PH>(pa, si, slot, parts, acc, sm); break;
   }
 }
 
-// Block b takes tiles b, b + G, ...; a system's tiles are contiguous, so the block meets its tiles
-// of one system one after another and sums their dot products before one flush per system.
+// Block b runs the contiguous chunk [b T / G, (b + 1) T / G) of the phase's T tiles (the live
+// systems' tiles in system order), so it meets one or two systems and the chunks stay balanced as
+// systems stop.  The blocks that run tiles of a system are consecutive; the block's slot among them
+// and their number follow from the chunk bounds (with T < G every tile is its own block).
+//
+// The prefix is recomputed where the set of systems may have changed since it was last taken: at
+// P1 and P5 (the P4 reducers mark stopped systems), and at the set-up and final phases (every
+// system).  P2, P3 and P4 reuse P1's: a P4 reducer changes a system's liveness while other blocks
+// may still be in P4, and every block must split the same tile list.
 template <int PH>
 __device__ void run_phase(const PersistArgs &pa, Smem &sm, bool live_only) {
   constexpr int ND = PhaseInfo<PH>::ND;
-  int cur = -1, slot = 0;
+  constexpr bool RETAKE = !(PH == PH_P2 || PH == PH_P3 || PH == PH_P4);
+  const int64_t T = RETAKE ? phase_prefix(pa, sm, live_only) : sm.pref[pa.nsys];
+  const int64_t G = gridDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * T / G, t1 = ((int64_t)blockIdx.x + 1) * T / G;
+  int cur = -1, slot = 0, parts = 0;
   double2 acc[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
   LaneSc ls;
-  for (int64_t t = blockIdx.x; t < pa.ntiles; t += gridDim.x) {
-    const int si = find_sys(pa, t);
-    if (live_only && !__ldcg(pa.live + si)) continue;
+  for (int64_t t = t0; t < t1; ++t) {
+    const int si = find_sys(sm, pa.nsys, t);
     const PersistSys &S = pa.sys[si];
-    const int tl = (int)(t - S.tile0);
+    const int64_t L0 = sm.pref[si], L1 = sm.pref[si + 1];
+    const int tl = (int)(t - L0);
     if (si != cur) {
       if constexpr (ND > 0) {
-        if (cur >= 0) flush_kp<PH>(pa, cur, slot, acc, sm);
+        if (cur >= 0) flush_kp<PH>(pa, cur, slot, parts, acc, sm);
 #pragma unroll
         for (int d = 0; d < 3; ++d) acc[d] = make_double2(0.0, 0.0);
       }
       cur = si;
-      slot = tl;
+      if (T < G) {  // one tile per block
+        slot = tl;
+        parts = (int)(L1 - L0);
+      } else {      // blocks b_first..b_last, b_first = the last block whose chunk starts at or before L0
+        const int64_t bf = ((L0 + 1) * G - 1) / T, bl = (L1 * G - 1) / T;
+        slot = (int)(blockIdx.x - bf);
+        parts = (int)(bl - bf + 1);
+      }
       switch (S.kp) {
         case 1: ls = lane_scalars<1, PH>(S); break;
         case 2: ls = lane_scalars<2, PH>(S); break;
@@ -535,11 +630,12 @@ __device__ void run_phase(const PersistArgs &pa, Smem &sm, bool live_only) {
     }
   }
   if constexpr (ND > 0) {
-    if (cur >= 0) flush_kp<PH>(pa, cur, slot, acc, sm);
+    if (cur >= 0) flush_kp<PH>(pa, cur, slot, parts, acc, sm);
   }
 }
 
-__global__ void __launch_bounds__(kPT, kPersistMaxBlocksPerSm) persist_kernel(const PersistArgs pa) {
+template <int MINB>
+__global__ void __launch_bounds__(kPT, MINB) persist_kernel(const PersistArgs pa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   if (threadIdx.x == 0) {
@@ -568,17 +664,29 @@ __global__ void __launch_bounds__(kPT, kPersistMaxBlocksPerSm) persist_kernel(co
   run_phase<PH_FINAL>(pa, sm, false);
 }
 
+template <int MINB>
+void *persist_fn() {
+  return reinterpret_cast<void *>(persist_kernel<MINB>);
+}
+void *persist_variant(int minb) { return minb >= 6 ? persist_fn<6>() : persist_fn<4>(); }
+
+cudaError_t set_smem(int minb) {
+  const int smem = (int)sizeof(Smem);
+  return minb >= 6 ? cudaFuncSetAttribute(persist_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                   : cudaFuncSetAttribute(persist_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 }  // namespace
 
 cudaError_t add_persist_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const PersistArgs &pa,
-                             int grid, cudaGraphNode_t *node) {
+                             int grid, int minb, cudaGraphNode_t *node) {
   const size_t smem = sizeof(Smem);
-  cudaError_t e = cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem(minb);
   if (e != cudaSuccess) return e;
   PersistArgs arg = pa;
   void *params[1] = {&arg};
   cudaKernelNodeParams kp = {};
-  kp.func = reinterpret_cast<void *>(persist_kernel);
+  kp.func = persist_variant(minb);
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(kPT);
   kp.sharedMemBytes = (unsigned)smem;
@@ -590,19 +698,22 @@ cudaError_t add_persist_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t 
   return cudaGraphKernelNodeSetAttribute(*node, cudaLaunchAttributeCooperative, &v);
 }
 
-int persist_blocks_per_sm() {
+int persist_blocks_per_sm(int minb) {
   int nb = 0;
-  const size_t smem = sizeof(Smem);
-  if (cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persist_kernel, kPT, smem) != cudaSuccess) return 0;
+  if (set_smem(minb) != cudaSuccess) return 0;
+  const cudaError_t e = minb >= 6
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persist_kernel<6>, kPT, sizeof(Smem))
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persist_kernel<4>, kPT, sizeof(Smem));
+  if (e != cudaSuccess) return 0;
   return nb;
 }
 
-cudaError_t launch_persist(const PersistArgs &pa, int grid, cudaStream_t s) {
+cudaError_t launch_persist(const PersistArgs &pa, int grid, int minb, cudaStream_t s) {
   const size_t smem = sizeof(Smem);
-  cudaError_t e = cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem(minb);
   if (e != cudaSuccess) return e;
+  PersistArgs arg = pa;
+  void *params[1] = {&arg};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kPT);
@@ -613,7 +724,7 @@ cudaError_t launch_persist(const PersistArgs &pa, int grid, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, persist_kernel, pa);
+  return cudaLaunchKernelExC(&cfg, persist_variant(minb), params);
 }
 
 }  // namespace bicgk

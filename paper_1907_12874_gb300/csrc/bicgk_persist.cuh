@@ -11,7 +11,7 @@ namespace bicgk {
 
 constexpr int kPersistThreads = 256;  // threads per block of the persistent kernel
 constexpr int kPersistStage = 2048;   // staged CSR entries per 256-row pass (kp <= 2)
-constexpr int kPersistMaxBlocksPerSm = 4;
+constexpr int kPersistMaxSys = 1024;  // systems of one persistent batch (tile prefix in shared memory)
 
 // Vector roles of a system in the persistent solve (pointers into its batch workspace).
 enum PersistRole : int { P_X = 0, P_R, P_R0, P_P, P_V, P_S, P_T, P_B, P_NROLE };
@@ -63,12 +63,13 @@ struct PersistArgs {
 
 // Rows of one 256-thread pass for padded width kp.
 inline int persist_rows_per_pass(int kp) { return kPersistThreads / (kp >= 4 ? kp / 2 : 1); }
-// Co-resident blocks per SM of the persistent kernel (0 on error).
-int persist_blocks_per_sm();
+// Co-resident blocks per SM of the persistent kernel compiled for `minb` blocks per SM (4: up to
+// 64 registers a thread; 6: up to 40); 0 on error.
+int persist_blocks_per_sm(int minb);
 // Cooperative launch of `grid` blocks (grid must not exceed the co-resident count).
-cudaError_t launch_persist(const PersistArgs &pa, int grid, cudaStream_t s);
+cudaError_t launch_persist(const PersistArgs &pa, int grid, int minb, cudaStream_t s);
 // The same launch as a cooperative kernel node of graph g after `deps`.
 cudaError_t add_persist_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, const PersistArgs &pa,
-                             int grid, cudaGraphNode_t *node);
+                             int grid, int minb, cudaGraphNode_t *node);
 
 }  // namespace bicgk

@@ -251,3 +251,37 @@ def test_persistent_tuner(bk, cuda):
     for a, b in zip(X0, X1):
         a, b = a.cpu().numpy(), b.cpu().numpy()
         assert np.all(np.linalg.norm(a - b, axis=0) <= 1e-12 * np.linalg.norm(a, axis=0))
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_solve_in_the_persistent_kernel(bk, cuda, k):
+    """bicgk_solve with BICGK_OPT_PERSISTENT = 2 runs the whole solve as one cooperative launch of
+    the persistent kernel: x_m and the residual history after 6 fixed iterations within 1e-12 and
+    1e-10 of the oracle's (and of the graph path's), the solve to tolerance within the oracle's
+    bars (stable operator), one kernel launch per solve."""
+    from oracle_bars import colerr, column_bars
+    torch = cuda
+    A = I.convdiff7(14, peclet=True)
+    B = I.rhs(A.n, k, 40)
+    Bd = torch.from_numpy(B).cuda()
+    with bk.Operator(A) as op:
+        rg = op.solve(Bd, tol=0.0, maxit=6, flags=bk.FLAG_NO_STOP_TEST)
+        Xg = rg.X.cpu().numpy()
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, 2)
+        rp6 = op.solve(Bd, tol=0.0, maxit=6, flags=bk.FLAG_NO_STOP_TEST)
+        assert bk.last_stats(op.handle)["kernel_launches"] == 1
+        rp = op.solve(Bd, tol=1e-9, maxit=1000)
+        X = rp.X.cpu().numpy()
+    ro6 = oracle.solve(A, B, tol=0.0, maxit=6, flags=oracle.NO_STOP_TEST)
+    X6 = rp6.X.cpu().numpy()
+    assert np.all(colerr(X6, ro6.X) <= 1e-12) and np.all(colerr(X6, Xg) <= 1e-12)
+    np.testing.assert_allclose(rp6.hist, ro6.hist, rtol=1e-10)
+    ro = oracle.solve(A, B, tol=1e-9, maxit=1000)
+    sol_bar, it_bar = column_bars(A, B, ro, tol=1e-9, maxit=1000)
+    assert np.array_equal(rp.status, ro.status) and np.all(np.abs(rp.iters - ro.iters) <= it_bar)
+    assert np.all(colerr(X, ro.X) <= sol_bar), colerr(X, ro.X)
+    # histories at each column's own place; near convergence the merged estimate theta - omega phi
+    # is a difference of much larger numbers, so two summation orders agree only to about 1e-2 there
+    for c in range(k):
+        m = int(min(rp.iters[c], ro.iters[c]))
+        np.testing.assert_allclose(rp.hist[: m + 1, c], ro.hist[: m + 1, c], rtol=1e-2)
