@@ -302,9 +302,11 @@ enum bicgk_option {
                                       preconditioner on device blocks: 2 runs the solve as ONE
                                       cooperative launch of the persistent batch kernel (a
                                       one-system batch over this operator, kept for the next
-                                      solve of the same k; see BICGK_BATCH_PERSISTENT), with its
-                                      scalar rules and a residual history; 0 (default) and 1:
-                                      the graph path.  Not in profiling mode.                 */
+                                      solve of the same k, whose first solve tunes its launch
+                                      shape with bicgk_batch_tune_persistent; see
+                                      BICGK_BATCH_PERSISTENT), with its scalar rules and a
+                                      residual history; 0 (default) and 1: the graph path.  Not
+                                      in profiling mode.                                       */
 };
 
 /*
@@ -353,10 +355,12 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value);
  *   the block, and the next solve starts from a clean state.
  * bicgk_batch_tune_persistent: autotuner of the persistent mode: rows per CTA tile (1, 2, 4 or
  *   8 passes of 256 threads: 256..2048 rows at kp <= 2, 64..512 at kp = 8) x blocks per SM (the
- *   kernel compiled for 4 blocks of up to 64 registers a thread, or 6 of up to 40); times `reps`
- *   persistent solves of 4 fixed iterations with right-hand sides of ones for each of the 8
- *   shapes and keeps the fastest (allocates two temporary blocks).  Writes each system's rows
- *   per tile to the nullable array [nsys]; bicgk_batch_persistent_info gives the grid.
+ *   kernel compiled for 4 blocks of up to 64 registers a thread, or 6 of up to 40) on the full
+ *   co-resident grid, then the best of those on 1/2, 1/4, 1/8, 1/16 of the grid (small
+ *   problems: fewer blocks in every barrier and reduction); times `reps` persistent solves of 4
+ *   fixed iterations with right-hand sides of ones for each of the 12 shapes and keeps the
+ *   fastest (allocates two temporary blocks).  Writes each system's rows per tile to the
+ *   nullable array [nsys]; bicgk_batch_persistent_info gives the grid.
  * bicgk_batch_set_deadline: longest wait of one grid barrier of the persistent kernel, in
  *   microseconds (0..3.6e9; 0 makes every wait that does not find all blocks arrived fail).
  * bicgk_batch_last_launches: kernels the last bicgk_batch_solve launched (persistent: 1).

@@ -11,6 +11,7 @@
 //      returns to the host;
 //   3. unpack X and copy the per-column results to the host.
 // The graph of each (variant, kp) is captured once per operator and reused.
+#include <condition_variable>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -240,6 +241,8 @@ struct Workspace {
 
 }  // namespace
 
+class CopyPool;
+
 struct bicgk_op_s {
   int device = 0;
   int nsm = 0;
@@ -257,6 +260,7 @@ struct bicgk_op_s {
   double *d_stage[2] = {nullptr, nullptr};  // caller-layout staging for host-memory calls
   int64_t stage_elems = 0;
   void *h_bounce = nullptr;  // two page-locked chunks for copies of pageable host blocks
+  CopyPool *copy_pool = nullptr;  // host threads for those copies (made with the chunks)
   cudaEvent_t bounce_ev[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t fork = nullptr;
@@ -478,31 +482,97 @@ const void *mapped_host_ptr(const void *p) {
 // while the DMA engine moves the other.
 constexpr size_t kBounceBytes = size_t(32) << 20;
 
-void parallel_memcpy(void *dst, const void *src, size_t bytes) {
-  const unsigned hw = std::thread::hardware_concurrency();
-  const unsigned nt = hw < 8 ? (hw ? hw : 1) : 8;
-  if (nt <= 1 || bytes < (size_t(1) << 20)) {
-    std::memcpy(dst, src, bytes);
-    return;
-  }
-  std::vector<std::thread> th;
-  const size_t part = (bytes + nt - 1) / nt;
-  size_t done = 0;  // bytes handed to threads; the rest is copied here (also if a thread cannot start)
-  try {
-    for (unsigned t = 0; t < nt; ++t) {
-      const size_t off = t * part;
-      if (off >= bytes) break;
-      const size_t len = part < bytes - off ? part : bytes - off;
-      th.emplace_back([=] { std::memcpy(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, len); });
-      done = off + len;
+}  // namespace
+
+// Host threads kept by an operator for its copies of pageable blocks through the bounce chunks:
+// every chunk is split between the calling thread and the workers (starting threads per 32 MB
+// chunk would cost about as much as the copy).  Workers that cannot start are simply absent.
+class CopyPool {
+ public:
+  explicit CopyPool(unsigned workers) {
+    try {
+      for (unsigned i = 0; i < workers; ++i) th_.emplace_back([this, i] { loop(i); });
+    } catch (...) {
     }
-  } catch (...) {
   }
-  if (done < bytes) std::memcpy(static_cast<char *>(dst) + done, static_cast<const char *>(src) + done, bytes - done);
-  for (std::thread &x : th) x.join();
+  ~CopyPool() {
+    {
+      std::lock_guard<std::mutex> l(mu_);
+      stop_ = true;
+    }
+    go_.notify_all();
+    for (std::thread &t : th_) t.join();
+  }
+  // dst <- src (bytes); returns when every share is copied.
+  void copy(void *dst, const void *src, size_t bytes) {
+    const unsigned nw = (unsigned)th_.size();
+    if (nw == 0 || bytes < (size_t(1) << 20)) {
+      std::memcpy(dst, src, bytes);
+      return;
+    }
+    const size_t part = (bytes + nw) / (nw + 1);
+    {
+      std::lock_guard<std::mutex> l(mu_);
+      dst_ = static_cast<char *>(dst);
+      src_ = static_cast<const char *>(src);
+      bytes_ = bytes;
+      part_ = part;
+      pending_ = nw;
+      ++gen_;
+    }
+    go_.notify_all();
+    const size_t off = (size_t)nw * part;  // the caller's share: the last one
+    if (off < bytes) std::memcpy(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, bytes - off);
+    std::unique_lock<std::mutex> l(mu_);
+    done_.wait(l, [&] { return pending_ == 0; });
+  }
+
+ private:
+  void loop(unsigned i) {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> l(mu_);
+    for (;;) {
+      go_.wait(l, [&] { return stop_ || gen_ != seen; });
+      if (stop_) return;
+      seen = gen_;
+      char *d = dst_;
+      const char *sp = src_;
+      const size_t off = (size_t)i * part_, bytes = bytes_;
+      const size_t len = off < bytes ? (part_ < bytes - off ? part_ : bytes - off) : 0;
+      l.unlock();
+      if (len) std::memcpy(d + off, sp + off, len);
+      l.lock();
+      if (--pending_ == 0) done_.notify_one();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable go_, done_;
+  char *dst_ = nullptr;
+  const char *src_ = nullptr;
+  size_t bytes_ = 0, part_ = 0;
+  unsigned pending_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+namespace {
+
+void parallel_memcpy(bicgk_op A, void *dst, const void *src, size_t bytes) {
+  if (A->copy_pool) A->copy_pool->copy(dst, src, bytes);
+  else std::memcpy(dst, src, bytes);
 }
 
 int ensure_bounce(bicgk_op A) {
+  if (!A->copy_pool) {  // up to 7 workers beside the calling thread
+    const unsigned hw = std::thread::hardware_concurrency();
+    const unsigned nt = hw < 8 ? (hw ? hw : 1) : 8;
+    try {
+      A->copy_pool = new CopyPool(nt - 1);
+    } catch (...) {
+      A->copy_pool = nullptr;  // plain copies
+    }
+  }
   if (A->h_bounce) return BICGK_OK;
   for (int i = 0; i < 2; ++i)
     if (!A->bounce_ev[i]) CK(cudaEventCreateWithFlags(&A->bounce_ev[i], cudaEventDisableTiming));
@@ -519,7 +589,7 @@ int copy_in_pageable(bicgk_op A, void *dst, const void *src, size_t bytes, cudaS
     const size_t len = kBounceBytes < bytes - off ? kBounceBytes : bytes - off;
     char *b = static_cast<char *>(A->h_bounce) + slot * kBounceBytes;
     CK(cudaEventSynchronize(A->bounce_ev[slot]));  // the chunk's previous copy has finished
-    parallel_memcpy(b, static_cast<const char *>(src) + off, len);
+    parallel_memcpy(A, b, static_cast<const char *>(src) + off, len);
     CK(cudaMemcpyAsync(static_cast<char *>(dst) + off, b, len, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(A->bounce_ev[slot], s));
   }
@@ -541,7 +611,7 @@ int copy_out_pageable(bicgk_op A, void *dst, const void *src, size_t bytes, cuda
     const int slot = (int)(i & 1);
     const size_t off = i * kBounceBytes, len = kBounceBytes < bytes - off ? kBounceBytes : bytes - off;
     CK(cudaEventSynchronize(A->bounce_ev[slot]));
-    parallel_memcpy(static_cast<char *>(dst) + off, static_cast<char *>(A->h_bounce) + slot * kBounceBytes, len);
+    parallel_memcpy(A, static_cast<char *>(dst) + off, static_cast<char *>(A->h_bounce) + slot * kBounceBytes, len);
     if (i + 2 < n) {  // the drained chunk takes the one after next
       const size_t o2 = (i + 2) * kBounceBytes, l2 = kBounceBytes < bytes - o2 ? kBounceBytes : bytes - o2;
       CK(cudaMemcpyAsync(static_cast<char *>(A->h_bounce) + slot * kBounceBytes, static_cast<const char *>(src) + o2,
@@ -1054,6 +1124,7 @@ int bicgk_op_destroy(bicgk_op A) {
   cudaFree(A->d_stage[0]);
   cudaFree(A->d_stage[1]);
   cudaFreeHost(A->h_bounce);
+  delete A->copy_pool;
   for (cudaEvent_t e : A->bounce_ev)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : A->ev) cudaEventDestroy(e);
@@ -1688,6 +1759,7 @@ struct bicgk_batch_s {
   int p_grid = 0;
   int p_sub = 1;              // 256-thread passes per tile (rows per CTA tile; bicgk_batch_tune_persistent)
   int p_minb = 4;             // blocks per SM of the kernel variant (4 or 6; bicgk_batch_tune_persistent)
+  int p_div = 1;              // the grid is the co-resident maximum / p_div blocks (tuned)
   int64_t deadline_us = 1000000;  // longest wait at one grid barrier
   GraphEntry pgraph;          // clear the control block, the cooperative kernel
   bool pgraph_ok = false;
@@ -1852,7 +1924,8 @@ int persist_prepare(bicgk_batch b) {
   if (!b->p_grid) {
     const int nb = persist_blocks_per_sm(b->p_minb);
     if (nb < 1) return cuda_fail(cudaGetLastError(), "persistent kernel occupancy");
-    b->p_grid = b->ops[0]->nsm * (nb < b->p_minb ? nb : b->p_minb);
+    const int full = b->ops[0]->nsm * (nb < b->p_minb ? nb : b->p_minb);
+    b->p_grid = full / b->p_div > 0 ? full / b->p_div : 1;
   }
   return BICGK_OK;
 }
@@ -1987,6 +2060,8 @@ int persist_single(bicgk_op A, int32_t k, const double *B, const double *X0, dou
     }
     A->pbatch = b;
     A->pbatch_k = k;
+    // the first solve of this width picks the launch shape (a few short solves, temporaries)
+    if ((rc = bicgk_batch_tune_persistent(b, 2, nullptr, s))) return rc;
   }
   bicgk_batch b = A->pbatch;
   const double *Bv[1] = {B};
@@ -2304,13 +2379,18 @@ int bicgk_batch_tune_persistent(bicgk_batch b, int32_t reps, int32_t *rows_per_t
       (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
     rc = cuda_fail(e, "bicgk_batch_tune_persistent");
   // blocks per SM (the kernel variant for 4 or 6) x rows per CTA tile (1, 2, 4, 8 passes of 256
-  // threads); 4 fixed iterations of every system
-  int best_sub = b->p_sub, best_minb = b->p_minb;
+  // threads) at the full co-resident grid, then that shape on 1/2 .. 1/16 of the grid (small
+  // problems: fewer blocks take part in every barrier and reduction); 4 fixed iterations of every
+  // system
+  int best_sub = b->p_sub, best_minb = b->p_minb, best_div = 1;
   float best = 1e30f;
-  for (int cfg = 0; cfg < 8 && rc == BICGK_OK; ++cfg) {
-    const int sub = 1 << (cfg & 3), minb = cfg < 4 ? 4 : 6;
-    if (minb != b->p_minb) {
+  for (int cfg = 0; cfg < 12 && rc == BICGK_OK; ++cfg) {
+    const int sub = cfg < 8 ? 1 << (cfg & 3) : best_sub;
+    const int minb = cfg < 8 ? (cfg < 4 ? 4 : 6) : best_minb;
+    const int div = cfg < 8 ? 1 : 2 << (cfg - 8);
+    if (minb != b->p_minb || div != b->p_div) {
       b->p_minb = minb;
+      b->p_div = div;
       b->p_grid = 0;  // re-derived from the variant's occupancy
       persist_drop_graph(b);
     }
@@ -2330,11 +2410,13 @@ int bicgk_batch_tune_persistent(bicgk_batch b, int32_t reps, int32_t *rows_per_t
       best = total;
       best_sub = sub;
       best_minb = minb;
+      best_div = div;
     }
   }
   b->p_sub = best_sub;
-  if (b->p_minb != best_minb) b->p_grid = 0;
+  if (b->p_minb != best_minb || b->p_div != best_div) b->p_grid = 0;
   b->p_minb = best_minb;
+  b->p_div = best_div;
   persist_drop_graph(b);
   if (rc == BICGK_OK) rc = persist_prepare(b);
   if (rc == BICGK_OK && rows_per_tile_out)

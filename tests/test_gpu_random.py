@@ -91,8 +91,13 @@ def test_random_system(bk, cuda, case):
             rp = oracle.solve(A, B * (1.0 + 2.0 ** -52 * gt.standard_normal(B.shape)), tol=0.0, maxit=m,
                               variant=variant, flags=oracle.NO_STOP_TEST | flags)
             tsens = max(tsens, float(_colerr(rp.X, ro.X).max()))
-        assert np.all(_colerr(X, ro.X) <= max(1e-11, 10.0 * tsens)), (A.n, B.shape[1], m, _colerr(X, ro.X).max(), tsens)
-        np.testing.assert_allclose(r.hist[: m + 1], ro.hist[: m + 1], rtol=max(1e-10, 10.0 * tsens), atol=1e-300)
+        # capped at 1e-9: a sensitivity estimate that has grown beyond that would hide a real defect
+        # in the first iterates rather than measure rounding (the largest seen: 3.3e-11)
+        tbar = min(1e-9, max(1e-11, 10.0 * tsens))
+        print(f"[random case {case}] {variant} n={A.n} k={B.shape[1]} m={m}: x_m GPU-oracle "
+              f"{_colerr(X, ro.X).max():.2e}, oracle one-unit response {tsens:.2e}, bar {tbar:.2e}")
+        assert np.all(_colerr(X, ro.X) <= tbar), (A.n, B.shape[1], m, _colerr(X, ro.X).max(), tsens)
+        np.testing.assert_allclose(r.hist[: m + 1], ro.hist[: m + 1], rtol=max(1e-10, tbar), atol=1e-300)
         r = op.solve(Bd, tol=1e-10, maxit=2000, variant=variant, flags=bk.FLAG_JACOBI if jacobi else 0)
         ro = oracle.solve(A, B, tol=1e-10, maxit=2000, variant=variant, flags=flags)
         X = r.X.cpu().numpy()
