@@ -527,8 +527,8 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
     model T = Sigma / B (Eq. SpMV_mem, x read C + 1 times) with B the measured HBM bandwidth."""
     import oracle
     N, nnz = A.n, A.nnz
-    res = {"workload": f"{args.grid}^3 benchmark operator, {nit} fixed iterations per form and k; oracle_err: "
-                       f"column 0 after the {nit} iterations against the oracle's",
+    res = {"workload": f"{args.grid}^3 benchmark operator, {nit} fixed iterations per form and k; "
+                       f"oracle_err_8_iterations: column 0 after 8 fixed iterations against the oracle's",
            "hbm_gbs": hbm_gbs, "rows": {}}
     with bicgk.Operator(A) as opw:
         for k in (1, 2, 4, 8, 16, 32):
@@ -556,10 +556,14 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
                                             "algorithmic_gb_per_iter": byts / 1e9,
                                             "hbm_frac": byts / s_it / (hbm_gbs * 1e9),
                                             "paper_model_ms": model * 1e3}
+                # error against the oracle: column 0 after 8 fixed iterations of the same solve (past
+                # a few dozen iterations this operator amplifies rounding differences to the percent
+                # level in any two implementations, the oracle's own one-unit response included)
+                opw.solve(Bk, X=Xk, tol=0.0, maxit=8, variant=v, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
                 col0[v] = Xk[:, :1].cpu().numpy()
-            jobs = [(0, dict(tol=0.0, maxit=nit, variant=v, flags=oracle.NO_STOP_TEST)) for v in col0]
+            jobs = [(0, dict(tol=0.0, maxit=8, variant=v, flags=oracle.NO_STOP_TEST)) for v in col0]
             for v, ro in zip(col0, oracle_columns(A, Bh, jobs)):
-                res["rows"][f"{v}/k{k}"]["oracle_err"] = float(colerr(col0[v], ro.X)[0])
+                res["rows"][f"{v}/k{k}"]["oracle_err_8_iterations"] = float(colerr(col0[v], ro.X)[0])
     return res
 
 

@@ -19,3 +19,13 @@ def cuda():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch
+
+
+def pytest_terminal_summary(terminalreporter):
+    """The parity bars measured on the oracle during the run (tests/oracle_bars.py), one line each."""
+    mod = sys.modules.get("oracle_bars")
+    if mod is None or not getattr(mod, "RECORD", None):
+        return
+    terminalreporter.section("parity bars measured on the oracle")
+    for line in mod.RECORD:
+        terminalreporter.write_line(line)

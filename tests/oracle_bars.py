@@ -43,6 +43,9 @@ import oracle
 
 ULP = 2.0 ** -52
 
+# one line per measured bar, printed by tests/conftest.py in the run's terminal summary
+RECORD: list = []
+
 
 def colerr(X, Xo):
     """Relative 2-norm difference per column (absolute where the reference column is zero)."""
@@ -130,9 +133,11 @@ def derived_bars(A, B, ro, floor=1e-10, draws=None, seed=11, cols=None, X0=None,
     n = sol.shape[0]
     sol_bar = np.full(n, max(floor, 10.0 * float(sol.max())))
     it_bar = np.full(n, max(1, 2 * int(spread.max())))
-    print(f"[bars{(' ' + label) if label else ''}] oracle one-unit response over {draws} draws x {n} columns: "
-          f"solution {np.array2string(sol, precision=2)}, iterations +-{spread.tolist()} -> solution bar "
-          f"{sol_bar[0]:.2e}, iteration bar +-{it_bar[0]}")
+    line = (f"{label or A.name}: oracle one-unit response over {draws} draws x {n} columns: solution max "
+            f"{sol.max():.2e}, iterations +-{int(spread.max())} -> solution bar {sol_bar[0]:.2e}, iteration bar "
+            f"+-{it_bar[0]}")
+    RECORD.append(line)
+    print(f"[bars] {line}")
     return sol_bar, it_bar
 
 
@@ -160,6 +165,8 @@ def column_bars(A, B, ro, floor=1e-10, draws=3, seed=13, X0=None, label="", **kw
     sol_bar = np.maximum(floor, 10.0 * sol)
     it_bar = np.maximum(1, 2 * spread)
     if np.any(sol_bar > floor):
-        print(f"[bars{(' ' + label) if label else ''}] per-column one-unit response "
-              f"{np.array2string(sol, precision=2)} -> solution bars {np.array2string(sol_bar, precision=2)}")
+        line = (f"{label or A.name}: per-column one-unit response max {sol.max():.2e} -> solution bars up to "
+                f"{sol_bar.max():.2e}")
+        RECORD.append(line)
+        print(f"[bars] {line}")
     return sol_bar, it_bar

@@ -25,7 +25,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle_bars import colerr, derived_bars, solve_columns, trajectory_bars
+from oracle_bars import RECORD, colerr, derived_bars, solve_columns, trajectory_bars
 from paper_1907_12874_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -81,9 +81,11 @@ def test_full_size_trajectory_all_columns(bk, cuda, system):
             bar, ro, sens, hbar = trajectory_bars(A, B, m)
             err = colerr(X, ro.X)
             herr = np.max(np.abs(r.hist[: m + 1] - ro.hist[: m + 1]) / np.abs(ro.hist[: m + 1]), axis=0)
-            print(f"[trajectory 128^3 k=32 m={m}] max GPU-oracle {err.max():.2e}, oracle one-unit response "
-                  f"max {sens.max():.2e}, bar max {bar.max():.2e}; history max {herr.max():.2e}, bar max "
-                  f"{hbar.max():.2e}")
+            line = (f"trajectory 128^3 k=32 m={m}: max GPU-oracle {err.max():.2e}, oracle one-unit response "
+                    f"max {sens.max():.2e}, bar max {bar.max():.2e}; history max {herr.max():.2e}, bar max "
+                    f"{hbar.max():.2e}")
+            RECORD.append(line)
+            print(f"[bars] {line}")
             assert np.all(err <= bar), (m, err, bar)
             assert np.all(herr <= hbar), (m, herr, hbar)
 
@@ -175,10 +177,12 @@ def test_full_size_mixed_matches_oracle(bk, cuda):
     spread = np.abs(np.array(inner) - ro.inner_iters[None, :]).max(axis=0)
     bar = np.maximum(10.0 * resp, 1e-10 * np.abs(ro.X).max(axis=0))
     dev = np.abs(X[:, MIXED_SAMPLE] - ro.X).max(axis=0)
-    print(f"[mixed 128^3 k=32] max |x - x_oracle| {np.array2string(dev, precision=2)}, bar "
-          f"{np.array2string(bar, precision=2)} (max |x| {np.abs(ro.X).max():.2f}); passes GPU "
-          f"{r.outer_iters[MIXED_SAMPLE].tolist()} oracle {ro.outer_iters.tolist()}; FP32 iterations GPU "
-          f"{r.inner_iters[MIXED_SAMPLE].tolist()} oracle {ro.inner_iters.tolist()} spread {spread.tolist()}")
+    line = (f"mixed 128^3 k=32: max |x - x_oracle| {dev.max():.2e}, bar min {bar.min():.2e} (max |x| "
+            f"{np.abs(ro.X).max():.2f}); passes GPU {r.outer_iters[MIXED_SAMPLE].tolist()} oracle "
+            f"{ro.outer_iters.tolist()}; FP32 iterations GPU {r.inner_iters[MIXED_SAMPLE].tolist()} oracle "
+            f"{ro.inner_iters.tolist()} spread {spread.tolist()}")
+    RECORD.append(line)
+    print(f"[bars] {line}")
     assert np.all(np.abs(X[:, MIXED_SAMPLE] - ro.X) <= bar[None, :]), (dev, bar)
     assert np.all(np.abs(r.outer_iters[MIXED_SAMPLE] - ro.outer_iters) <= 1)
     assert np.all(np.abs(r.inner_iters[MIXED_SAMPLE] - ro.inner_iters) <= np.maximum(2, 2 * spread))
