@@ -585,7 +585,7 @@ def small_k_section(args, bicgk, inputs, torch, dev, A128):
     ro = oracle.solve(A16, B16h, tol=1e-8, maxit=1000)
     row = {"workload": "convdiff7 16^3 (4,096 rows), k=4, rel tol 1e-8, classical_merged"}
     with bicgk.Operator(A16) as op:
-        for name, opt in (("graph", 0), ("persistent", 2)):
+        for name, opt in (("graph", 1), ("persistent", 2)):
             bicgk.set_option(op.handle, bicgk.OPT_PERSISTENT, opt)
             r = op.solve(B16, X=X16, tol=1e-8, maxit=1000, want_hist=False)
             torch.cuda.synchronize()
@@ -611,7 +611,7 @@ def small_k_section(args, bicgk, inputs, torch, dev, A128):
             Xk = torch.empty_like(Bk)
             ro12 = oracle_columns(A128, Bh, [(0, dict(tol=0.0, maxit=12, flags=oracle.NO_STOP_TEST))])[0]
             row = {}
-            for name, opt in (("graph", 0), ("persistent", 2)):
+            for name, opt in (("graph", 1), ("persistent", 2)):
                 bicgk.set_option(op.handle, bicgk.OPT_PERSISTENT, opt)
                 op.solve(Bk, X=Xk, tol=0.0, maxit=3, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
                 torch.cuda.synchronize()

@@ -299,14 +299,17 @@ enum bicgk_option {
                                       1: never.  The iterates are those of the full layout up
                                       to summation order.                                      */
   BICGK_OPT_PERSISTENT = 8          /* merged classical BiCGStab (Algorithm 2) without
-                                      preconditioner on device blocks: 2 runs the solve as ONE
-                                      cooperative launch of the persistent batch kernel (a
-                                      one-system batch over this operator, kept for the next
-                                      solve of the same k, whose first solve tunes its launch
-                                      shape with bicgk_batch_tune_persistent; see
-                                      BICGK_BATCH_PERSISTENT), with its scalar rules and a
-                                      residual history; 0 (default) and 1: the graph path.  Not
-                                      in profiling mode.                                       */
+                                      preconditioner: run the solve as ONE cooperative launch of
+                                      the persistent batch kernel (a one-system batch over this
+                                      operator, kept for the next solve of the same k, whose
+                                      first solve tunes its launch shape with
+                                      bicgk_batch_tune_persistent; see BICGK_BATCH_PERSISTENT;
+                                      host blocks are staged), with its scalar rules and a
+                                      residual history.  0 (default): for small systems with at
+                                      least two right-hand sides (n_rows <= 32,768, kp <= 16,
+                                      n_rows*kp <= 2^19), where one launch is faster than the
+                                      graph path's many; 1: never; 2: always.  Never in
+                                      profiling mode.                                          */
 };
 
 /*

@@ -265,6 +265,7 @@ def test_solve_in_the_persistent_kernel(bk, cuda, k):
     B = I.rhs(A.n, k, 40)
     Bd = torch.from_numpy(B).cuda()
     with bk.Operator(A) as op:
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, 1)
         rg = op.solve(Bd, tol=0.0, maxit=6, flags=bk.FLAG_NO_STOP_TEST)
         Xg = rg.X.cpu().numpy()
         bk.set_option(op.handle, bk.OPT_PERSISTENT, 2)

@@ -319,11 +319,15 @@ def test_fixed_iteration_mode(bk, cuda, variant):
     assert np.all(_colerr(X, ro.X) <= 1e-11)
 
 
-def test_host_memory_path_is_bitwise_device_path(bk, cuda):
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_host_memory_path_is_bitwise_device_path(bk, cuda, persistent):
+    """Host blocks give bitwise the device call's results, on the graph path and (automatic at this
+    size) in the persistent kernel; repeated device calls are bitwise equal."""
     torch = cuda
     A = I.convdiff7(14)
     B = I.rhs(A.n, 5, 12)
     with bk.Operator(A) as op:
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, persistent)
         rh = op.solve(B, tol=1e-8, maxit=500)
         rd = op.solve(torch.from_numpy(B).cuda(), tol=1e-8, maxit=500)
         rd2 = op.solve(torch.from_numpy(B).cuda(), tol=1e-8, maxit=500)
@@ -356,6 +360,7 @@ def test_profiling_mode_keeps_the_column_groups(bk, cuda, k):
     B = torch.from_numpy(I.rhs(A.n, k, 13)).cuda()
     with bk.Operator(A) as op:
         bk.set_option(op.handle, bk.OPT_COMPACT, 1)
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, 1)   # the graph path (k = 8 would run persistent)
         rg = op.solve(B, tol=1e-8, maxit=500)
         groups = bk.last_stats(op.handle)["groups"]
         bk.set_profiling(op.handle, True)
@@ -457,6 +462,7 @@ def test_fused_dots_match_separate_kernels(bk, cuda, variant, k, kind):
     ro = oracle.solve(A, B, tol=0.0, maxit=6, variant=variant, flags=oracle.NO_STOP_TEST)
     X = {}
     with bk.Operator(A) as op:
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, 1)   # these options belong to the graph path
         for fz, th in ((1, 1), (2, 1), (1, 2), (2, 2)):
             bk.set_option(op.handle, bk.OPT_FUSED_DOTS, fz)
             bk.set_option(op.handle, bk.OPT_THETA_IN_S, th)
@@ -515,6 +521,7 @@ def test_column_compaction_matches_full_layout(bk, cuda, variant, k):
     G0d = torch.from_numpy(G0).cuda()
     res = {}
     with bk.Operator(A) as op:
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, 1)   # compaction belongs to the graph path
         for compact in (1, 0):
             bk.set_option(op.handle, bk.OPT_COMPACT, compact)
             r = op.solve(Bd, X0=G0d, tol=1e-9, maxit=600, variant=variant, flags=flags)
@@ -554,6 +561,7 @@ def test_column_compaction_down_to_one_column(bk, cuda, variant):
     B[:, 5] = I.rhs(A.n, 1, 3)[:, 0]
     ro = oracle.solve(A, B, tol=1e-10, maxit=500, variant=variant)
     with bk.Operator(A) as op:
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, 1)   # compaction belongs to the graph path
         r = op.solve(torch.from_numpy(B).cuda(), tol=1e-10, maxit=500, variant=variant)
         X = r.X.cpu().numpy()
         rh = op.solve(torch.from_numpy(B).pin_memory(), tol=1e-10, maxit=500, variant=variant)
@@ -576,6 +584,7 @@ def test_column_compaction_idle_without_stops(bk, cuda, variant):
     B = torch.from_numpy(I.rhs(A.n, 6, 8)).cuda()
     out = []
     with bk.Operator(A) as op:
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, 1)   # compaction belongs to the graph path
         for compact in (1, 0):
             bk.set_option(op.handle, bk.OPT_COMPACT, compact)
             r = op.solve(B, tol=0.0, maxit=7, variant=variant, flags=bk.FLAG_NO_STOP_TEST)
@@ -592,7 +601,8 @@ def test_options_validate_their_values(bk, cuda):
                                (bk.OPT_FUSED_DOTS, (0, 1, 2), (-1, 3)),
                                (bk.OPT_THETA_IN_S, (0, 1, 2), (-1, 3)),
                                (bk.OPT_HOST_ZERO_COPY, (0, 1), (-1, 2)),
-                               (bk.OPT_COMPACT, (0, 1), (-1, 2))):
+                               (bk.OPT_COMPACT, (0, 1), (-1, 2)),
+                               (bk.OPT_PERSISTENT, (0, 1, 2), (-1, 3))):
             for v in good:
                 bk.set_option(op.handle, opt, v)
             for v in bad:
@@ -600,3 +610,31 @@ def test_options_validate_their_values(bk, cuda):
                     bk.set_option(op.handle, opt, v)
         with pytest.raises(bk.BicgkError):
             bk.set_option(op.handle, 99, 0)
+
+
+def test_automatic_persistent_route(bk, cuda):
+    """BICGK_OPT_PERSISTENT = 0 runs small merged classical solves with two or more right-hand sides
+    in one launch of the persistent kernel and everything else on the graph path: 16^3 with k = 4 in
+    one launch; k = 1, 33^3 (35,937 rows), the basic form and the profiling mode on the graph path.
+    The one-launch solve agrees with the graph path's at trajectory level and with the oracle."""
+    torch = cuda
+    A = I.convdiff7(16, peclet=True)
+    B = torch.from_numpy(I.rhs(A.n, 4, 3)).cuda()
+    with bk.Operator(A) as op:
+        r = op.solve(B, tol=0.0, maxit=6, flags=bk.FLAG_NO_STOP_TEST)
+        assert bk.last_stats(op.handle)["kernel_launches"] == 1
+        Xp = r.X.cpu().numpy()
+        op.solve(B[:, :1].contiguous(), tol=1e-8, maxit=500)
+        assert bk.last_stats(op.handle)["kernel_launches"] > 1
+        op.solve(B, tol=1e-8, maxit=500, variant="classical_plain")
+        assert bk.last_stats(op.handle)["kernel_launches"] > 1
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, 1)
+        Xg = op.solve(B, tol=0.0, maxit=6, flags=bk.FLAG_NO_STOP_TEST).X.cpu().numpy()
+        assert bk.last_stats(op.handle)["kernel_launches"] > 1
+    assert np.all(_colerr(Xp, Xg) <= 1e-12)
+    ro = oracle.solve(A, B.cpu().numpy(), tol=0.0, maxit=6, flags=oracle.NO_STOP_TEST)
+    assert np.all(_colerr(Xp, ro.X) <= 1e-12)
+    A33 = I.convdiff7(33, peclet=True)
+    with bk.Operator(A33) as op:
+        op.solve(torch.from_numpy(I.rhs(A33.n, 2, 3)).cuda(), tol=0.0, maxit=3, flags=bk.FLAG_NO_STOP_TEST)
+        assert bk.last_stats(op.handle)["kernel_launches"] > 1

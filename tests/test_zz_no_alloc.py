@@ -65,6 +65,7 @@ def _reference(torch, A, B, X0, tol, maxit, variant):
     from paper_1907_12874_gb300 import bicgk
     with bicgk.Operator(A) as op:
         bicgk.set_option(op.handle, bicgk.OPT_COMPACT, 1)   # the allocation-free loop keeps its layout
+        bicgk.set_option(op.handle, bicgk.OPT_PERSISTENT, 1)  # and runs the graph path's kernels
         r = op.solve(torch.from_numpy(B).cuda(), X0=None if X0 is None else torch.from_numpy(X0).cuda(),
                      tol=tol, maxit=maxit, variant=variant)
         return r.X.cpu().numpy(), r.iters, r.status, r.hist, r.true_relres
