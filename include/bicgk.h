@@ -298,7 +298,7 @@ enum bicgk_option {
                                       column), so stopped columns stop costing arithmetic;
                                       1: never.  The iterates are those of the full layout up
                                       to summation order.                                      */
-  BICGK_OPT_PERSISTENT = 8          /* merged classical BiCGStab (Algorithm 2) without
+  BICGK_OPT_PERSISTENT = 8,         /* merged classical BiCGStab (Algorithm 2) without
                                       preconditioner: run the solve as ONE cooperative launch of
                                       the persistent batch kernel (a one-system batch over this
                                       operator, kept for the next solve of the same k, whose
@@ -310,6 +310,13 @@ enum bicgk_option {
                                       n_rows*kp <= 2^19), where one launch is faster than the
                                       graph path's many; 1: never; 2: always.  Never in
                                       profiling mode.                                          */
+  BICGK_OPT_SPMM32 = 9              /* the FP32 product of bicgk_solve_mixed and bicgk_spmm_f32
+                                      for kp >= 16 (kp: k rounded up to a power of two):
+                                      0 (default): the sweep kernel (each block sweeps one
+                                      contiguous range of rows, CSR entries prefetched a tile
+                                      ahead); 1: the segment kernel (blocks stride over the
+                                      rows).  Both sum every row in CSR order with FP32 FMAs:
+                                      their results are bitwise equal.                         */
 };
 
 /*

@@ -278,6 +278,7 @@ struct bicgk_op_s {
   int opt_zero_copy = 0;  // BICGK_OPT_HOST_ZERO_COPY
   int opt_compact = 0;    // BICGK_OPT_COMPACT
   int opt_persistent = 0; // BICGK_OPT_PERSISTENT
+  int opt_spmm32 = 0;     // BICGK_OPT_SPMM32
   bicgk_batch pbatch = nullptr;  // one-system batch over this operator for the persistent kernel
   int pbatch_k = 0;
   // launch shapes chosen by the batch autotuner (0 = the per-SM rule above)
@@ -352,7 +353,8 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
   }
   if (st.spmm == 3) {
     sa.vals = A->d_val32;
-    return launch_spmm32(a.kp, sa, A->nsm * spmm32_blocks_per_sm(a.kp, sa.stage_cap), s);
+    sa.fp32_kernel = A->opt_spmm32;
+    return launch_spmm32(a.kp, sa, A->nsm * spmm32_blocks_per_sm(a.kp, sa.stage_cap, sa.fp32_kernel), s);
   }
   if (st.spmm == 5) {  // the fused kernel's grid: its occupancy, at most the reduction buffers' capacity
     int nb = spmm_dot_blocks_per_sm(a.kp, st.op, sa.stage_cap);
@@ -1185,7 +1187,8 @@ int bicgk_spmm_f32(bicgk_op A, int32_t k, const float *X, float *Y, void *stream
   sa.n = A->n;
   sa.stage_cap = kp <= 2 ? A->stage_cap : 0;
   sa.cols_per_lane = 2;
-  const int grid = A->nsm * spmm32_blocks_per_sm(kp, sa.stage_cap);
+  sa.fp32_kernel = A->opt_spmm32;
+  const int grid = A->nsm * spmm32_blocks_per_sm(kp, sa.stage_cap, sa.fp32_kernel);
   if (kp == k && (kp == 1 || (aligned16(X) && aligned16(Y)))) {
     sa.x = X;
     sa.y = Y;
@@ -1691,6 +1694,10 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value) {
     case BICGK_OPT_PERSISTENT:
       if (value < 0 || value > 2) return BICGK_E_INVALID;
       A->opt_persistent = (int)value;
+      break;
+    case BICGK_OPT_SPMM32:
+      if (value < 0 || value > 1) return BICGK_E_INVALID;
+      A->opt_spmm32 = (int)value;
       break;
     default:
       return BICGK_E_INVALID;

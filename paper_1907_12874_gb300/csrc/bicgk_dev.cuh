@@ -139,6 +139,7 @@ struct SpmmArgs {
   int64_t n;
   int stage_cap;  // staged CSR entries per tile (kp <= 2); 0 = read entries directly
   int cols_per_lane = 2;  // RHS-tile width of a lane (kp >= 8 also accepts 4)
+  int fp32_kernel = 0;    // FP32, kp >= 16: 0 the sweep kernel, 1 the segment kernel
 };
 cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s);
 int spmm_blocks_per_sm(int kp, int mode, int stage_cap);
@@ -160,7 +161,7 @@ cudaError_t launch_sddmm(const int32_t *rowptr, const int32_t *colidx, const dou
                          double *g, int64_t n, int k, cudaStream_t s);
 // FP32 y = A x (values, x and y float; one FP32 FMA per nonzero and column).
 cudaError_t launch_spmm32(int kp, const SpmmArgs &a, int grid, cudaStream_t s);
-int spmm32_blocks_per_sm(int kp, int stage_cap);
+int spmm32_blocks_per_sm(int kp, int stage_cap, int fp32_kernel);
 
 // Pack columns [0, ncols) of a caller block with leading dimension ld into the workspace layout
 // (ld = kp, zero padding); X0 may be null.

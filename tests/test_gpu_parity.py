@@ -121,6 +121,30 @@ def test_spmm_f32_matches_oracle(bk, cuda, k, kind):
     assert np.all(np.abs(Y - Yo) <= bound + 1e-300)
 
 
+@pytest.mark.parametrize("k", [9, 16, 24, 32, 64])
+@pytest.mark.parametrize("kind", ["perturbed27_40", "random", "tiny", "perturbed27_9"])
+def test_spmm_f32_sweep_is_bitwise_segment(bk, cuda, k, kind):
+    """The two FP32 kernels (BICGK_OPT_SPMM32: the sweep kernel, default, and the segment kernel)
+    both sum every row in CSR order with FP32 FMAs, so their products are bitwise equal.  The
+    random matrix has empty rows and a 3000-entry row (a warp tile over the staging capacity reads
+    its entries from global memory); "tiny" has fewer rows than the sweep grid has blocks (empty
+    ranges), 9^3 rows leave partial tiles at the ends of the blocks' ranges; k = 9 and 24 are
+    padded to kp = 16 and 32."""
+    torch = cuda
+    A = {"perturbed27_40": lambda: I.perturbed27(40, seed=4), "random": lambda: _random_csr(3001, 7),
+         "tiny": lambda: I.convdiff7(3), "perturbed27_9": lambda: I.perturbed27(9, seed=2)}[kind]()
+    X32 = torch.from_numpy(I.rhs(A.n, k, 5).astype(np.float32)).cuda()
+    with bk.Operator(A) as op:
+        Ys = op.spmm_f32(X32)
+        bk.set_option(op.handle, bk.OPT_SPMM32, 1)
+        Yg = op.spmm_f32(X32)
+        bk.set_option(op.handle, bk.OPT_SPMM32, 0)
+        Ys2 = op.spmm_f32(X32)
+    assert torch.equal(Ys, Yg)
+    assert torch.equal(Ys, Ys2)
+    assert bool(torch.isfinite(Ys).all())
+
+
 @pytest.mark.parametrize("k", [2, 4, 8, 32])
 def test_spmm_unaligned_caller_arrays(bk, cuda, k):
     """Caller blocks that start 8 bytes (FP64) or 4 bytes (FP32) past a 16-byte boundary go
@@ -602,7 +626,8 @@ def test_options_validate_their_values(bk, cuda):
                                (bk.OPT_THETA_IN_S, (0, 1, 2), (-1, 3)),
                                (bk.OPT_HOST_ZERO_COPY, (0, 1), (-1, 2)),
                                (bk.OPT_COMPACT, (0, 1), (-1, 2)),
-                               (bk.OPT_PERSISTENT, (0, 1, 2), (-1, 3))):
+                               (bk.OPT_PERSISTENT, (0, 1, 2), (-1, 3)),
+                               (bk.OPT_SPMM32, (0, 1), (-1, 2))):
             for v in good:
                 bk.set_option(op.handle, opt, v)
             for v in bad:
