@@ -41,6 +41,7 @@ if ROOT not in sys.path:
 
 HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk x flop/FMA x max clock
+L1_PEAK_BPS = 152 * 128 * 2.070e9                   # SMs x L1 data-path bytes/clk x max clock (nominal)
 
 
 def parse():
@@ -398,6 +399,29 @@ def mixed_section(args, bicgk, inputs, torch, dev):
         "mixed_max_true_relres": float(rm.true_relres.max()), "mixed_converged": bool((rm.status == 0).all()),
         "speedup_vs_fp64": ms64 / msm,
     })
+    # the inner solves' dominant kernel, the FP32 product: per-launch event times of one profiled
+    # solve (its column groups one after another), against HBM and against the L1 data path that
+    # carries one x row of kp floats per nonzero
+    with bicgk.Operator(A) as opp:
+        bicgk.set_profiling(opp.handle, True)
+        opp.solve_mixed(B, tol=1e-10, max_outer=20, inner_tol=1e-5, max_inner=5000, want_hist=False)
+        torch.cuda.synchronize()
+        times = bicgk.kernel_times(opp.handle)
+    inner = {k: v for k, v in times.items() if k.startswith(("fp32_", "spmm32_"))}
+    name, (launches, kms) = max(((k, v) for k, v in inner.items() if k.startswith("spmm32_")),
+                                key=lambda kv: kv[1][1])
+    kp = int(name.rsplit("_k", 1)[1])
+    mean_s = kms / launches / 1e3
+    alg = 8.0 * A.nnz + 4.0 * (A.n + 1) + 2 * 4.0 * A.n * kp
+    x_l1 = 4.0 * A.nnz * kp
+    hbm, hbm_kind = hbm_peak()
+    res["fp32_product"] = {
+        "kernel": name, "launches": launches, "mean_launch_us": mean_s * 1e6,
+        "share_of_inner_kernel_time": kms / sum(t for _, t in inner.values()),
+        "algorithmic_bytes_per_launch": alg, "hbm_gbs": alg / mean_s / 1e9, "hbm_frac": alg / mean_s / 1e9 / hbm,
+        "hbm_peak_kind": f"{hbm_kind} copy bandwidth",
+        "l1_x_bytes_per_launch": x_l1, "l1_floor_frac": x_l1 / L1_PEAK_BPS / mean_s,
+        "l1_peak_kind": "nominal L1 data path: 152 SMs x 128 B/clk x 2070 MHz"}
     # error against the oracle's refinement (oracle.solve_mixed) on the sampled columns
     kw = dict(mixed=True, tol=1e-10, max_outer=20, inner_tol=1e-5, max_inner=5000)
     ro = oracle_columns(A, Bh, [(c, kw) for c in cols])

@@ -369,6 +369,7 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
 std::string step_name(const Step &st, int kp) {
   if (st.spmm == 0) return op_name(st.op);
   if (st.spmm == 5) return std::string(spmm_dot_name(st.op)) + "_k" + std::to_string(kp);
+  if (st.spmm == 3) return "spmm32_k" + std::to_string(kp);
   return std::string(st.spmm == 2 ? "spmm_resid_k" : "spmm_k") + std::to_string(kp);
 }
 
