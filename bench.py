@@ -544,7 +544,9 @@ def solve_gbs(A, k: int, variant: str, column_iterations: int, ms: float, groups
 
 def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
     """Every form at k = 1, 2, 4, 8, 16, 32 on the benchmark operator: fixed-iteration timing (graph
-    mode, CUDA events), RHS-iterations/s = k / time per iteration, and the achieved fraction of the
+    mode, CUDA events), RHS-iterations/s = k / time per iteration of a nit-iteration solve (its
+    set-up and finish included), the marginal time of an iteration (a 4 nit-iteration solve minus
+    the nit-iteration one, over 3 nit) with the fixed cost per solve it leaves, and the achieved fraction of the
     HBM copy bandwidth for the algorithmic bytes of one iteration: two products of
     12 nnz + 4 (N + 1) + 16 N k bytes (x read once) and 8 N k bytes per vector pass of Table 2
     (M^-1 copies as one read and one write each).  paper_model_ms is the paper's data-transfer
@@ -565,18 +567,26 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
                 opw.solve(Bk, X=Xk, tol=0.0, maxit=3, variant=v, flags=bicgk.FLAG_NO_STOP_TEST, want_hist=False)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                opw.solve(Bk, X=Xk, tol=0.0, maxit=nit, variant=v, flags=bicgk.FLAG_NO_STOP_TEST,
-                          want_hist=False, want_true=False)
-                e1.record()
-                torch.cuda.synchronize()
-                s_it = e0.elapsed_time(e1) / 1e3 / nit
+                t_solve = {}
+                for m in (nit, 4 * nit):
+                    e0.record()
+                    opw.solve(Bk, X=Xk, tol=0.0, maxit=m, variant=v, flags=bicgk.FLAG_NO_STOP_TEST,
+                              want_hist=False, want_true=False)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    t_solve[m] = e0.elapsed_time(e1) / 1e3
+                s_it = t_solve[nit] / nit
+                # the iteration alone: the difference of the two solves (their set-up, finish and
+                # transfers are the same) over the 3 nit iterations between them
+                s_marg = (t_solve[4 * nit] - t_solve[nit]) / (3 * nit)
                 vecs = TABLE2_VECTORS[base][0 if form == "plain" else 1] + 2 * TABLE2_COPIES[base]
                 # the passes this implementation makes (the SpMM dot epilogues save some at k >= 8)
                 byts = 2 * (12 * nnz + 4 * (N + 1) + 16 * N * k) + (vecs - fused_passes_saved(v, k)) * 8 * N * k
                 C = nnz / N
                 model = (2 * N * (8 * k * (C + 1) + 4 * (3 * C + 1)) + vecs * 8 * N * k) / (hbm_gbs * 1e9)
                 res["rows"][f"{v}/k{k}"] = {"rhs_iterations_per_s": k / s_it, "ms_per_iter": s_it * 1e3,
+                                            "marginal_ms_per_iter": s_marg * 1e3,
+                                            "fixed_ms_per_solve": (t_solve[nit] - nit * s_marg) * 1e3,
                                             "algorithmic_gb_per_iter": byts / 1e9,
                                             "hbm_frac": byts / s_it / (hbm_gbs * 1e9),
                                             "paper_model_ms": model * 1e3}

@@ -306,17 +306,27 @@ enum bicgk_option {
                                       bicgk_batch_tune_persistent; see BICGK_BATCH_PERSISTENT;
                                       host blocks are staged), with its scalar rules and a
                                       residual history.  0 (default): for small systems with at
-                                      least two right-hand sides (n_rows <= 32,768, kp <= 16,
-                                      n_rows*kp <= 2^19), where one launch is faster than the
+                                      least three right-hand sides (n_rows <= 32,768,
+                                      4 <= kp <= 16, n_rows*kp <= 2^19), where one launch is
+                                      faster than the
                                       graph path's many; 1: never; 2: always.  Never in
                                       profiling mode.                                          */
-  BICGK_OPT_SPMM32 = 9              /* the FP32 product of bicgk_solve_mixed and bicgk_spmm_f32
+  BICGK_OPT_SPMM32 = 9,             /* the FP32 product of bicgk_solve_mixed and bicgk_spmm_f32
                                       for kp >= 16 (kp: k rounded up to a power of two):
                                       0 (default): the sweep kernel (each block sweeps one
                                       contiguous range of rows, CSR entries prefetched a tile
                                       ahead); 1: the segment kernel (blocks stride over the
                                       rows).  Both sum every row in CSR order with FP32 FMAs:
                                       their results are bitwise equal.                         */
+  BICGK_OPT_SPMM_ROWS = 10          /* the one-lane-per-row product for kp <= 2 (FP64 and FP32):
+                                      0 (default): the warp-tile kernel where the rows hold at
+                                      most 8 entries on average (nnz <= 8 n_rows), else the
+                                      block-tile kernel; 1: always the block-tile kernel (a
+                                      block stages 256-row tiles of CSR entries in shared
+                                      memory between barriers); 2: always the warp-tile kernel
+                                      (each warp prefetches the entries of its next 32-row tile
+                                      while it multiplies the current one).  Both sum every row
+                                      in CSR order: their results are bitwise equal.           */
 };
 
 /*

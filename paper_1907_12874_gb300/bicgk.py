@@ -236,7 +236,7 @@ def solve(handle: int, B, X0=None, tol: float = 1e-8, maxit: int = 1000, variant
 
 
 (OPT_VEC_BLOCKS_PER_SM, OPT_SPMM_BLOCKS_PER_SM, OPT_RHS_GROUPS, OPT_FUSED_DOTS, OPT_THETA_IN_S,
- OPT_HOST_ZERO_COPY, OPT_COMPACT, OPT_PERSISTENT, OPT_SPMM32) = 1, 2, 3, 4, 5, 6, 7, 8, 9
+ OPT_HOST_ZERO_COPY, OPT_COMPACT, OPT_PERSISTENT, OPT_SPMM32, OPT_SPMM_ROWS) = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10
 
 
 def set_option(handle: int, option: int, value: int) -> None:

@@ -279,6 +279,7 @@ struct bicgk_op_s {
   int opt_compact = 0;    // BICGK_OPT_COMPACT
   int opt_persistent = 0; // BICGK_OPT_PERSISTENT
   int opt_spmm32 = 0;     // BICGK_OPT_SPMM32
+  int opt_spmm_rows = 0;  // BICGK_OPT_SPMM_ROWS
   bicgk_batch pbatch = nullptr;  // one-system batch over this operator for the persistent kernel
   int pbatch_k = 0;
   // launch shapes chosen by the batch autotuner (0 = the per-SM rule above)
@@ -316,23 +317,38 @@ KArgs make_args(bicgk_op A, const Workspace &W, int use_cond, cudaGraphCondition
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-int vec_grid(bicgk_op A, int op) {
+// Blocks of the streaming kernel of `op`: the occupancy (at most 4 per SM), or fewer by option.
+// A kernel that only reduces (no vector written) runs one block per SM at kp <= 2: there each
+// thread has few chunks, and the per-thread share of the block reduction (FP64 additions on the
+// FP64 pipe) and the reduction tail of a larger grid cost more than the latency hiding they buy
+// (128^3, k = 1: delta 18.8 -> 17.4 us, group 1 30.3 -> 25.8 us).
+int vec_grid(bicgk_op A, int op, int kp = 0) {
   if (A->grid_vec_abs > 0) return A->grid_vec_abs;
   int nb = vec_blocks_per_sm(op);
   if (nb > 4) nb = 4;
+  if (kp >= 1 && kp <= 2 && op_has_dots(op)) {
+    int r = 0, w = 0;
+    op_traffic(op, &r, &w);
+    if (w == 0) nb = 1;
+  }
   if (A->opt_vec_blocks > 0 && A->opt_vec_blocks < nb) nb = A->opt_vec_blocks;
   return A->nsm * nb;
 }
 
+// The kp <= 2 product: the warp-tile kernel for short rows (BICGK_OPT_SPMM_ROWS).
+int use_warp_rows(bicgk_op A) {
+  return A->opt_spmm_rows == 2 || (A->opt_spmm_rows == 0 && A->nnz <= 8 * A->n);
+}
+
 int spmm_grid(bicgk_op A, int kp, int mode) {
   if (A->grid_spmm_abs > 0) return A->grid_spmm_abs;
-  int nb = spmm_blocks_per_sm(kp, mode, A->stage_cap);
+  int nb = spmm_blocks_per_sm(kp, mode, A->stage_cap, kp <= 2 ? use_warp_rows(A) : 0);
   if (A->opt_spmm_blocks > 0 && A->opt_spmm_blocks < nb) nb = A->opt_spmm_blocks;
   return A->nsm * nb;
 }
 
 cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t s) {
-  if (st.spmm == 0) return launch_vec(st.op, a, vec_grid(A, st.op), s);
+  if (st.spmm == 0) return launch_vec(st.op, a, vec_grid(A, st.op, a.kp), s);
   SpmmArgs sa;
   sa.rowptr = A->d_rowptr;
   sa.colidx = A->d_col;
@@ -342,6 +358,7 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
   sa.b = st.spmm == 2 ? a.v[st.b] : nullptr;
   sa.n = A->n;
   sa.stage_cap = a.kp <= 2 ? A->stage_cap : 0;
+  sa.warp_rows = a.kp <= 2 ? use_warp_rows(A) : 0;
   sa.cols_per_lane = a.kp >= 8 ? A->spmm_cpl : 2;
   if (st.spmm == 4) {  // y = A^T x: the SpMM kernel over the transposed copy
     bicgk_op T = A->trans;
@@ -349,12 +366,13 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
     sa.colidx = T->d_col;
     sa.vals = T->d_val;
     sa.stage_cap = a.kp <= 2 ? T->stage_cap : 0;
+    sa.warp_rows = a.kp <= 2 ? use_warp_rows(T) : 0;
     return launch_spmm(a.kp, 0, sa, spmm_grid(T, a.kp, 0), s);
   }
   if (st.spmm == 3) {
     sa.vals = A->d_val32;
     sa.fp32_kernel = A->opt_spmm32;
-    return launch_spmm32(a.kp, sa, A->nsm * spmm32_blocks_per_sm(a.kp, sa.stage_cap, sa.fp32_kernel), s);
+    return launch_spmm32(a.kp, sa, A->nsm * spmm32_blocks_per_sm(a.kp, sa.stage_cap, sa.fp32_kernel, sa.warp_rows), s);
   }
   if (st.spmm == 5) {  // the fused kernel's grid: its occupancy, at most the reduction buffers' capacity
     int nb = spmm_dot_blocks_per_sm(a.kp, st.op, sa.stage_cap);
@@ -930,7 +948,7 @@ bool use_persistent(bicgk_op A, int k, int variant, bool jacobi) {
   if (A->opt_persistent == 1 || A->profiling || variant != BICGK_CLASSICAL_MERGED || jacobi) return false;
   if (A->opt_persistent == 2) return true;
   const int kp = pow2_at_least(k);
-  return k >= 2 && kp <= 16 && A->n <= 32768 && A->n * kp <= (int64_t(1) << 19);
+  return kp >= 4 && kp <= 16 && A->n <= 32768 && A->n * kp <= (int64_t(1) << 19);
 }
 
 int build_graph(bicgk_op A, Workspace &W, int variant, bool jacobi, int opts, GraphEntry *ge) {
@@ -1151,6 +1169,7 @@ int bicgk_spmm(bicgk_op A, int32_t k, const double *X, double *Y, void *stream) 
   sa.b = nullptr;
   sa.n = A->n;
   sa.stage_cap = kp <= 2 ? A->stage_cap : 0;
+  sa.warp_rows = kp <= 2 ? use_warp_rows(A) : 0;
   // the caller's layout is the kernel layout when k is a power of two; the kernels read and
   // write kp >= 2 blocks as 16-byte vectors, so the caller's arrays must then be 16-byte aligned
   if (kp == k && (kp == 1 || (aligned16(X) && aligned16(Y)))) {
@@ -1189,7 +1208,8 @@ int bicgk_spmm_f32(bicgk_op A, int32_t k, const float *X, float *Y, void *stream
   sa.stage_cap = kp <= 2 ? A->stage_cap : 0;
   sa.cols_per_lane = 2;
   sa.fp32_kernel = A->opt_spmm32;
-  const int grid = A->nsm * spmm32_blocks_per_sm(kp, sa.stage_cap, sa.fp32_kernel);
+  sa.warp_rows = kp <= 2 ? use_warp_rows(A) : 0;
+  const int grid = A->nsm * spmm32_blocks_per_sm(kp, sa.stage_cap, sa.fp32_kernel, sa.warp_rows);
   if (kp == k && (kp == 1 || (aligned16(X) && aligned16(Y)))) {
     sa.x = X;
     sa.y = Y;
@@ -1699,6 +1719,10 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value) {
     case BICGK_OPT_SPMM32:
       if (value < 0 || value > 1) return BICGK_E_INVALID;
       A->opt_spmm32 = (int)value;
+      break;
+    case BICGK_OPT_SPMM_ROWS:
+      if (value < 0 || value > 2) return BICGK_E_INVALID;
+      A->opt_spmm_rows = (int)value;
       break;
     default:
       return BICGK_E_INVALID;
@@ -2595,6 +2619,7 @@ extern "C" int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *r
   A.d_col = const_cast<int32_t *>(colidx);
   A.d_val = const_cast<double *>(vals);
   A.stage_cap = 0;  // the k <= 2 SpMM reads CSR entries from global memory (same arithmetic)
+  A.opt_spmm_rows = 1;  // ... in the block-tile kernel, whose grid needs no shared memory here
   A.opt_groups = 1;  // one column group, no dot epilogues: bicgk_solve's sequence for k < 8
   A.opt_fused = 1;
   Workspace W;

@@ -127,6 +127,74 @@ cudaError_t launch_vec(int op, const KArgs &a, int grid, cudaStream_t s);
 // Blocks per SM the streaming kernel of `op` reaches (occupancy query).
 int vec_blocks_per_sm(int op);
 
+// Staged-tile helpers of the one-lane-per-row products (kp <= 2).
+//
+// stage_entries: entries [te0, te1) of a row tile into shared memory.  Each thread issues the
+// loads of up to kStageUnroll entries before it stores any of them, so a tile costs one DRAM
+// latency per round of blockDim.x * kStageUnroll entries instead of one per blockDim.x entries.
+constexpr int kStageUnroll = 4;
+template <typename T>
+__device__ __forceinline__ void stage_entries(const int32_t *__restrict__ ci, const T *__restrict__ va, int te0,
+                                              int te1, T *s_val, int32_t *s_col) {
+  const int nt = (int)blockDim.x;
+  for (int e = te0 + (int)threadIdx.x; e < te1; e += nt * kStageUnroll) {
+    T v[kStageUnroll];
+    int32_t c[kStageUnroll];
+#pragma unroll
+    for (int u = 0; u < kStageUnroll; ++u) {
+      const int q = e + u * nt;
+      if (q < te1) {
+        v[u] = __ldg(va + q);
+        c[u] = __ldg(ci + q);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kStageUnroll; ++u) {
+      const int q = e + u * nt;
+      if (q < te1) {
+        s_val[q - te0] = v[u];
+        s_col[q - te0] = c[u];
+      }
+    }
+  }
+}
+
+// One row's sum over staged entries [q0, q1) (tile-relative), four x gathers in flight, the FMAs
+// in entry order (the sum of the entry-by-entry loop).  X: T (kp = 1) or its two-wide vector
+// (kp = 2); the result has X's type.
+template <typename T>
+__device__ __forceinline__ T staged_row(const T *s_val, const int32_t *s_col, const T *__restrict__ xs, int q0,
+                                        int q1) {
+  T y = 0;
+  int q = q0;
+  for (; q + 3 < q1; q += 4) {
+    T a[4], u[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      a[j] = s_val[q + j];
+      u[j] = __ldg(xs + s_col[q + j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y = fma(a[j], u[j], y);
+  }
+  for (; q < q1; ++q) y = fma(s_val[q], __ldg(xs + s_col[q]), y);
+  return y;
+}
+template <typename T, typename T2>
+__device__ __forceinline__ T2 staged_row2(const T *s_val, const int32_t *s_col, const T2 *__restrict__ x2, int q0,
+                                          int q1) {
+  T2 y;
+  y.x = 0;
+  y.y = 0;
+  for (int q = q0; q < q1; ++q) {
+    const T a = s_val[q];
+    const T2 u = __ldg(x2 + s_col[q]);
+    y.x = fma(a, u.x, y.x);
+    y.y = fma(a, u.y, y.y);
+  }
+  return y;
+}
+
 // SpMM: y = A x (mode 0) or y = b - A x (mode 1) for kp in {1,2,4,...,64}.
 // vals, x, y, b point to double (launch_spmm) or float (launch_spmm32) arrays.
 struct SpmmArgs {
@@ -140,9 +208,10 @@ struct SpmmArgs {
   int stage_cap;  // staged CSR entries per tile (kp <= 2); 0 = read entries directly
   int cols_per_lane = 2;  // RHS-tile width of a lane (kp >= 8 also accepts 4)
   int fp32_kernel = 0;    // FP32, kp >= 16: 0 the sweep kernel, 1 the segment kernel
+  int warp_rows = 0;      // kp <= 2: 1 the warp-tile kernel (short rows), 0 the block-tile kernel
 };
 cudaError_t launch_spmm(int kp, int mode, const SpmmArgs &a, int grid, cudaStream_t s);
-int spmm_blocks_per_sm(int kp, int mode, int stage_cap);
+int spmm_blocks_per_sm(int kp, int mode, int stage_cap, int warp_rows = 0);
 // y = A x with the dots of the next listing step taken in the product's epilogue (FP64), then
 // the grid reduction and that step's scalar rule, as the separate dot kernel would do them.
 enum SpmmEpi : int {
@@ -161,7 +230,7 @@ cudaError_t launch_sddmm(const int32_t *rowptr, const int32_t *colidx, const dou
                          double *g, int64_t n, int k, cudaStream_t s);
 // FP32 y = A x (values, x and y float; one FP32 FMA per nonzero and column).
 cudaError_t launch_spmm32(int kp, const SpmmArgs &a, int grid, cudaStream_t s);
-int spmm32_blocks_per_sm(int kp, int stage_cap, int fp32_kernel);
+int spmm32_blocks_per_sm(int kp, int stage_cap, int fp32_kernel, int warp_rows = 0);
 
 // Pack columns [0, ncols) of a caller block with leading dimension ld into the workspace layout
 // (ld = kp, zero padding); X0 may be null.

@@ -911,10 +911,32 @@ __device__ void reduce_and_finalize(const KArgs &a, double2 (&acc)[ND > 0 ? ND :
   const int ntop = two_level ? ngrp : nblk;
   if (sm.ticket != (unsigned)ngrp - 1 + (two_level ? 0 : nblk - 1)) return;
   __threadfence();
+  // few outputs (small kp): several warps per output, so that every thread loads at most a few
+  // partials (one round trip to L2); their warp sums are added in warp order
+  int wpo = 1;
+  while (wpo * 2 * nout * 32 <= (int)blockDim.x) wpo *= 2;
+  if (wpo > 1) {
+    const int tpo = wpo * 32;
+    const int o = threadIdx.x / tpo, sub = threadIdx.x % tpo;
+    double s = 0.0;
+    if (o < nout) {
+      const int d = o / kp, c = o - d * kp;
+#pragma unroll 4
+      for (int b = sub; b < ntop; b += tpo) s += __ldcg(top + (size_t)b * kStride + d * kMaxKp + c);
+    }
+    for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) sm.red[warp][0][0] = s;
+    __syncthreads();
+    if ((int)threadIdx.x < nout) {
+      double t = 0.0;
+      for (int j = 0; j < wpo; ++j) t += sm.red[threadIdx.x * wpo + j][0][0];
+      sm.sums[threadIdx.x] = t;
+    }
+  }
   int tpo = 32;  // lanes per output in the final sum (strided, then a butterfly)
   while (tpo > 1 && tpo * nout > (int)blockDim.x) tpo >>= 1;
   const int groups = blockDim.x / tpo;
-  for (int o0 = 0; o0 < nout; o0 += groups) {
+  for (int o0 = 0; o0 < (wpo > 1 ? 0 : nout); o0 += groups) {
     const int o = o0 + threadIdx.x / tpo, sub = threadIdx.x % tpo;
     double s = 0.0;
     if (o < nout) {
@@ -1131,12 +1153,7 @@ __global__ void __launch_bounds__(kSpmmThreads) spmm_dot_kernel(const SpmmArgs s
       const int64_t r1 = (r0 + kSpmmTileRows < sp.n) ? r0 + kSpmmTileRows : sp.n;
       const int te0 = __ldg(rp + r0), te1 = __ldg(rp + r1);
       const bool staged = (te1 - te0) <= cap;
-      if (staged) {
-        for (int e = te0 + threadIdx.x; e < te1; e += blockDim.x) {
-          s_val[e - te0] = __ldg(va + e);
-          s_col[e - te0] = __ldg(ci + e);
-        }
-      }
+      if (staged) stage_entries<double>(ci, va, te0, te1, s_val, s_col);
       __syncthreads();
       const int64_t r = r0 + threadIdx.x;
       if (r < r1) {
@@ -1145,7 +1162,7 @@ __global__ void __launch_bounds__(kSpmmThreads) spmm_dot_kernel(const SpmmArgs s
           const double *__restrict__ xs = static_cast<const double *>(sp.x);
           double y = 0.0;
           if (staged)
-            for (int e = e0; e < e1; ++e) y = fma(s_val[e - te0], __ldg(xs + s_col[e - te0]), y);
+            y = staged_row<double>(s_val, s_col, xs, e0 - te0, e1 - te0);
           else
             for (int e = e0; e < e1; ++e) y = fma(__ldg(va + e), __ldg(xs + __ldg(ci + e)), y);
           static_cast<double *>(sp.y)[r] = y;
@@ -1154,12 +1171,7 @@ __global__ void __launch_bounds__(kSpmmThreads) spmm_dot_kernel(const SpmmArgs s
           const double2 *__restrict__ x2 = static_cast<const double2 *>(sp.x);
           double2 y = make_double2(0.0, 0.0);
           if (staged) {
-            for (int e = e0; e < e1; ++e) {
-              const double av = s_val[e - te0];
-              const double2 u = __ldg(x2 + s_col[e - te0]);
-              y.x = fma(av, u.x, y.x);
-              y.y = fma(av, u.y, y.y);
-            }
+            y = staged_row2<double, double2>(s_val, s_col, x2, e0 - te0, e1 - te0);
           } else {
             for (int e = e0; e < e1; ++e) {
               const double av = __ldg(va + e);

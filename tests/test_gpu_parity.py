@@ -145,6 +145,34 @@ def test_spmm_f32_sweep_is_bitwise_segment(bk, cuda, k, kind):
     assert bool(torch.isfinite(Ys).all())
 
 
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("kind", ["convdiff7_13", "random", "tiny", "perturbed27_9", "convdiff7_40"])
+def test_row_products_warp_tile_is_bitwise_block_tile(bk, cuda, k, kind):
+    """The two one-lane-per-row products for kp <= 2 (BICGK_OPT_SPMM_ROWS: the warp-tile kernel,
+    default for short rows, and the block-tile kernel) both sum every row in CSR order, so FP64
+    and FP32 products and whole solves (which also run y = b - A x) are bitwise equal.  The random
+    matrix has empty rows and a 3000-entry row, and 27-point rows overflow the warp tile's staging
+    (both read those entries from global memory); "tiny" has fewer rows than the grid has warps."""
+    torch = cuda
+    A = {"convdiff7_13": lambda: I.convdiff7(13), "random": lambda: _random_csr(3001, 7),
+         "tiny": lambda: I.convdiff7(3), "perturbed27_9": lambda: I.perturbed27(9, seed=2),
+         "convdiff7_40": lambda: I.convdiff7(40)}[kind]()
+    X = torch.from_numpy(I.rhs(A.n, k, 5)).cuda()
+    B = torch.from_numpy(I.rhs(A.n, k, 6)).cuda()
+    out = {}
+    with bk.Operator(A) as op:
+        bk.set_option(op.handle, bk.OPT_PERSISTENT, 1)   # the graph path's products
+        for rows in (2, 1):
+            bk.set_option(op.handle, bk.OPT_SPMM_ROWS, rows)
+            Y = op.spmm(X)
+            Y32 = op.spmm_f32(X.float())
+            r = op.solve(B, tol=1e-8, maxit=60, want_hist=False)
+            out[rows] = (Y, Y32, torch.as_tensor(r.X), r.iters.copy())
+    for a, b in zip(out[2][:3], out[1][:3]):
+        assert torch.equal(a, b)
+    assert np.array_equal(out[2][3], out[1][3])
+
+
 @pytest.mark.parametrize("k", [2, 4, 8, 32])
 def test_spmm_unaligned_caller_arrays(bk, cuda, k):
     """Caller blocks that start 8 bytes (FP64) or 4 bytes (FP32) past a 16-byte boundary go
@@ -627,7 +655,8 @@ def test_options_validate_their_values(bk, cuda):
                                (bk.OPT_HOST_ZERO_COPY, (0, 1), (-1, 2)),
                                (bk.OPT_COMPACT, (0, 1), (-1, 2)),
                                (bk.OPT_PERSISTENT, (0, 1, 2), (-1, 3)),
-                               (bk.OPT_SPMM32, (0, 1), (-1, 2))):
+                               (bk.OPT_SPMM32, (0, 1), (-1, 2)),
+                               (bk.OPT_SPMM_ROWS, (0, 1, 2), (-1, 3))):
             for v in good:
                 bk.set_option(op.handle, opt, v)
             for v in bad:
@@ -638,9 +667,10 @@ def test_options_validate_their_values(bk, cuda):
 
 
 def test_automatic_persistent_route(bk, cuda):
-    """BICGK_OPT_PERSISTENT = 0 runs small merged classical solves with two or more right-hand sides
-    in one launch of the persistent kernel and everything else on the graph path: 16^3 with k = 4 in
-    one launch; k = 1, 33^3 (35,937 rows), the basic form and the profiling mode on the graph path.
+    """BICGK_OPT_PERSISTENT = 0 runs small merged classical solves with three or more right-hand
+    sides in one launch of the persistent kernel and everything else on the graph path: 16^3 with
+    k = 4 in one launch; k = 1 and 2, 33^3 (35,937 rows), the basic form and the profiling mode on
+    the graph path.
     The one-launch solve agrees with the graph path's at trajectory level and with the oracle."""
     torch = cuda
     A = I.convdiff7(16, peclet=True)
@@ -650,6 +680,8 @@ def test_automatic_persistent_route(bk, cuda):
         assert bk.last_stats(op.handle)["kernel_launches"] == 1
         Xp = r.X.cpu().numpy()
         op.solve(B[:, :1].contiguous(), tol=1e-8, maxit=500)
+        assert bk.last_stats(op.handle)["kernel_launches"] > 1
+        op.solve(B[:, :2].contiguous(), tol=1e-8, maxit=500)
         assert bk.last_stats(op.handle)["kernel_launches"] > 1
         op.solve(B, tol=1e-8, maxit=500, variant="classical_plain")
         assert bk.last_stats(op.handle)["kernel_launches"] > 1
