@@ -589,6 +589,7 @@ def sweep_section(args, bicgk, inputs, torch, dev, A, hbm_gbs, nit=40):
                                             "fixed_ms_per_solve": (t_solve[nit] - nit * s_marg) * 1e3,
                                             "algorithmic_gb_per_iter": byts / 1e9,
                                             "hbm_frac": byts / s_it / (hbm_gbs * 1e9),
+                                            "hbm_frac_marginal": byts / s_marg / (hbm_gbs * 1e9),
                                             "paper_model_ms": model * 1e3}
                 # error against the oracle: column 0 after 8 fixed iterations of the same solve (past
                 # a few dozen iterations this operator amplifies rounding differences to the percent
