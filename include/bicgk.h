@@ -266,7 +266,8 @@ int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *rowptr, cons
 /* Launch-shape options of an operator (bicgk_set_option); 0 restores the default. */
 enum bicgk_option {
   BICGK_OPT_VEC_BLOCKS_PER_SM = 1, /* blocks of 512 threads per SM for the streaming kernels (0..4;
-                                      default: the occupancy maximum, 2)                      */
+                                      default: the occupancy maximum, 2; one for the kernels
+                                      that only reduce when kp <= 2); a value caps the default */
   BICGK_OPT_SPMM_BLOCKS_PER_SM = 2, /* blocks of 256 threads per SM for the SpMM (0..32; default:
                                       the occupancy maximum)                                   */
   BICGK_OPT_RHS_GROUPS = 3,         /* 0 (default): k >= 8 is solved as two column groups
