@@ -375,7 +375,7 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
     return launch_spmm32(a.kp, sa, A->nsm * spmm32_blocks_per_sm(a.kp, sa.stage_cap, sa.fp32_kernel, sa.warp_rows), s);
   }
   if (st.spmm == 5) {  // the fused kernel's grid: its occupancy, at most the reduction buffers' capacity
-    int nb = spmm_dot_blocks_per_sm(a.kp, st.op, sa.stage_cap);
+    int nb = spmm_dot_blocks_per_sm(a.kp, st.op, sa.stage_cap, sa.warp_rows);
     if (nb > kPartBlocksPerSm) nb = kPartBlocksPerSm;
     if (A->opt_spmm_blocks > 0 && A->opt_spmm_blocks < nb) nb = A->opt_spmm_blocks;
     return launch_spmm_dot(a.kp, st.op, sa, a, A->nsm * nb, s);

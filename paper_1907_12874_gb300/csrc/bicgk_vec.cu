@@ -1190,6 +1190,29 @@ __global__ void __launch_bounds__(kSpmmThreads) spmm_dot_kernel(const SpmmArgs s
   reduce_and_finalize<E, kSpmmThreads>(a, acc);
 }
 
+// kp <= 2 over short rows: the warp-tile product (warp_tile_rows, the kernel spmm_warp_kernel
+// runs) with the same epilogue dots, then the same reduction.
+template <int KP, class E>
+__global__ void __launch_bounds__(kSpmmThreads) spmm_dot_warp_kernel(const SpmmArgs sp, const KArgs a) {
+  static_assert(KP == 1 || KP == 2, "warp tiles: kp <= 2");
+  __shared__ double s_val[kSpmmThreads / 32][kWarpCap];
+  __shared__ int32_t s_col[kSpmmThreads / 32][kWarpCap];
+  double2 acc[E::ND];
+#pragma unroll
+  for (int d = 0; d < E::ND; ++d) acc[d] = make_double2(0.0, 0.0);
+  const int w = threadIdx.x >> 5;
+  warp_tile_rows<double, KP>(sp, s_val[w], s_col[w], [&](int64_t row, auto y) {
+    if constexpr (KP == 1) {
+      static_cast<double *>(sp.y)[row] = y;
+      E::acc1(a, row, y, acc);
+    } else {
+      static_cast<double2 *>(sp.y)[row] = y;
+      E::acc2(a, row, y, acc);
+    }
+  });
+  reduce_and_finalize<E, kSpmmThreads>(a, acc);
+}
+
 // ------------------------------------------------------------------ pack / unpack / reset
 
 // Columns [0, ncols) of a caller block with leading dimension ld (B, X0 already offset to the
@@ -1388,6 +1411,12 @@ cudaError_t dot_smem(int stage_cap, size_t *smem) {
 }
 template <int KP, class E>
 cudaError_t launch_dot_kp(const SpmmArgs &s, const KArgs &a, int grid, cudaStream_t st) {
+  if constexpr (KP <= 2) {
+    if (s.warp_rows) {
+      spmm_dot_warp_kernel<KP, E><<<grid, kSpmmThreads, 0, st>>>(s, a);
+      return cudaGetLastError();
+    }
+  }
   size_t smem = 0;
   cudaError_t e = dot_smem<KP, E>(s.stage_cap, &smem);
   if (e != cudaSuccess) return e;
@@ -1395,9 +1424,17 @@ cudaError_t launch_dot_kp(const SpmmArgs &s, const KArgs &a, int grid, cudaStrea
   return cudaGetLastError();
 }
 template <int KP, class E>
-int occ_dot_kp(int stage_cap) {
+int occ_dot_kp(int stage_cap, int warp_rows) {
   size_t smem = 0;
   int nb = 0;
+  if constexpr (KP <= 2) {
+    if (warp_rows) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_dot_warp_kernel<KP, E>, kSpmmThreads, 0) !=
+          cudaSuccess)
+        return 1;
+      return nb > 0 ? nb : 1;
+    }
+  }
   if (dot_smem<KP, E>(stage_cap, &smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_dot_kernel<KP, E>, kSpmmThreads, smem) != cudaSuccess)
     return 1;
@@ -1417,15 +1454,15 @@ cudaError_t launch_dot_e(int kp, const SpmmArgs &s, const KArgs &a, int grid, cu
   }
 }
 template <class E>
-int occ_dot_e(int kp, int stage_cap) {
+int occ_dot_e(int kp, int stage_cap, int warp_rows) {
   switch (kp) {
-    case 1: return occ_dot_kp<1, E>(stage_cap);
-    case 2: return occ_dot_kp<2, E>(stage_cap);
-    case 4: return occ_dot_kp<4, E>(stage_cap);
-    case 8: return occ_dot_kp<8, E>(stage_cap);
-    case 16: return occ_dot_kp<16, E>(stage_cap);
-    case 32: return occ_dot_kp<32, E>(stage_cap);
-    case 64: return occ_dot_kp<64, E>(stage_cap);
+    case 1: return occ_dot_kp<1, E>(stage_cap, warp_rows);
+    case 2: return occ_dot_kp<2, E>(stage_cap, warp_rows);
+    case 4: return occ_dot_kp<4, E>(stage_cap, warp_rows);
+    case 8: return occ_dot_kp<8, E>(stage_cap, warp_rows);
+    case 16: return occ_dot_kp<16, E>(stage_cap, warp_rows);
+    case 32: return occ_dot_kp<32, E>(stage_cap, warp_rows);
+    case 64: return occ_dot_kp<64, E>(stage_cap, warp_rows);
     default: return 1;
   }
 }
@@ -1437,10 +1474,10 @@ cudaError_t launch_spmm_dot(int kp, int epi, const SpmmArgs &s, const KArgs &a, 
   if (epi == EPI_G1_PP) return launch_dot_e<EpiG1PP>(kp, s, a, grid, st);
   return cudaErrorInvalidValue;
 }
-int spmm_dot_blocks_per_sm(int kp, int epi, int stage_cap) {
-  if (epi == EPI_DELTA) return occ_dot_e<EpiDelta>(kp, stage_cap);
-  if (epi == EPI_G1) return occ_dot_e<EpiG1>(kp, stage_cap);
-  if (epi == EPI_G1_PP) return occ_dot_e<EpiG1PP>(kp, stage_cap);
+int spmm_dot_blocks_per_sm(int kp, int epi, int stage_cap, int warp_rows) {
+  if (epi == EPI_DELTA) return occ_dot_e<EpiDelta>(kp, stage_cap, warp_rows);
+  if (epi == EPI_G1) return occ_dot_e<EpiG1>(kp, stage_cap, warp_rows);
+  if (epi == EPI_G1_PP) return occ_dot_e<EpiG1PP>(kp, stage_cap, warp_rows);
   return 1;
 }
 const char *spmm_dot_name(int epi) {

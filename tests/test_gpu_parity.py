@@ -504,9 +504,10 @@ def test_fused_dots_match_separate_kernels(bk, cuda, variant, k, kind):
     """The dot kernel that follows an SpMM taken into the SpMM's epilogue (BICGK_OPT_FUSED_DOTS),
     and theta = (s, s) taken in the s update (BICGK_OPT_THETA_IN_S), give the iterates of the
     separate kernels up to the summation order of those dots, and the oracle's.  Each forced on
-    and off at every kp, so the fused one-lane-per-row kernel (kp <= 2) runs with staged tiles
-    (7-point stencil) and with tiles larger than the stage buffer (27-point stencil, 256-row
-    tiles of 6,912 entries)."""
+    and off at every kp, so the fused one-lane-per-row kernels (kp <= 2) run with staged tiles
+    (7-point stencil: the warp-tile kernel, and the block-tile kernel by BICGK_OPT_SPMM_ROWS = 1)
+    and with tiles larger than the stage buffer (27-point stencil, 256-row tiles of 6,912
+    entries)."""
     torch = cuda
     A = I.convdiff7(12, peclet=True) if kind == "convdiff7_peclet" else I.perturbed27(11, seed=5)
     B = I.rhs(A.n, k, 4)
@@ -523,6 +524,13 @@ def test_fused_dots_match_separate_kernels(bk, cuda, variant, k, kind):
             assert np.all(_colerr(X[fz, th], ro.X) <= 1e-12), (fz, th)
             np.testing.assert_allclose(r.hist[:7], ro.hist[:7], rtol=1e-10)
             assert np.all(_colerr(X[fz, th], X[1, 1]) <= 1e-13), (fz, th)
+        if k <= 2 and kind == "convdiff7_peclet":   # the fused block-tile kernel on short rows too
+            bk.set_option(op.handle, bk.OPT_SPMM_ROWS, 1)
+            bk.set_option(op.handle, bk.OPT_FUSED_DOTS, 2)
+            r = op.solve(Bd, tol=0.0, maxit=6, variant=variant, flags=bk.FLAG_NO_STOP_TEST)
+            assert np.all(_colerr(r.X.cpu().numpy(), ro.X) <= 1e-12)
+            assert np.all(_colerr(r.X.cpu().numpy(), X[1, 1]) <= 1e-13)
+            bk.set_option(op.handle, bk.OPT_SPMM_ROWS, 0)
         r = op.solve(Bd, tol=1e-8, maxit=1000, variant=variant)  # both forced on
         Xf = r.X.cpu().numpy()
     rof = oracle.solve(A, B, tol=1e-8, maxit=1000, variant=variant)
