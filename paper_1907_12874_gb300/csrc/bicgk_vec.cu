@@ -981,16 +981,14 @@ BICGK_ONE_BLOCK(OP3_L1)
 BICGK_ONE_BLOCK(OP3_L2)
 #undef BICGK_ONE_BLOCK
 
-// Chunks of two doubles each thread loads before computing (memory-level parallelism).  Group 3
-// of Algorithm 2 streams five vectors: one chunk already keeps 80 KB per SM in flight, more than
-// the ~36 KB the copy bandwidth needs at DRAM latency, and two spilled under the 64-register cap.
+// Chunks of two doubles each thread loads before computing (memory-level parallelism): two
+// for every op.  Group 3 of Algorithm 2 streams five vectors and spills 60 bytes per thread with
+// two chunks under the 64-register cap, yet the four-group benchmark loop runs 0.5 % faster with
+// them than with one (10,607 against 10,553 RHS-iterations/s, three runs each; the same
+// per-thread order of the chunks, so the same results).
 template <int OP>
 struct VecChunks {
   static constexpr int value = 2;
-};
-template <>
-struct VecChunks<OP_G3> {
-  static constexpr int value = 1;
 };
 
 template <int OP>
