@@ -146,17 +146,28 @@ def test_spmm_f32_sweep_is_bitwise_segment(bk, cuda, k, kind):
 
 
 @pytest.mark.parametrize("k", [1, 2])
-@pytest.mark.parametrize("kind", ["convdiff7_13", "random", "tiny", "perturbed27_9", "convdiff7_40"])
+@pytest.mark.parametrize("kind", ["convdiff7_13", "random", "tiny", "perturbed27_9", "convdiff7_40", "one_row",
+                                  "empty_rows"])
 def test_row_products_warp_tile_is_bitwise_block_tile(bk, cuda, k, kind):
     """The two one-lane-per-row products for kp <= 2 (BICGK_OPT_SPMM_ROWS: the warp-tile kernel,
     default for short rows, and the block-tile kernel) both sum every row in CSR order, so FP64
     and FP32 products and whole solves (which also run y = b - A x) are bitwise equal.  The random
     matrix has empty rows and a 3000-entry row, and 27-point rows overflow the warp tile's staging
-    (both read those entries from global memory); "tiny" has fewer rows than the grid has warps."""
+    (both read those entries from global memory); "tiny" has fewer rows than the grid has warps,
+    "one_row" a single row, "empty_rows" no entries at all."""
     torch = cuda
     A = {"convdiff7_13": lambda: I.convdiff7(13), "random": lambda: _random_csr(3001, 7),
          "tiny": lambda: I.convdiff7(3), "perturbed27_9": lambda: I.perturbed27(9, seed=2),
-         "convdiff7_40": lambda: I.convdiff7(40)}[kind]()
+         "convdiff7_40": lambda: I.convdiff7(40),
+         "one_row": lambda: I.CSR(np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]), "one_row"),
+         "empty_rows": lambda: I.CSR(np.zeros(101, np.int32), np.zeros(0, np.int32), np.zeros(0), "empty")}[kind]()
+    if kind == "empty_rows":   # no entries: both products are zero; no solve (A is singular)
+        X = torch.from_numpy(I.rhs(A.n, k, 5)).cuda()
+        with bk.Operator(A) as op:
+            for rows in (2, 1):
+                bk.set_option(op.handle, bk.OPT_SPMM_ROWS, rows)
+                assert not bool(op.spmm(X).any()) and not bool(op.spmm_f32(X.float()).any())
+        return
     X = torch.from_numpy(I.rhs(A.n, k, 5)).cuda()
     B = torch.from_numpy(I.rhs(A.n, k, 6)).cuda()
     out = {}
