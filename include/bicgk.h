@@ -267,9 +267,13 @@ int bicgk_solve_noalloc(int64_t n_rows, int64_t nnz, const int32_t *rowptr, cons
 enum bicgk_option {
   BICGK_OPT_VEC_BLOCKS_PER_SM = 1, /* blocks of 512 threads per SM for the streaming kernels (0..4;
                                       default: the occupancy maximum, 2; one for the kernels
-                                      that only reduce when kp <= 2); a value caps the default */
+                                      that only reduce when kp <= 2, and one for every
+                                      streaming kernel of a solve that runs four concurrent
+                                      column groups); a value caps the occupancy maximum       */
   BICGK_OPT_SPMM_BLOCKS_PER_SM = 2, /* blocks of 256 threads per SM for the SpMM (0..32; default:
-                                      the occupancy maximum)                                   */
+                                      the occupancy maximum, at most 4 in a solve of four
+                                      concurrent column groups and in a one-group solve of
+                                      kp = 4); a value caps the occupancy maximum              */
   BICGK_OPT_RHS_GROUPS = 3,         /* 0 (default): k >= 8 is solved as two column groups
                                       running concurrently on internal streams, k >= 32 as four
                                       (bicgk_solve_mixed: two from k = 16); 1: one group;

@@ -280,6 +280,7 @@ struct bicgk_op_s {
   int opt_persistent = 0; // BICGK_OPT_PERSISTENT
   int opt_spmm32 = 0;     // BICGK_OPT_SPMM32
   int opt_spmm_rows = 0;  // BICGK_OPT_SPMM_ROWS
+  int cur_groups = 1;     // column groups of the solve being captured or run (launch shapes)
   bicgk_batch pbatch = nullptr;  // one-system batch over this operator for the persistent kernel
   int pbatch_k = 0;
   // launch shapes chosen by the batch autotuner (0 = the per-SM rule above)
@@ -331,8 +332,26 @@ int vec_grid(bicgk_op A, int op, int kp = 0) {
     op_traffic(op, &r, &w);
     if (w == 0) nb = 1;
   }
-  if (A->opt_vec_blocks > 0 && A->opt_vec_blocks < nb) nb = A->opt_vec_blocks;
+  if (A->opt_vec_blocks > 0) {
+    if (A->opt_vec_blocks < nb) nb = A->opt_vec_blocks;
+  } else if (A->cur_groups >= 4) {
+    nb = 1;  // four concurrent groups: the other groups' kernels fill the SMs (see auto_spmm_cap)
+  }
   return A->nsm * nb;
+}
+
+// Automatic cap on the SpMM blocks per SM (0: none), by the solve's concurrency.  Measured at 128^3
+// (7-point, merged classical, fixed 300 iterations, ms per iteration): with four concurrent groups
+// 4 product blocks per SM and 1 streaming block per SM (vec_grid) gave 2.884 against 2.961 (k = 32)
+// and 5.737 against 5.845 (k = 64): fewer blocks of each kernel let the four groups' FP64-bound
+// products and bandwidth-bound updates share every SM; over the twelve forms at k = 32 (bench
+// sweep) nine gained 2-5 %, the merged Pipelined and Improved forms lost 0.5-1.4 %.  With two
+// groups 4 product blocks were 10 % slower, and the streaming cap helped merged classical
+// (0.5-2 %) but cost other forms up to 5 %: neither is taken.  One group of kp = 4 took 0.449
+// against 0.462 with 4 product blocks (every form 2-3 % faster; the streaming cap was slower).
+int auto_spmm_cap(bicgk_op A, int kp) {
+  if (A->cur_groups >= 4 || (A->cur_groups == 1 && kp == 4)) return 4;
+  return 0;
 }
 
 // The kp <= 2 product: the warp-tile kernel for short rows (BICGK_OPT_SPMM_ROWS).
@@ -343,7 +362,8 @@ int use_warp_rows(bicgk_op A) {
 int spmm_grid(bicgk_op A, int kp, int mode) {
   if (A->grid_spmm_abs > 0) return A->grid_spmm_abs;
   int nb = spmm_blocks_per_sm(kp, mode, A->stage_cap, kp <= 2 ? use_warp_rows(A) : 0);
-  if (A->opt_spmm_blocks > 0 && A->opt_spmm_blocks < nb) nb = A->opt_spmm_blocks;
+  const int cap = A->opt_spmm_blocks > 0 ? A->opt_spmm_blocks : auto_spmm_cap(A, kp);
+  if (cap > 0 && cap < nb) nb = cap;
   return A->nsm * nb;
 }
 
@@ -377,7 +397,8 @@ cudaError_t launch_step(bicgk_op A, const Step &st, const KArgs &a, cudaStream_t
   if (st.spmm == 5) {  // the fused kernel's grid: its occupancy, at most the reduction buffers' capacity
     int nb = spmm_dot_blocks_per_sm(a.kp, st.op, sa.stage_cap, sa.warp_rows);
     if (nb > kPartBlocksPerSm) nb = kPartBlocksPerSm;
-    if (A->opt_spmm_blocks > 0 && A->opt_spmm_blocks < nb) nb = A->opt_spmm_blocks;
+    const int cap = A->opt_spmm_blocks > 0 ? A->opt_spmm_blocks : auto_spmm_cap(A, a.kp);
+    if (cap > 0 && cap < nb) nb = cap;
     return launch_spmm_dot(a.kp, st.op, sa, a, A->nsm * nb, s);
   }
   const int mode = st.spmm == 2 ? 1 : 0;
@@ -1267,6 +1288,13 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
   // them one after another on the caller's stream.
   const int ngroups = num_groups(A, k);
   const bool concurrent = !A->profiling && ngroups >= 2;
+  // the launch shapes follow the solve's groups (auto_spmm_cap, vec_grid), in the profiling mode
+  // too, so that it times the kernels the graph runs; other entry points see one group
+  struct GroupsScope {
+    bicgk_op A;
+    ~GroupsScope() { A->cur_groups = 1; }
+  } groups_scope{A};
+  A->cur_groups = ngroups;
   int c0[kMaxGroups + 1];
   for (int g = 0; g <= ngroups; ++g) c0[g] = (int)((int64_t)g * k / ngroups);
   int rc;
@@ -1331,7 +1359,7 @@ int bicgk_solve(bicgk_op A, int32_t k, const double *B, const double *X0, double
       if ((rc = run_profiled(A, W, variant, jacobi, opts, a0, gs))) return rc;
     } else {
       const bool cg = compact_columns(A, variant, W.kp);
-      const int key = gkey + 10000 * (cg ? 1 : 0);
+      const int key = gkey + 10000 * (cg ? 1 : 0) + 100000 * ngroups;  // shapes depend on the groups
       auto it = W.graphs.find(key);
       if (it == W.graphs.end()) {
         GraphEntry ge;
