@@ -355,8 +355,10 @@ int bicgk_set_option(bicgk_op A, int option, int64_t value);
  * bicgk_batch_tune: autotuner.  For every system, times its streaming kernel (group 3 of
  *   Algorithm 2) over grid sizes of 1..64 double2 chunks per thread, and its SpMM over
  *   1..64 passes of rows per block (rows per CTA) and 2 or 4 columns per lane (RHS-tile width,
- *   kp >= 8), `reps` launches each, and keeps the fastest.  Writes the chosen grid sizes and
- *   tile widths to the nullable arrays [nsys].  The shapes apply to both solve modes.
+ *   kp >= 8), `reps` launches each, and keeps the fastest, within at most 4 SpMM blocks of 256
+ *   and 1 streaming block of 512 threads per SM (the systems share the GPU in the graph mode;
+ *   without tuning those are the shapes).  Writes the chosen grid sizes and tile widths to the
+ *   nullable arrays [nsys].  The shapes apply to both solve modes.
  * bicgk_batch_solve: B[i], X0[i] (X0 nullable, or entries nullable), X[i] are DEVICE arrays of
  *   n_rows[i]*k[i] FP64 in the layout of bicgk_solve; every other argument as there.  iters,
  *   status, true_relres (nullable) are host arrays of sum(k) entries, systems in order.

@@ -2179,11 +2179,18 @@ int bicgk_batch_create(bicgk_batch *out, int32_t nsys, const int64_t *n_rows, co
   // each system runs as one column group without dot epilogues or column compaction, in the
   // graph and in the launch loop alike (the loop calls bicgk_solve with these operators, on the
   // graph path)
+  // Launch shapes: the systems' kernels share the GPU (the graph runs them as concurrent
+  // branches), so each takes at most 4 SpMM blocks and 1 streaming block per SM, the caps that pay
+  // for four concurrent column groups of one solve (auto_spmm_cap).  Measured on the 64-system
+  // batch (16^3-64^3, k = 1..8, tuned shapes): graph 313 against 339 ms, launch loop 596 against
+  // 627 ms (the streaming cap carries it: 4 SpMM blocks with 2 streaming blocks changed nothing).
   for (int i = 0; i < nsys && rc == BICGK_OK; ++i) {
     b->ops[i]->opt_groups = 1;
     b->ops[i]->opt_fused = 1;
     b->ops[i]->opt_compact = 1;
     b->ops[i]->opt_persistent = 1;
+    b->ops[i]->opt_spmm_blocks = 4;
+    b->ops[i]->opt_vec_blocks = 1;
   }
   if (rc == BICGK_OK) rc = batch_alloc_state(b);
   if (rc != BICGK_OK) {
